@@ -1,0 +1,294 @@
+"""FP64 CPU oracle for cyclic compact banded solves -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library never imports it, and
+it imports nothing from the GPU library: the two share no code.  Inputs reach
+both sides from the seeded generators in ``paper_2101_02286_gb300.workloads``,
+which hold none of the method's arithmetic.
+
+What the oracle computes is the plain definition of the method's result:
+
+* ``central_rhs``      d = S f, periodic central differences, paper Eq. 1
+                       (right-hand side; K-term Lele form).
+* ``solve_cyclic``     x = A^{-1} d for cyclic banded A.  Tridiagonal: Thomas +
+                       Sherman-Morrison; any half-bandwidth r: banded LU +
+                       rank-2r Woodbury (C routines in ``cbs_oracle.c``).
+                       The paper's solver is direct (abstract, Sec. 3), so its
+                       exact result is this solution.
+* ``derivative``       x = A^{-1} S f, the compact first derivative (Eq. 1).
+* ``dense_matrix`` / ``dense_solve``  brute force for tiny n (partial pivoting).
+* ``adjoint_variable_tri``  gradients of L = <g, x> for x = A(alpha)^{-1} S f:
+                       lambda = A^{-T} g, grad_f = S^T lambda,
+                       grad_alpha_i = -lambda_i (x_{i-1} + x_{i+1}).  The paper
+                       has no adjoint; this is the textbook adjoint of a linear
+                       solve.
+* ``reduced_system_dense``  the interface system A-hat of Sec. 3 formed as the
+                       Schur complement of the permuted matrix P A P^T
+                       (Fig. 4 block-LU view), by dense linear algebra.
+
+Every routine is FP64.  Parity is pinned in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cbs_oracle.c")
+_LIB = os.path.join(_HERE, "libcbs_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP over lines) into oracle/."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L = ctypes.c_long
+        lib.orc_central_rhs.argtypes = [dp, dp, L, L, dp, ctypes.c_int, ctypes.c_double]
+        lib.orc_central_rhs_transpose.argtypes = [dp, dp, L, L, dp, ctypes.c_int, ctypes.c_double]
+        lib.orc_cyclic_tri.argtypes = [dp, L, dp, dp, L, L]
+        lib.orc_cyclic_tri.restype = ctypes.c_int
+        lib.orc_cyclic_banded.argtypes = [dp, L, dp, dp, L, L, ctypes.c_int]
+        lib.orc_cyclic_banded.restype = ctypes.c_int
+        lib.orc_banded_matvec.argtypes = [dp, L, dp, dp, L, L, ctypes.c_int]
+        lib.orc_dense_solve.argtypes = [dp, dp, L]
+        lib.orc_dense_solve.restype = ctypes.c_int
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the batched C routines use."""
+    return int(_load().orc_num_threads())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _lines(a: np.ndarray, axis: int):
+    """Move `axis` last and return a contiguous (lines, n) FP64 view + restore info."""
+    a = np.moveaxis(np.asarray(a, dtype=np.float64), axis, -1)
+    shape = a.shape
+    return np.ascontiguousarray(a).reshape(-1, shape[-1]), shape
+
+
+def _unlines(a2: np.ndarray, shape, axis: int) -> np.ndarray:
+    return np.moveaxis(a2.reshape(shape), -1, axis)
+
+
+# ---------------------------------------------------------------- stencils
+def central_rhs(f, coefs, h, axis=-1):
+    """d_i = sum_k coefs[k-1] (f_{i+k} - f_{i-k}) / (2 k h), periodic (Eq. 1 RHS)."""
+    f2, shape = _lines(f, axis)
+    c = np.ascontiguousarray(coefs, dtype=np.float64)
+    out = np.empty_like(f2)
+    _load().orc_central_rhs(_ptr(f2), _ptr(out), f2.shape[0], f2.shape[1], _ptr(c), len(c), float(h))
+    return _unlines(out, shape, axis)
+
+
+def central_rhs_transpose(g, coefs, h, axis=-1):
+    """S^T g for the stencil of central_rhs (scatter form)."""
+    g2, shape = _lines(g, axis)
+    c = np.ascontiguousarray(coefs, dtype=np.float64)
+    out = np.empty_like(g2)
+    _load().orc_central_rhs_transpose(_ptr(g2), _ptr(out), g2.shape[0], g2.shape[1], _ptr(c), len(c), float(h))
+    return _unlines(out, shape, axis)
+
+
+# ---------------------------------------------------------------- matrices
+def toeplitz_bands(n, lhs):
+    """Bands (2r+1, n) of the symmetric cyclic Toeplitz LHS with diagonal 1.
+
+    lhs = (alpha,) gives B[alpha, 1, alpha] (Eq. 1 LHS); lhs = (alpha, beta)
+    gives B[beta, alpha, 1, alpha, beta].
+    """
+    lhs = list(lhs)
+    r = len(lhs)
+    b = np.zeros((2 * r + 1, n))
+    b[r] = 1.0
+    for q in range(1, r + 1):
+        b[r - q] = lhs[q - 1]
+        b[r + q] = lhs[q - 1]
+    return b
+
+
+def variable_alpha_bands(alpha_lines):
+    """Row-wise variable tridiagonal bands: A[i,i-1] = A[i,i+1] = alpha_i, A[i,i] = 1.
+
+    alpha_lines: (lines, n).  Returns (lines, 3, n).
+    """
+    a = np.asarray(alpha_lines, dtype=np.float64)
+    return np.stack([a, np.ones_like(a), a], axis=-2)
+
+
+def transpose_bands(bands):
+    """Bands of A^T from bands of A (any r): A^T[i, i+q] = A[i+q, i]."""
+    bands = np.asarray(bands, dtype=np.float64)
+    w = bands.shape[-2]
+    r = (w - 1) // 2
+    out = np.empty_like(bands)
+    for k in range(w):
+        q = k - r  # A^T[i, i+q] = A[i+q, i] lives on diagonal -q of row i+q
+        out[..., k, :] = np.roll(bands[..., 2 * r - k, :], -q, axis=-1)
+    return out
+
+
+def dense_matrix(bands):
+    """Dense n x n cyclic matrix from one band set (2r+1, n)."""
+    bands = np.asarray(bands, dtype=np.float64)
+    w, n = bands.shape
+    r = (w - 1) // 2
+    A = np.zeros((n, n))
+    for i in range(n):
+        for k in range(w):
+            A[i, (i + k - r) % n] += bands[k, i]
+    return A
+
+
+def dense_solve(A, b):
+    """Gaussian elimination with partial pivoting (C), for tiny systems."""
+    A = np.array(A, dtype=np.float64, order="C")
+    x = np.array(b, dtype=np.float64, order="C")
+    if _load().orc_dense_solve(_ptr(A), _ptr(x), A.shape[0]):
+        raise ArithmeticError("singular dense system")
+    return x
+
+
+# ---------------------------------------------------------------- solves
+def solve_cyclic(bands, d, axis=-1, method="auto"):
+    """x = A^{-1} d along `axis`.
+
+    bands: (2r+1, n) shared by all lines, or (..., 2r+1, n) with one band set
+    per line (leading dims equal to those of d with `axis` moved last).
+    method: "sm" (tridiagonal Thomas + Sherman-Morrison), "woodbury" (banded LU
+    + rank-2r Woodbury) or "auto" (sm for r = 1).
+    """
+    d2, shape = _lines(d, axis)
+    lines, n = d2.shape
+    bands = np.asarray(bands, dtype=np.float64)
+    w = bands.shape[-2]
+    r = (w - 1) // 2
+    if bands.ndim == 2:
+        b2 = np.ascontiguousarray(bands)
+        stride = 0
+    else:
+        b2 = np.ascontiguousarray(bands.reshape(lines, w, n))
+        stride = w * n
+    x = np.empty_like(d2)
+    lib = _load()
+    if method == "auto":
+        method = "sm" if r == 1 else "woodbury"
+    if method == "sm":
+        assert r == 1
+        rc = lib.orc_cyclic_tri(_ptr(b2), stride, _ptr(d2), _ptr(x), lines, n)
+    else:
+        rc = lib.orc_cyclic_banded(_ptr(b2), stride, _ptr(d2), _ptr(x), lines, n, r)
+    if rc:
+        raise ArithmeticError("zero pivot in the oracle solve")
+    return _unlines(x, shape, axis)
+
+
+def matvec(bands, x, axis=-1):
+    """A x along `axis` (bands shared or per line, as in solve_cyclic)."""
+    x2, shape = _lines(x, axis)
+    lines, n = x2.shape
+    bands = np.asarray(bands, dtype=np.float64)
+    w = bands.shape[-2]
+    r = (w - 1) // 2
+    if bands.ndim == 2:
+        b2, stride = np.ascontiguousarray(bands), 0
+    else:
+        b2, stride = np.ascontiguousarray(bands.reshape(lines, w, n)), w * n
+    out = np.empty_like(x2)
+    _load().orc_banded_matvec(_ptr(b2), stride, _ptr(x2), _ptr(out), lines, n, r)
+    return _unlines(out, shape, axis)
+
+
+def derivative(f, lhs, coefs, h, axis=-1):
+    """Compact first derivative along `axis`: x = A^{-1} S f (Eq. 1)."""
+    n = np.shape(f)[axis]
+    return solve_cyclic(toeplitz_bands(n, lhs), central_rhs(f, coefs, h, axis), axis)
+
+
+def derivative_variable_tri(f, alpha, coefs, h, axis=-1):
+    """x = A(alpha)^{-1} S f with row-wise alpha (same shape as f)."""
+    a2, shape = _lines(alpha, axis)
+    d2, _ = _lines(central_rhs(f, coefs, h, axis), axis)
+    x2 = solve_cyclic(variable_alpha_bands(a2), d2, axis=-1)
+    return _unlines(x2, shape, axis)
+
+
+def adjoint_variable_tri(f, alpha, g, coefs, h, axis=-1):
+    """Gradients of L = sum(g * x) for x = A(alpha)^{-1} S f.
+
+    Returns (grad_f, grad_alpha, lam, x) with lam = A^{-T} g,
+    grad_f = S^T lam and grad_alpha_i = -lam_i (x_{i-1} + x_{i+1}).
+    """
+    a2, shape = _lines(alpha, axis)
+    g2, _ = _lines(g, axis)
+    f2, _ = _lines(f, axis)
+    bands = variable_alpha_bands(a2)
+    d2 = central_rhs(f2, coefs, h, -1)
+    x2 = solve_cyclic(bands, d2, -1)
+    lam2 = solve_cyclic(transpose_bands(bands), g2, -1)
+    gf2 = central_rhs_transpose(lam2, coefs, h, -1)
+    ga2 = -lam2 * (np.roll(x2, 1, axis=-1) + np.roll(x2, -1, axis=-1))
+    return (_unlines(gf2, shape, axis), _unlines(ga2, shape, axis),
+            _unlines(lam2, shape, axis), _unlines(x2, shape, axis))
+
+
+# ---------------------------------------------------------------- interface system
+def partition_bounds(n, p):
+    """Partition starts/sizes: the first n mod p partitions get ceil(n/p) rows."""
+    base, extra = divmod(n, p)
+    sizes = [base + (1 if i < extra else 0) for i in range(p)]
+    starts = np.cumsum([0] + sizes[:-1]).tolist()
+    return starts, sizes
+
+
+def reduced_system_dense(bands, p):
+    """Interface system A-hat of Sec. 3 as a dense Schur complement.
+
+    The interface unknowns are the first r rows of each partition (Fig. 3);
+    the permutation P moves every bulk block D_i first and every interface
+    block last (Fig. 4), and block Gaussian elimination leaves
+    A-hat = A_II - A_IB A_BB^{-1} A_BI as the trailing block.  Returns the
+    (p r) x (p r) matrix and the index lists (interface, bulk).
+    """
+    A = dense_matrix(bands)
+    n = A.shape[0]
+    r = (bands.shape[0] - 1) // 2
+    starts, sizes = partition_bounds(n, p)
+    iface = [s + q for s in starts for q in range(r)]
+    bulk = [j for j in range(n) if j not in set(iface)]
+    A_II = A[np.ix_(iface, iface)]
+    A_IB = A[np.ix_(iface, bulk)]
+    A_BI = A[np.ix_(bulk, iface)]
+    A_BB = A[np.ix_(bulk, bulk)]
+    Ahat = A_II - A_IB @ np.linalg.solve(A_BB, A_BI)
+    return Ahat, iface, bulk
+
+
+# ---------------------------------------------------------------- errors
+def rel_err(x, ref):
+    """Norm-wise infinity relative error ||x - ref||_inf / ||ref||_inf."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.max(np.abs(ref))
+    return float(np.max(np.abs(x - ref)) / (den if den > 0 else 1.0))

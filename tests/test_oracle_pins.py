@@ -1,0 +1,230 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+None of these compares the oracle with itself or with the GPU path:
+  * exact Taylor matching (Fractions) of the scheme coefficients;
+  * the closed-form modified wavenumber of Eq. 1 on single Fourier modes,
+    k'h = (a sin kh + (b/2) sin 2kh + (c/3) sin 3kh) / (1 + 2 alpha cos kh
+    + 2 beta cos 2kh), which pins the stencil (signs, indices, 1/(2qh)) and
+    the cyclic solve together;
+  * dense brute force (numpy LAPACK and the oracle's own pivoting LU) on
+    random cyclic banded systems;
+  * FFT diagonalisation of circulant systems (any n);
+  * the block-LU identity behind the interface system (Sec. 3, Fig. 4);
+  * finite differences and an explicit-inverse gradient for the adjoint.
+"""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_02286_gb300 import workloads as W
+
+
+# ---------------------------------------------------------------- scheme order
+def _taylor_order(alphas, coefs, kmax=14):
+    """Largest P such that the compact scheme
+         sum_t A_t f'(t) = sum_q c_q (f(q) - f(-q)) / (2q)      (h = 1)
+    is exact for every monomial f = x^k, k <= P (exact rational arithmetic)."""
+    A = {0: Fr(1)}
+    for q, a in enumerate(alphas, start=1):
+        A[q] = A[-q] = Fr(a)
+    order = -1
+    for k in range(0, kmax + 1):
+        lhs = sum(At * (k * Fr(t) ** (k - 1) if k >= 1 else 0) for t, At in A.items())
+        rhs = sum(Fr(c) * (Fr(q) ** k - Fr(-q) ** k) / (2 * q) for q, c in enumerate(coefs, start=1))
+        if lhs != rhs:
+            break
+        order = k
+    return order
+
+
+def test_scheme_coefficients_orders():
+    f = Fr
+    assert _taylor_order([f(1, 3)], [f(14, 9), f(1, 9)]) == 6
+    assert _taylor_order([f(1, 2), f(1, 20)], [f(17, 12), f(101, 150), f(1, 100)]) == 10
+    assert _taylor_order([], [f(4, 3), f(-1, 3)]) == 4
+    # the float constants used by the workloads are these rationals
+    assert W.LELE6_TRI["lhs"] == (1 / 3,) and W.LELE6_TRI["rhs"] == (14 / 9, 1 / 9)
+    assert W.PENTA10["lhs"] == (1 / 2, 1 / 20) and W.PENTA10["rhs"] == (17 / 12, 101 / 150, 1 / 100)
+    # a perturbed coefficient loses the order (the check is not vacuous)
+    assert _taylor_order([f(1, 3)], [f(14, 9), f(1, 10)]) < 6
+
+
+# ---------------------------------------------------------------- modified wavenumber
+def modified_wavenumber(k, n, lhs, rhs):
+    """k' for integer wavenumber k on n points, h = 2 pi / n (derived from Eq. 1)."""
+    th = 2 * np.pi * k / n
+    num = sum((c / q) * np.sin(q * th) for q, c in enumerate(rhs, start=1))
+    den = 1.0 + sum(2 * a * np.cos(q * th) for q, a in enumerate(lhs, start=1))
+    return num / den / (2 * np.pi / n)
+
+
+@pytest.mark.parametrize("scheme", [W.LELE6_TRI, W.PENTA10, {"lhs": (), "rhs": W.CENTRAL4["rhs"]}])
+@pytest.mark.parametrize("axis_dir", [0, 1, 2])
+def test_closed_form_fourier_cube(scheme, axis_dir):
+    # config "64^3, sum of 8 seeded modes": exact answer by linearity
+    f, modes = W.fourier_cube(64, 8)
+    n = 64
+    h = W.grid_spacing(n)
+    axis = 2 - axis_dir  # array order (z, y, x)
+    lhs = scheme["lhs"]
+    got = (oracle.derivative(f, lhs, scheme["rhs"], h, axis=axis) if lhs
+           else oracle.central_rhs(f, scheme["rhs"], h, axis=axis))
+    x = np.arange(n) * h
+    want = np.zeros_like(f)
+    for (kx, ky, kz), a in zip(modes.k, modes.amp):
+        kd = (kx, ky, kz)[axis_dir]
+        phase = kx * x[None, None, :] + ky * x[None, :, None] + kz * x[:, None, None]
+        want += a * modified_wavenumber(kd, n, lhs, scheme["rhs"]) * np.cos(phase)
+    assert oracle.rel_err(got, want) < 1e-13
+
+
+def test_closed_form_detects_wrong_sign():
+    # planting a sign error in the stencil (oracle input side) breaks the pin
+    f, modes = W.fourier_cube(64, 8)
+    h = W.grid_spacing(64)
+    good = oracle.derivative(f, (1 / 3,), (14 / 9, 1 / 9), h, axis=2)
+    bad = oracle.derivative(f, (1 / 3,), (14 / 9, -1 / 9), h, axis=2)
+    assert oracle.rel_err(bad, good) > 1e-3
+
+
+# ---------------------------------------------------------------- brute force
+def _random_bands(rng, n, r):
+    b = rng.uniform(-1.0, 1.0, size=(2 * r + 1, n))
+    b[r] = 2.0 * r + 1.0 + rng.uniform(0.5, 1.5, size=n)  # diagonally dominant
+    return b
+
+
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("n", [8, 9, 13, 16, 31, 64])
+def test_cyclic_solve_vs_dense(r, n):
+    rng = np.random.default_rng(100 + 7 * n + r)
+    bands = _random_bands(rng, n, r)
+    d = rng.standard_normal(n)
+    A = oracle.dense_matrix(bands)
+    ref = np.linalg.solve(A, d)
+    ref2 = oracle.dense_solve(A, d)
+    assert oracle.rel_err(ref2, ref) < 1e-13
+    for method in (["sm", "woodbury"] if r == 1 else ["woodbury"]):
+        x = oracle.solve_cyclic(bands, d[None, :], method=method)[0]
+        assert oracle.rel_err(x, ref) < 1e-12, method
+
+
+def test_dense_matrix_layout():
+    # bands[k, i] = A[i, (i + k - r) mod n]: check the corners explicitly
+    n, r = 6, 2
+    b = np.arange(5 * n, dtype=float).reshape(5, n) + 1
+    A = oracle.dense_matrix(b)
+    assert A[0, n - 2] == b[0, 0] and A[0, n - 1] == b[1, 0] and A[0, 0] == b[2, 0]
+    assert A[n - 1, 0] == b[3, n - 1] and A[n - 1, 1] == b[4, n - 1]
+
+
+def test_per_line_bands_batch():
+    rng = np.random.default_rng(5)
+    n, lines = 20, 7
+    bands = np.stack([_random_bands(rng, n, 1) for _ in range(lines)])
+    d = rng.standard_normal((lines, n))
+    x = oracle.solve_cyclic(bands, d)
+    for l in range(lines):
+        assert oracle.rel_err(x[l], np.linalg.solve(oracle.dense_matrix(bands[l]), d[l])) < 1e-12
+
+
+@pytest.mark.parametrize("lhs", [(1 / 3,), (1 / 2, 1 / 20), (0.45,)])
+@pytest.mark.parametrize("n", [512, 1000, 4096])
+def test_circulant_fft(lhs, n):
+    rng = np.random.default_rng(n)
+    d = rng.standard_normal((3, n))
+    bands = oracle.toeplitz_bands(n, lhs)
+    x = oracle.solve_cyclic(bands, d)
+    col = np.zeros(n)
+    col[0] = 1.0
+    for q, a in enumerate(lhs, start=1):
+        col[q] = col[-q] = a
+    ref = np.real(np.fft.ifft(np.fft.fft(d, axis=-1) / np.fft.fft(col), axis=-1))
+    assert oracle.rel_err(x, ref) < 1e-13
+    res = oracle.matvec(bands, x) - d
+    assert np.max(np.abs(res)) < 1e-13 * np.max(np.abs(d))
+
+
+def test_special_cases():
+    rng = np.random.default_rng(9)
+    d = rng.standard_normal((4, 32))
+    # alpha = 0: identity
+    assert np.array_equal(oracle.solve_cyclic(oracle.toeplitz_bands(32, (0.0,)), d), d)
+    # constant field has zero derivative
+    f = np.full((2, 64), 3.25)
+    assert np.max(np.abs(oracle.derivative(f, (1 / 3,), (14 / 9, 1 / 9), 0.1))) == 0.0
+
+
+# ---------------------------------------------------------------- block-LU identity (Sec. 3)
+@pytest.mark.parametrize("r,n,p", [(1, 24, 4), (1, 23, 5), (1, 12, 1), (1, 12, 2), (2, 40, 5), (2, 33, 3)])
+def test_schur_complement_identity(r, n, p):
+    rng = np.random.default_rng(n * 10 + p)
+    bands = _random_bands(rng, n, r)
+    b = rng.standard_normal(n)
+    Ahat, iface, bulk = oracle.reduced_system_dense(bands, p)
+    A = oracle.dense_matrix(bands)
+    x = np.linalg.solve(A, b)
+    A_IB = A[np.ix_(iface, bulk)]
+    A_BB = A[np.ix_(bulk, bulk)]
+    bhat = b[iface] - A_IB @ np.linalg.solve(A_BB, b[bulk])
+    assert np.allclose(np.linalg.solve(Ahat, bhat), x[iface], rtol=0, atol=1e-12)
+    assert Ahat.shape == (p * r, p * r)
+
+
+# ---------------------------------------------------------------- adjoint
+def test_transpose_bands_is_dense_transpose():
+    rng = np.random.default_rng(3)
+    for r in (1, 2):
+        b = _random_bands(rng, 11, r)
+        assert np.allclose(oracle.dense_matrix(oracle.transpose_bands(b)), oracle.dense_matrix(b).T)
+
+
+def test_stencil_transpose_is_dense_transpose():
+    n, coefs, h = 12, (14 / 9, 1 / 9), 0.3
+    S = np.stack([oracle.central_rhs(np.eye(n)[j], coefs, h) for j in range(n)], axis=1)
+    ST = np.stack([oracle.central_rhs_transpose(np.eye(n)[j], coefs, h) for j in range(n)], axis=1)
+    assert np.allclose(ST, S.T, atol=1e-14)
+
+
+def test_adjoint_dense_inverse_n16():
+    rng = np.random.default_rng(4)
+    n, coefs, h = 16, W.CENTRAL4["rhs"], W.grid_spacing(16)
+    f = rng.uniform(-1, 1, n)
+    alpha = rng.uniform(0.2, 0.4, n)
+    g = rng.standard_normal(n)
+    gf, ga, lam, x = oracle.adjoint_variable_tri(f[None], alpha[None], g[None], coefs, h)
+    A = oracle.dense_matrix(oracle.variable_alpha_bands(alpha[None])[0])
+    S = np.stack([oracle.central_rhs(np.eye(n)[j], coefs, h) for j in range(n)], axis=1)
+    Ainv = np.linalg.inv(A)
+    x_ref = Ainv @ S @ f
+    lam_ref = Ainv.T @ g
+    assert oracle.rel_err(x[0], x_ref) < 1e-13
+    assert oracle.rel_err(lam[0], lam_ref) < 1e-13
+    assert oracle.rel_err(gf[0], S.T @ lam_ref) < 1e-13
+    # dL/dalpha_i = -lam_i (x_{i-1} + x_{i+1}) from dA/dalpha_i = e_i (e_{i-1} + e_{i+1})^T
+    ga_ref = np.array([-(lam_ref @ (np.outer(np.eye(n)[i], np.eye(n)[(i - 1) % n] + np.eye(n)[(i + 1) % n]) @ x_ref))
+                       for i in range(n)])
+    assert oracle.rel_err(ga[0], ga_ref) < 1e-13
+
+
+def test_adjoint_finite_differences():
+    rng = np.random.default_rng(44)
+    n, coefs, h = 32, W.CENTRAL4["rhs"], W.grid_spacing(32)
+    f = rng.uniform(-1, 1, (2, n))
+    alpha = rng.uniform(0.2, 0.4, (2, n))
+    g = rng.standard_normal((2, n))
+    gf, ga, _, _ = oracle.adjoint_variable_tri(f, alpha, g, coefs, h)
+
+    def loss(ff, aa):
+        return float(np.sum(g * oracle.derivative_variable_tri(ff, aa, coefs, h)))
+
+    eps = 1e-6
+    for (l, i) in [(0, 0), (1, 7), (0, 31)]:
+        e = np.zeros_like(f)
+        e[l, i] = eps
+        fd_f = (loss(f + e, alpha) - loss(f - e, alpha)) / (2 * eps)
+        fd_a = (loss(f, alpha + e) - loss(f, alpha - e)) / (2 * eps)
+        assert abs(fd_f - gf[l, i]) < 1e-7 * max(1.0, abs(gf[l, i]))
+        assert abs(fd_a - ga[l, i]) < 1e-7 * max(1.0, abs(ga[l, i]))
