@@ -1,0 +1,217 @@
+/*
+ * cbs.h -- C-ABI of the GB300 cyclic compact banded solver.
+ *
+ * The library solves many independent cyclic (periodic) compact banded linear
+ * systems A x = b, tridiagonal (bandwidth w = 3) or pentadiagonal (w = 5), one
+ * per grid line of a 3-D field, with the two-level partition method of Song et
+ * al., "Scalable Parallel Linear Solver for Compact Banded Systems on
+ * Heterogeneous Architectures" (arXiv 2101.02286):
+ *
+ *   - each line is split into p partitions (Sec. 3, Fig. 3); the first r =
+ *     (w-1)/2 rows of a partition are its interface unknowns, the rest its
+ *     bulk block D_i;
+ *   - y_i = D_i^{-1} b_i inside each partition (Eq. 17);
+ *   - the reduced cyclic block-tridiagonal interface system A-hat x~ = b-hat
+ *     (Eq. 11, 18-21) is solved by block PCR with detach/reattach
+ *     (Algorithms 1-4), always in FP64;
+ *   - back-substitution x_i = y_i - S_i x~_i - R_i x~_{i+1} (Eq. 22).
+ *
+ * Everything RHS-independent (S_i, R_i, the reduced blocks and the PCR
+ * coefficients of every stage) is pre-factorised once per plan (Sec. 4, last
+ * paragraph).  Optionally the right-hand side is produced in the same launch
+ * from a field f by the periodic central stencil of Eq. 1.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments named "device" are device pointers owned by the caller;
+ *     the library never frees or keeps them beyond the call (except
+ *     cbs_desc.bands, see below).  Host arrays are plain host pointers.
+ *   - A field has dims (nx, ny, nz) with x contiguous: element (i, j, k) is at
+ *     offset i + nx * (j + ny * k).  Lines run along `direction`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Launches are asynchronous; device-side errors are reported through
+ *     cbs_status_poll.
+ *   - Every call returns a cbs_status; no C++ exception crosses the ABI.
+ *     cbs_last_error_string() describes the last failure of the calling thread.
+ *   - A plan may be used from several host threads, but concurrent launches on
+ *     one plan must be ordered by the caller's streams (the plan's device
+ *     status word is shared).
+ */
+#ifndef CBS_H
+#define CBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cbs_status;
+enum {
+    CBS_OK = 0,
+    CBS_ERR_INVALID_ARG = 1, /* a descriptor field or pointer is invalid      */
+    CBS_ERR_UNSUPPORTED = 2, /* valid request outside what is implemented     */
+    CBS_ERR_SINGULAR = 3,    /* zero / non-finite pivot or interface block    */
+    CBS_ERR_TIMEOUT = 4,     /* a bounded device wait expired                 */
+    CBS_ERR_CUDA = 5,        /* a CUDA runtime call failed                    */
+    CBS_ERR_NO_MEMORY = 6    /* host or device allocation failed              */
+};
+
+/* Arithmetic of the bulk solve.  The interface system is FP64 in all modes. */
+enum {
+    CBS_FP64 = 0,        /* everything in FP64                                    */
+    CBS_FP32 = 1,        /* bulk in FP32, no refinement (error ~ cond * 2^-24)    */
+    CBS_FP32_REFINE = 2  /* FP32 bulk + `refine_sweeps` iterative-refinement
+                            sweeps whose residual b - A x is evaluated to FP64
+                            accuracy; output FP64                                 */
+};
+
+/* Element type of the caller's arrays. */
+enum { CBS_DTYPE_F64 = 0, CBS_DTYPE_F32 = 1 };
+
+/* Left-hand side. */
+enum {
+    CBS_LHS_TOEPLITZ = 0,    /* constant bands: (beta,) alpha, 1, alpha (, beta)      */
+    CBS_LHS_VARIABLE = 1     /* tridiagonal, row-wise alpha_i read from cbs_desc.bands:
+                                A[i,i-1] = A[i,i+1] = alpha_i, A[i,i] = 1            */
+};
+
+/* Right-hand side. */
+enum {
+    CBS_RHS_NONE = 0,        /* the input array already holds b                       */
+    CBS_RHS_CENTRAL = 1      /* b_i = sum_k c_k (f_{i+k} - f_{i-k}) / (2 k h), Eq. 1 */
+};
+
+typedef struct cbs_desc {
+    /* geometry */
+    int64_t dims[3];        /* nx, ny, nz (>= 1); x contiguous                     */
+    int32_t direction;      /* 0 = x, 1 = y, 2 = z: the solve axis; n = dims[dir]  */
+    /* matrix */
+    int32_t bandwidth;      /* 3 or 5                                              */
+    int32_t cyclic;         /* 1 = periodic; 0 = acyclic (corner blocks zero)      */
+    int32_t lhs_kind;       /* CBS_LHS_*                                            */
+    double  alpha, beta;    /* Toeplitz bands (beta ignored for bandwidth 3)       */
+    const void* bands;      /* CBS_LHS_VARIABLE: device array of alpha_i, same dims
+                               and dtype as the input; read at every solve (the
+                               caller keeps it alive and may change its values)    */
+    /* right-hand side */
+    int32_t rhs_kind;       /* CBS_RHS_*                                            */
+    int32_t rhs_terms;      /* K = 1..3 stencil terms (CBS_RHS_CENTRAL)            */
+    double  rhs_coef[3];    /* c_1..c_K (Lele's a, b, c)                           */
+    double  h;              /* grid spacing (> 0)                                  */
+    /* solver */
+    int32_t segments;       /* p partitions per line; 0 = choose automatically     */
+    int32_t precision;      /* CBS_FP64 / CBS_FP32 / CBS_FP32_REFINE               */
+    int32_t refine_sweeps;  /* CBS_FP32_REFINE: 1 or 2                              */
+    int32_t in_dtype;       /* CBS_DTYPE_* of the input (f or b)                   */
+    int32_t out_dtype;      /* CBS_DTYPE_* of the output x (F64 for FP32_REFINE)   */
+} cbs_desc;
+
+typedef struct cbs_plan cbs_plan;
+typedef struct cbs_batch cbs_batch;
+
+/* Plan introspection: what the plan chose, and the interface schedule. */
+typedef struct cbs_plan_info {
+    int32_t n, bandwidth, segments;
+    int32_t rows_big, rows_small, count_big; /* partition sizes (first count_big get rows_big) */
+    int32_t pcr_steps;        /* block-PCR steps on the interface system            */
+    int32_t detach_steps;     /* detach rounds (= reattach rounds)                  */
+    int32_t detached_rows;    /* rows detached over the whole solve                 */
+    int32_t stage_count;      /* stages the device executes on x~ per solve         */
+    int32_t kernel;           /* implementation id (0 = on-chip lines, 1 = long lines) */
+    int32_t threads_per_line;
+    int64_t lines;            /* independent systems in one solve                   */
+} cbs_plan_info;
+
+/* Create a plan: validates the descriptor, chooses p when segments == 0,
+ * pre-factorises everything RHS-independent in FP64 on the host (Sec. 4) and
+ * uploads the tables to the current device.  Allocates device memory.
+ * Errors: INVALID_ARG (n < 2 r p, bad enum, ...), UNSUPPORTED, SINGULAR (a
+ * zero or non-finite pivot in D_i or an interface block), CUDA, NO_MEMORY. */
+cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* desc);
+
+/* Rebind the alpha field of a CBS_LHS_VARIABLE plan (device pointer, same
+ * dims and dtype as the plan's input; the caller keeps it alive).  Takes
+ * effect for launches issued after the call.  INVALID_ARG for Toeplitz
+ * plans or NULL. */
+cbs_status cbs_plan_set_bands(cbs_plan* plan, const void* bands);
+
+/* Destroy a plan and free its device memory (synchronises the device). */
+cbs_status cbs_plan_destroy(cbs_plan* plan);
+
+/* x = A^{-1} b along every line, with b = S f when the plan has a stencil.
+ * in: device, in_dtype, the field f (or b); out: device, out_dtype, same dims.
+ * `out` must not alias `in`.  Asynchronous on `stream`. */
+cbs_status cbs_solve(cbs_plan* plan, const void* in, void* out, void* stream);
+
+/* Adjoint of cbs_solve (Sec. 3 operators transposed):
+ *   lambda = A^{-T} g, and, when the plan has a stencil, grad_in = S^T lambda.
+ * Any of lambda / grad_in may be NULL (not written).  For CBS_LHS_VARIABLE,
+ * when x and grad_bands are both non-NULL, also writes the band gradient
+ * grad_bands_i = -lambda_i (x_{i-1} + x_{i+1}) (same as cbs_band_grad).
+ * g, x, lambda, grad_in, grad_bands: device, the plan's dims; g and x of
+ * out_dtype, lambda / grad_in / grad_bands of in_dtype. */
+cbs_status cbs_solve_transpose(cbs_plan* plan, const void* g, const void* x,
+                               void* lambda, void* grad_in, void* grad_bands,
+                               void* stream);
+
+/* grad_bands_i = -lambda_i (x_{i-1} + x_{i+1}) along the plan's lines
+ * (periodic), the gradient of <g, x> with respect to row-wise alpha_i when
+ * lambda = A^{-T} g.  Device arrays of the plan's dims, in_dtype. */
+cbs_status cbs_band_grad(cbs_plan* plan, const void* lambda, const void* x,
+                         void* grad_bands, void* stream);
+
+/* Read (and clear) the plan's device status word: CBS_OK, CBS_ERR_SINGULAR or
+ * CBS_ERR_TIMEOUT from kernels that already ran.  Synchronises the device. */
+cbs_status cbs_status_poll(cbs_plan* plan, int32_t* device_status);
+
+/* Fill *info with the plan's choices and interface schedule counts. */
+cbs_status cbs_plan_info_get(const cbs_plan* plan, cbs_plan_info* info);
+
+/* Interface schedule of Algorithm 1 for p partitions (host only, no device):
+ * writes up to `cap` stages as triples (type, s, n_a) into `stages`
+ * (type 0 = detach, 1 = PCR step, 2 = final block solve, 3 = reattach) and
+ * their count into *count.  cyclic selects the cyclic (floor(log2 p) PCR
+ * steps) or acyclic (ceil(log2 p)) variant (Sec. 4). */
+cbs_status cbs_schedule(int32_t p, int32_t cyclic, int32_t* stages, int32_t cap,
+                        int32_t* count);
+
+/* Host-only model of a plan's interface system (no device work, no GPU
+ * needed): builds the tables cbs_plan_create would build for `desc` with
+ * p partitions (desc->segments is ignored) and
+ *   - writes the reduced blocks D-hat_i, L-hat_i, U-hat_i of Eq. 18-20
+ *     (r x r row-major, partition-major, p*r*r doubles each) when non-NULL;
+ *   - when bhat and xt are non-NULL, applies the pre-factorised stage
+ *     coefficients (Algorithms 2-4) to b-hat (p*r doubles) and writes
+ *     x~ = A-hat^{-1} b-hat to xt, exactly as the device kernels do.
+ * Toeplitz LHS only.  Errors: INVALID_ARG, UNSUPPORTED, SINGULAR. */
+cbs_status cbs_interface_model(const cbs_desc* desc, int32_t p, double* dhat, double* lhat,
+                               double* uhat, const double* bhat, double* xt);
+
+/* Ragged batch: up to `count` independent problems (each its own cbs_desc,
+ * in and out arrays) solved by one persistent launch per call.  The batch
+ * pre-builds every problem's plan tables and a work table of line tiles.
+ * Allocates device memory at creation, none per solve. */
+cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t count);
+cbs_status cbs_batch_destroy(cbs_batch* batch);
+/* ins[k] / outs[k]: device arrays of problem k (host array of `count`
+ * pointers).  No allocation and no host synchronisation: capturable in a CUDA
+ * graph when the pointers are fixed. */
+cbs_status cbs_batch_solve(cbs_batch* batch, const void* const* ins,
+                           void* const* outs, void* stream);
+cbs_status cbs_batch_status_poll(cbs_batch* batch, int32_t* device_status);
+
+/* Number of kernel launches the last cbs_solve / cbs_batch_solve of this
+ * thread issued (for launch accounting). */
+int32_t cbs_last_launch_count(void);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* cbs_last_error_string(void);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t cbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBS_H */

@@ -1,0 +1,210 @@
+"""ctypes binding of the C-ABI in include/cbs.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Pointers are
+plain integers (device addresses from torch tensors, or host addresses);
+every non-zero status raises CbsError with the library's message.  There is
+no fallback: if libcbs.so is missing or fails to load, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcbs.so")
+
+# status codes (cbs.h)
+CBS_OK, CBS_ERR_INVALID_ARG, CBS_ERR_UNSUPPORTED, CBS_ERR_SINGULAR, CBS_ERR_TIMEOUT, CBS_ERR_CUDA, \
+    CBS_ERR_NO_MEMORY = range(7)
+CBS_FP64, CBS_FP32, CBS_FP32_REFINE = 0, 1, 2
+CBS_DTYPE_F64, CBS_DTYPE_F32 = 0, 1
+CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE = 0, 1
+CBS_RHS_NONE, CBS_RHS_CENTRAL = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA",
+                6: "NO_MEMORY"}
+
+# every entry point declared in include/cbs.h
+EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transpose", "cbs_band_grad",
+           "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
+           "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
+           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands")
+
+
+class CbsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class cbs_desc(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int64 * 3),
+        ("direction", ctypes.c_int32),
+        ("bandwidth", ctypes.c_int32),
+        ("cyclic", ctypes.c_int32),
+        ("lhs_kind", ctypes.c_int32),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("bands", ctypes.c_void_p),
+        ("rhs_kind", ctypes.c_int32),
+        ("rhs_terms", ctypes.c_int32),
+        ("rhs_coef", ctypes.c_double * 3),
+        ("h", ctypes.c_double),
+        ("segments", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("refine_sweeps", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int32),
+        ("out_dtype", ctypes.c_int32),
+    ]
+
+
+class cbs_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("bandwidth", ctypes.c_int32), ("segments", ctypes.c_int32),
+        ("rows_big", ctypes.c_int32), ("rows_small", ctypes.c_int32), ("count_big", ctypes.c_int32),
+        ("pcr_steps", ctypes.c_int32), ("detach_steps", ctypes.c_int32), ("detached_rows", ctypes.c_int32),
+        ("stage_count", ctypes.c_int32), ("kernel", ctypes.c_int32), ("threads_per_line", ctypes.c_int32),
+        ("lines", ctypes.c_int64),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libcbs.so is not built (run __graft_entry__.build() or "
+                          "python paper_2101_02286_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "cbs_plan_create": ([P(vp), P(cbs_desc)], st),
+        "cbs_plan_destroy": ([vp], st),
+        "cbs_solve": ([vp, vp, vp, vp], st),
+        "cbs_solve_transpose": ([vp, vp, vp, vp, vp, vp, vp], st),
+        "cbs_band_grad": ([vp, vp, vp, vp, vp], st),
+        "cbs_status_poll": ([vp, P(i32)], st),
+        "cbs_plan_info_get": ([vp, P(cbs_plan_info)], st),
+        "cbs_schedule": ([i32, i32, P(i32), i32, P(i32)], st),
+        "cbs_batch_create": ([P(vp), P(cbs_desc), i32], st),
+        "cbs_batch_destroy": ([vp], st),
+        "cbs_batch_solve": ([vp, P(vp), P(vp), vp], st),
+        "cbs_batch_status_poll": ([vp, P(i32)], st),
+        "cbs_last_launch_count": ([], i32),
+        "cbs_last_error_string": ([], ctypes.c_char_p),
+        "cbs_version": ([], i32),
+        "cbs_interface_model": ([P(cbs_desc), i32, vp, vp, vp, vp, vp], st),
+        "cbs_plan_set_bands": ([vp, vp], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int):
+    if status != CBS_OK:
+        raise CbsError(status, _lib.cbs_last_error_string().decode())
+
+
+def cbs_plan_create(desc: cbs_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.cbs_plan_create(ctypes.byref(h), ctypes.byref(desc)))
+    return h.value
+
+
+def cbs_plan_destroy(plan: int) -> None:
+    _check(_lib.cbs_plan_destroy(plan))
+
+
+def cbs_plan_set_bands(plan: int, bands: int) -> None:
+    _check(_lib.cbs_plan_set_bands(plan, bands))
+
+
+def cbs_solve(plan: int, inp: int, out: int, stream: int = 0) -> None:
+    _check(_lib.cbs_solve(plan, inp, out, stream))
+
+
+def cbs_solve_transpose(plan: int, g: int, x: int | None, lam: int | None, grad_in: int | None,
+                        grad_bands: int | None, stream: int = 0) -> None:
+    _check(_lib.cbs_solve_transpose(plan, g, x, lam, grad_in, grad_bands, stream))
+
+
+def cbs_band_grad(plan: int, lam: int, x: int, grad_bands: int, stream: int = 0) -> None:
+    _check(_lib.cbs_band_grad(plan, lam, x, grad_bands, stream))
+
+
+def cbs_status_poll(plan: int) -> int:
+    v = ctypes.c_int32()
+    _check(_lib.cbs_status_poll(plan, ctypes.byref(v)))
+    return v.value
+
+
+def cbs_plan_info_get(plan: int) -> dict:
+    info = cbs_plan_info()
+    _check(_lib.cbs_plan_info_get(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in cbs_plan_info._fields_}
+
+
+def cbs_schedule(p: int, cyclic: bool = True) -> list[tuple[int, int, int]]:
+    count = ctypes.c_int32()
+    _check(_lib.cbs_schedule(p, int(cyclic), None, 0, ctypes.byref(count)))
+    buf = (ctypes.c_int32 * (3 * max(count.value, 1)))()
+    _check(_lib.cbs_schedule(p, int(cyclic), buf, count.value, ctypes.byref(count)))
+    return [(buf[3 * k], buf[3 * k + 1], buf[3 * k + 2]) for k in range(count.value)]
+
+
+def cbs_interface_model(desc: cbs_desc, p: int, bhat=None):
+    """Host-only: (Dhat, Lhat, Uhat) blocks of Eq. 18-20 as numpy (p, r, r)
+    arrays, and x~ = A-hat^{-1} b-hat via the plan's stage coefficients when
+    bhat (p*r values) is given."""
+    import numpy as np
+    r = (desc.bandwidth - 1) // 2
+    D = np.zeros((p, r, r))
+    L = np.zeros((p, r, r))
+    U = np.zeros((p, r, r))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    xt = None
+    if bhat is not None:
+        b = np.ascontiguousarray(bhat, dtype=np.float64).reshape(p * r)
+        xt = np.zeros(p * r)
+        _check(_lib.cbs_interface_model(ctypes.byref(desc), p, ptr(D), ptr(L), ptr(U), ptr(b), ptr(xt)))
+    else:
+        _check(_lib.cbs_interface_model(ctypes.byref(desc), p, ptr(D), ptr(L), ptr(U), None, None))
+    return D, L, U, xt
+
+
+def cbs_batch_create(descs: list[cbs_desc]) -> int:
+    arr = (cbs_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(_lib.cbs_batch_create(ctypes.byref(h), arr, len(descs)))
+    return h.value
+
+
+def cbs_batch_destroy(batch: int) -> None:
+    _check(_lib.cbs_batch_destroy(batch))
+
+
+def cbs_batch_solve(batch: int, ins: list[int], outs: list[int], stream: int = 0) -> None:
+    n = len(ins)
+    a = (ctypes.c_void_p * n)(*ins)
+    b = (ctypes.c_void_p * n)(*outs)
+    _check(_lib.cbs_batch_solve(batch, a, b, stream))
+
+
+def cbs_batch_status_poll(batch: int) -> int:
+    v = ctypes.c_int32()
+    _check(_lib.cbs_batch_status_poll(batch, ctypes.byref(v)))
+    return v.value
+
+
+def cbs_last_launch_count() -> int:
+    return int(_lib.cbs_last_launch_count())
+
+
+def cbs_version() -> int:
+    return int(_lib.cbs_version())

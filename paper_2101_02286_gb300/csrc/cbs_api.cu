@@ -1,0 +1,674 @@
+// cbs_api.cu -- the C-ABI: plan creation (validation, partition choice,
+// host pre-factorisation, upload) and the solve entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "cbs_line_launch.cuh"
+#include "cbs_var.cuh"
+
+using namespace cbs;
+
+namespace cbs {
+template <> cudaError_t launch_line_mode_r<0, 1>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
+template <> cudaError_t launch_line_mode_r<0, 2>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
+template <> cudaError_t launch_line_mode_r<1, 1>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
+template <> cudaError_t launch_line_mode_r<1, 2>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
+template <> cudaError_t launch_line_mode_r<2, 1>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
+template <> cudaError_t launch_line_mode_r<2, 2>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
+cudaError_t launch_var(int M, int KS, bool adj, bool f64, const VarArgs& a, const DevLineTables& t,
+                       cudaStream_t s);
+cudaError_t launch_band_grad(bool f64, const void* lam, const void* x, void* ga, int64_t nx, int64_t ny,
+                             int64_t nz, int dir, cudaStream_t s);
+struct BatchProblem;
+int batch_variant_host(int R, int KS, int M, int MODE);
+cudaError_t batch_configure(size_t smem);
+cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitems, const void* const* ins,
+                         void* const* outs, int count, int grid, size_t smem, cudaStream_t s);
+size_t batch_problem_bytes();
+void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant);
+constexpr int kBatchMax = 256;
+}  // namespace cbs
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int g_launches = 0;
+
+cbs_status fail(cbs_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+cbs_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return CBS_ERR_CUDA;
+}
+
+int next_pow2(int p) {
+  int w = 1;
+  while (w < p) w *= 2;
+  return w;
+}
+
+}  // namespace
+
+struct cbs_batch {
+  std::vector<cbs_plan*> plans;
+  void* dprobs = nullptr;
+  void* ditems = nullptr;
+  int nitems = 0, count = 0, grid = 1;
+  size_t smem = 0;
+  int64_t unknowns = 0;
+};
+
+struct cbs_plan {
+  cbs_desc desc;
+  int n = 0, r = 1, kind = 0, M = 16, ks = 0;
+  int64_t nlines = 0;
+  LineTables host;
+  DevLineTables dev;
+  void* dbuf = nullptr;
+  int* dstatus = nullptr;
+  LineArgs args;
+  bool var = false;
+  VarArgs vargs;
+};
+
+namespace {
+
+cbs_status validate(const cbs_desc* d) {
+  if (!d) return fail(CBS_ERR_INVALID_ARG, "null descriptor");
+  for (int k = 0; k < 3; k++)
+    if (d->dims[k] < 1) return fail(CBS_ERR_INVALID_ARG, "dims must be >= 1");
+  if (d->direction < 0 || d->direction > 2) return fail(CBS_ERR_INVALID_ARG, "direction must be 0, 1 or 2");
+  if (d->bandwidth != 3 && d->bandwidth != 5) return fail(CBS_ERR_INVALID_ARG, "bandwidth must be 3 or 5");
+  if (d->cyclic != 0 && d->cyclic != 1) return fail(CBS_ERR_INVALID_ARG, "cyclic must be 0 or 1");
+  if (d->lhs_kind != CBS_LHS_TOEPLITZ && d->lhs_kind != CBS_LHS_VARIABLE)
+    return fail(CBS_ERR_INVALID_ARG, "bad lhs_kind");
+  if (d->rhs_kind != CBS_RHS_NONE && d->rhs_kind != CBS_RHS_CENTRAL) return fail(CBS_ERR_INVALID_ARG, "bad rhs_kind");
+  if (d->rhs_kind == CBS_RHS_CENTRAL) {
+    if (d->rhs_terms < 1 || d->rhs_terms > 3) return fail(CBS_ERR_INVALID_ARG, "rhs_terms must be 1..3");
+    if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(CBS_ERR_INVALID_ARG, "h must be positive");
+    if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the central stencil is periodic: needs cyclic = 1");
+  }
+  if (d->precision < CBS_FP64 || d->precision > CBS_FP32_REFINE) return fail(CBS_ERR_INVALID_ARG, "bad precision");
+  if (d->precision == CBS_FP32_REFINE && (d->refine_sweeps < 1 || d->refine_sweeps > 2))
+    return fail(CBS_ERR_INVALID_ARG, "refine_sweeps must be 1 or 2");
+  if (d->in_dtype != CBS_DTYPE_F64 && d->in_dtype != CBS_DTYPE_F32) return fail(CBS_ERR_INVALID_ARG, "bad in_dtype");
+  if (d->out_dtype != CBS_DTYPE_F64 && d->out_dtype != CBS_DTYPE_F32) return fail(CBS_ERR_INVALID_ARG, "bad out_dtype");
+  if (d->precision != CBS_FP32 && d->out_dtype != CBS_DTYPE_F64)
+    return fail(CBS_ERR_INVALID_ARG, "FP64 and FP32_REFINE write FP64 output");
+  if (!std::isfinite(d->alpha) || !std::isfinite(d->beta)) return fail(CBS_ERR_INVALID_ARG, "non-finite bands");
+  if (d->segments < 0) return fail(CBS_ERR_INVALID_ARG, "segments must be >= 0");
+  if ((d->direction == 1 && d->dims[2] > 65535) || (d->direction == 2 && d->dims[1] > 65535))
+    return fail(CBS_ERR_UNSUPPORTED, "y/z lines: the remaining grid extent must be <= 65535");
+  if (d->dims[0] * d->dims[1] * d->dims[2] >= (int64_t)1 << 40) return fail(CBS_ERR_UNSUPPORTED, "field too large");
+  if (d->lhs_kind == CBS_LHS_VARIABLE) {
+    if (d->bandwidth != 3) return fail(CBS_ERR_UNSUPPORTED, "variable bands: tridiagonal only");
+    if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "variable bands: cyclic only");
+    if (!d->bands) return fail(CBS_ERR_INVALID_ARG, "variable bands need the alpha field pointer");
+    if (d->precision == CBS_FP32_REFINE) return fail(CBS_ERR_UNSUPPORTED, "variable bands: FP64 or FP32");
+    const int want = d->precision == CBS_FP64 ? CBS_DTYPE_F64 : CBS_DTYPE_F32;
+    if (d->in_dtype != want || d->out_dtype != want)
+      return fail(CBS_ERR_INVALID_ARG, "variable bands: input, output and alpha share the precision's dtype");
+  }
+  return CBS_OK;
+}
+
+// Default partition count for the on-chip kernel: the fewest partitions
+// (<= 32 lanes) whose size fits the register budget of the mode.
+int default_segments(int n, int r, int precision) {
+  const int target = (precision == CBS_FP32_REFINE) ? 16 : 16;
+  for (int p = 1; p <= kMaxLanes; p *= 2)
+    if ((n + p - 1) / p <= target && n / p >= 2 * r) return p;
+  for (int p = kMaxLanes; p >= 1; p /= 2)
+    if (n / p >= 2 * r && (n + p - 1) / p <= 32) return p;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cbs_last_error_string(void) { return g_err.c_str(); }
+int32_t cbs_version(void) { return 100; }
+int32_t cbs_last_launch_count(void) { return g_launches; }
+
+cbs_status cbs_schedule(int32_t p, int32_t cyclic, int32_t* stages, int32_t cap, int32_t* count) {
+  if (p < 1 || !count || (cap > 0 && !stages)) return fail(CBS_ERR_INVALID_ARG, "bad schedule arguments");
+  std::vector<Stage> st = build_schedule(p, cyclic != 0);
+  *count = (int32_t)st.size();
+  for (int k = 0; k < (int)st.size() && k < cap; k++) {
+    stages[3 * k + 0] = st[k].type;
+    stages[3 * k + 1] = st[k].s;
+    stages[3 * k + 2] = st[k].na;
+  }
+  return CBS_OK;
+}
+
+cbs_status cbs_interface_model(const cbs_desc* d, int32_t p, double* dhat, double* lhat, double* uhat,
+                               const double* bhat, double* xt) {
+  cbs_status st = validate(d);
+  if (st) return st;
+  if (d->lhs_kind != CBS_LHS_TOEPLITZ) return fail(CBS_ERR_UNSUPPORTED, "Toeplitz LHS only");
+  const int r = (d->bandwidth - 1) / 2, n = (int)d->dims[d->direction];
+  if (p < 1 || n < 2 * r * p) return fail(CBS_ERR_INVALID_ARG, "need 1 <= p and n >= 2 r p");
+  Bands A;
+  A.r = r;
+  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
+  A.v[r] = 1.0;
+  A.v[r - 1] = A.v[r + 1] = d->alpha;
+  if (r == 2) A.v[0] = A.v[4] = d->beta;
+  LineTables T;
+  bool singular = false;
+  std::string msg = build_line_tables(T, n, A, p, d->cyclic != 0, &singular, /*max_lanes=*/1 << 30);
+  if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
+  const size_t nb = (size_t)p * r * r;
+  if (dhat) std::memcpy(dhat, T.Dhat.data(), nb * sizeof(double));
+  if (lhat) std::memcpy(lhat, T.Lhat.data(), nb * sizeof(double));
+  if (uhat) std::memcpy(uhat, T.Uhat.data(), nb * sizeof(double));
+  if (bhat && xt) {
+    std::vector<double> x(bhat, bhat + (size_t)p * r), y((size_t)p * r);
+    const int rr = r * r;
+    for (int s = 0; s < (int)T.stages.size(); s++) {
+      for (int i = 0; i < p; i++) {
+        const int sm = T.src[(size_t)(s * 2 + 0) * p + i], sp = T.src[(size_t)(s * 2 + 1) * p + i];
+        for (int q = 0; q < r; q++) {
+          double acc = 0.0;
+          for (int e = 0; e < r; e++) {
+            const double C = T.coef[((size_t)(s * 3 + 0) * rr + q * r + e) * p + i];
+            const double KM = T.coef[((size_t)(s * 3 + 1) * rr + q * r + e) * p + i];
+            const double KP = T.coef[((size_t)(s * 3 + 2) * rr + q * r + e) * p + i];
+            acc += C * x[(size_t)i * r + e] - KM * x[(size_t)sm * r + e] - KP * x[(size_t)sp * r + e];
+          }
+          y[(size_t)i * r + q] = acc;
+        }
+      }
+      x.swap(y);
+    }
+    std::memcpy(xt, x.data(), (size_t)p * r * sizeof(double));
+  }
+  return CBS_OK;
+}
+
+cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
+  if (!out) return fail(CBS_ERR_INVALID_ARG, "null plan pointer");
+  *out = nullptr;
+  cbs_status st = validate(d);
+  if (st) return st;
+  cbs_plan* P = new (std::nothrow) cbs_plan();
+  if (!P) return fail(CBS_ERR_NO_MEMORY, "host allocation failed");
+  P->desc = *d;
+  P->r = (d->bandwidth - 1) / 2;
+  P->n = (int)d->dims[d->direction];
+  if ((int64_t)P->n != d->dims[d->direction]) {
+    delete P;
+    return fail(CBS_ERR_INVALID_ARG, "line length too large");
+  }
+  P->nlines = d->dims[0] * d->dims[1] * d->dims[2] / P->n;
+  P->var = d->lhs_kind == CBS_LHS_VARIABLE;
+  int p = d->segments;
+  if (!p) {
+    if (P->var) {
+      // registers hold ~5 arrays of rows per lane: keep partitions <= 8 rows
+      p = 1;
+      while (p < kMaxLanes && (P->n + p - 1) / p > 8) p *= 2;
+      while (p > 1 && P->n / p < 2) p /= 2;
+    } else {
+      p = default_segments(P->n, P->r, d->precision);
+    }
+  }
+  if (p < 1) {
+    delete P;
+    return fail(CBS_ERR_UNSUPPORTED, "line too long for the on-chip kernel");
+  }
+  if (P->n < 2 * P->r * p) {
+    delete P;
+    return fail(CBS_ERR_INVALID_ARG, "need n >= 2 r p (every partition holds at least 2r rows)");
+  }
+  if (p > kMaxLanes) {
+    delete P;
+    return fail(CBS_ERR_UNSUPPORTED, "more than 32 partitions per line needs the long-line kernel");
+  }
+  Bands A;
+  A.r = P->r;
+  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
+  A.v[P->r] = 1.0;
+  A.v[P->r - 1] = A.v[P->r + 1] = P->var ? 0.25 : d->alpha;  // variable: geometry only
+  if (P->r == 2) A.v[0] = A.v[4] = d->beta;
+  bool singular = false;
+  std::string msg = build_line_tables(P->host, P->n, A, p, d->cyclic != 0, &singular, kMaxLanes);
+  if (!msg.empty()) {
+    delete P;
+    return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
+  }
+  const LineTables& T = P->host;
+  const int maxM = (d->precision == CBS_FP32_REFINE || P->var) ? 16 : 32;
+  int M = 8;
+  while (M < T.rows_big) M *= 2;
+  if (M > maxM || T.nmax > kMaxBulk) {
+    delete P;
+    return fail(CBS_ERR_UNSUPPORTED, "partitions too long for the on-chip kernel (raise segments)");
+  }
+  P->M = M;
+  P->ks = 0;
+  if (d->rhs_kind == CBS_RHS_CENTRAL) P->ks = d->rhs_terms <= 2 ? 2 : 3;
+
+  // ---- device tables ----
+  DevLineTables& D = P->dev;
+  std::memset(&D, 0, sizeof(D));
+  const int r = P->r, F = 2 * r + 1;
+  for (int j = 0; j < T.nmax; j++)
+    for (int c = 0; c < F; c++) {
+      D.fac[j * F + c] = T.fac[(size_t)j * F + c];
+      D.facF[j * F + c] = (float)T.fac[(size_t)j * F + c];
+    }
+  const int iB = 0, iS = (T.count_big < p) ? T.count_big : 0;
+  for (int j = 0; j < T.rows_big - r; j++)
+    for (int c = 0; c < 2 * r; c++) {
+      D.srB[j * 2 * r + c] = T.sr[((size_t)j * 2 * r + c) * p + iB];
+      D.srBF[j * 2 * r + c] = (float)D.srB[j * 2 * r + c];
+    }
+  for (int j = 0; j < T.rows_small - r; j++)
+    for (int c = 0; c < 2 * r; c++) {
+      D.srS[j * 2 * r + c] = T.sr[((size_t)j * 2 * r + c) * p + iS];
+      D.srSF[j * 2 * r + c] = (float)D.srS[j * 2 * r + c];
+    }
+  for (int q = 0; q < r; q++)
+    for (int e = 0; e < r; e++) {
+      D.Lt[q][e] = T.Lt[q][e];
+      D.Ut[q][e] = T.Ut[q][e];
+      D.LtF[q][e] = (float)T.Lt[q][e];
+      D.UtF[q][e] = (float)T.Ut[q][e];
+    }
+  // uniform interface: p a power of two, cyclic, only PCR / final stages and
+  // identical blocks on every lane (then sources are (i -+ s) mod p)
+  {
+    const int rr = r * r, ns = (int)T.stages.size();
+    bool uni = d->cyclic && (p & (p - 1)) == 0;
+    for (int st = 0; st < ns && uni; st++) {
+      const Stage& S_ = T.stages[st];
+      if (S_.type != kPcr && S_.type != kFinal) uni = false;
+      for (int i = 0; i < p && uni; i++) {
+        for (int m = 0; m < 3 * rr; m++)
+          if (T.coef[((size_t)st * 3 * rr + m) * p + i] != T.coef[((size_t)st * 3 * rr + m) * p]) uni = false;
+        if (S_.type == kPcr) {
+          if (T.src[(size_t)(st * 2 + 0) * p + i] != ((i - S_.s) & (p - 1)) ||
+              T.src[(size_t)(st * 2 + 1) * p + i] != ((i + S_.s) & (p - 1)))
+            uni = false;
+        }
+      }
+    }
+    D.uniform = uni ? 1 : 0;
+    if (uni)
+      for (int st = 0; st < ns; st++) {
+        D.ustage_s[st] = (T.stages[st].type == kPcr) ? T.stages[st].s : 0;
+        for (int m = 0; m < 3 * rr; m++) {
+          D.ucoef[st][m] = T.coef[((size_t)st * 3 * rr + m) * p];
+          D.ucoefF[st][m] = (float)D.ucoef[st][m];
+        }
+      }
+  }
+  for (int k = 0; k < F; k++) {
+    D.band[k] = A.v[k];
+    D.bandHi[k] = (float)A.v[k];
+    D.bandLo[k] = (float)(A.v[k] - (double)D.bandHi[k]);
+  }
+  D.n = P->n;
+  D.r = r;
+  D.p = p;
+  D.pw = next_pow2(p);
+  D.rows_big = T.rows_big;
+  D.rows_small = T.rows_small;
+  D.count_big = T.count_big;
+  // shared-memory tile geometry (see tile_copy): sp odd, lsz chosen so the
+  // lanes of different lines in one wavefront hit different banks
+  {
+    const bool wide = (d->in_dtype == CBS_DTYPE_F64 || d->out_dtype == CBS_DTYPE_F64);
+    const int mod = wide ? 16 : 32;
+    const int pw = next_pow2(p);
+    D.sp = pw + 1;
+    const int target = (pw < mod) ? pw : 1;
+    int lsz = T.rows_big * D.sp;
+    while (lsz % mod != target % mod) lsz++;
+    D.lsz = lsz;
+    D.bound = T.count_big * T.rows_big;
+    auto mag = [](int dd) -> unsigned {
+      return dd <= 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + (unsigned)dd - 1) / (unsigned)dd);
+    };
+    D.mag_b = mag(T.rows_big);
+    D.mag_s = mag(T.rows_small);
+    D.mag_n = mag(P->n);
+    D.rows_lg = -1;
+    if (T.count_big == p && (T.rows_big & (T.rows_big - 1)) == 0) {
+      int lg = 0;
+      while ((1 << lg) < T.rows_big) lg++;
+      D.rows_lg = lg;
+    }
+  }
+  D.nstage = (int)T.stages.size();
+  D.cyclic = d->cyclic;
+  for (int s = 0; s < D.nstage; s++) D.stage_has_c[s] = T.stage_has_c[s];
+  const size_t ncoef = T.coef.size(), nsrc = T.src.size();
+  const size_t bytes = ncoef * sizeof(double) + ncoef * sizeof(float) + nsrc * sizeof(int) + 256;
+  std::vector<float> coefF(T.coef.begin(), T.coef.end());
+  cudaError_t e = cudaMalloc(&P->dbuf, bytes);
+  if (e != cudaSuccess) {
+    delete P;
+    return cuda_fail(e, "cudaMalloc(plan tables)");
+  }
+  char* base = (char*)P->dbuf;
+  e = cudaMemcpy(base, T.coef.data(), ncoef * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + ncoef * sizeof(double), coefF.data(), ncoef * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + ncoef * (sizeof(double) + sizeof(float)), T.src.data(), nsrc * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&P->dstatus, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(P->dbuf);
+    if (P->dstatus) cudaFree(P->dstatus);
+    delete P;
+    return cuda_fail(e, "uploading plan tables");
+  }
+  D.coef = (const double*)base;
+  D.coefF = (const float*)(base + ncoef * sizeof(double));
+  D.src = (const int*)(base + ncoef * (sizeof(double) + sizeof(float)));
+
+  // ---- kernel arguments that do not change between solves ----
+  LineArgs& a = P->args;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = d->dims[0];
+  a.ny = d->dims[1];
+  a.nz = d->dims[2];
+  a.nlines = P->nlines;
+  a.dir = d->direction;
+  a.K = (d->rhs_kind == CBS_RHS_CENTRAL) ? d->rhs_terms : 0;
+  a.sweeps = d->refine_sweeps;
+  for (int q = 0; q < kMaxRhsTerms; q++) {
+    const double w = (q < a.K) ? d->rhs_coef[q] / (2.0 * (q + 1) * d->h) : 0.0;
+    a.w[q] = w;
+    a.wHi[q] = (float)w;
+    a.wLo[q] = (float)(w - (double)a.wHi[q]);
+  }
+  a.status = P->dstatus;
+  P->kind = 0;
+  if (P->var) {
+    VarArgs& v = P->vargs;
+    std::memset(&v, 0, sizeof(v));
+    v.alpha = d->bands;
+    v.nx = a.nx;
+    v.ny = a.ny;
+    v.nz = a.nz;
+    v.nlines = a.nlines;
+    v.dir = a.dir;
+    for (int q = 0; q < kMaxRhsTerms; q++) v.w[q] = a.w[q];
+    for (int k = 0; k < (int)T.stages.size(); k++) {
+      v.stage_type[k] = T.stages[k].type;
+      v.stage_s[k] = T.stages[k].s;
+      v.stage_na[k] = T.stages[k].na;
+    }
+    v.status = P->dstatus;
+  }
+  *out = P;
+  return CBS_OK;
+}
+
+cbs_status cbs_plan_set_bands(cbs_plan* P, const void* bands) {
+  if (!P || !bands) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  if (!P->var) return fail(CBS_ERR_INVALID_ARG, "plan has Toeplitz bands");
+  P->desc.bands = bands;
+  P->vargs.alpha = bands;
+  return CBS_OK;
+}
+
+cbs_status cbs_plan_destroy(cbs_plan* P) {
+  if (!P) return fail(CBS_ERR_INVALID_ARG, "null plan");
+  cudaDeviceSynchronize();
+  if (P->dbuf) cudaFree(P->dbuf);
+  if (P->dstatus) cudaFree(P->dstatus);
+  delete P;
+  return CBS_OK;
+}
+
+cbs_status cbs_plan_info_get(const cbs_plan* P, cbs_plan_info* info) {
+  if (!P || !info) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n = P->n;
+  info->bandwidth = P->desc.bandwidth;
+  info->segments = P->host.p;
+  info->rows_big = P->host.rows_big;
+  info->rows_small = P->host.rows_small;
+  info->count_big = P->host.count_big;
+  info->pcr_steps = P->host.pcr_steps;
+  info->detach_steps = P->host.detach_steps;
+  info->detached_rows = P->host.detached_rows;
+  info->stage_count = (int32_t)P->host.stages.size();
+  info->kernel = P->kind;
+  info->threads_per_line = P->dev.pw;
+  info->lines = P->nlines;
+  return CBS_OK;
+}
+
+cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
+  g_launches = 0;
+  if (!P || !in || !out) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  if (in == out) return fail(CBS_ERR_INVALID_ARG, "out must not alias in");
+  const cbs_desc& d = P->desc;
+  if (P->var) {
+    VarArgs v = P->vargs;
+    v.f = in;
+    v.out = out;
+    v.alpha = d.bands;
+    cudaError_t e = launch_var(P->M, P->ks, false, d.precision == CBS_FP64, v, P->dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "variable-band kernel launch");
+    g_launches = 1;
+    return CBS_OK;
+  }
+  LineArgs a = P->args;
+  a.in = in;
+  a.out = out;
+  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaErrorInvalidValue;
+  const int R = P->r;
+#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, P->ks, d.in_dtype, d.out_dtype, a, P->dev, s)
+  if (mode == kModeF64) e = (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
+  else if (mode == kModeF32) e = (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
+  else e = (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+#undef CBS_L
+  if (e != cudaSuccess) return cuda_fail(e, "line kernel launch");
+  g_launches = 1;
+  return CBS_OK;
+}
+
+cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* lambda, void* grad_in,
+                               void* grad_bands, void* stream) {
+  g_launches = 0;
+  if (!P || !g) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  const cbs_desc& d = P->desc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (P->var) {
+    if (!lambda && !grad_in && !(x && grad_bands)) return CBS_OK;
+    VarArgs v = P->vargs;
+    v.f = g;
+    v.alpha = d.bands;
+    v.x = (x && grad_bands) ? x : nullptr;
+    v.grad_alpha = (x && grad_bands) ? grad_bands : nullptr;
+    v.lam = lambda;
+    v.out = (P->ks > 0) ? grad_in : nullptr;
+    cudaError_t e = launch_var(P->M, P->ks, true, d.precision == CBS_FP64, v, P->dev, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+    g_launches = 1;
+    return CBS_OK;
+  }
+  // Toeplitz: A is symmetric, and on a periodic grid A^{-1} and the central
+  // stencil S are both circulant, so S^T A^{-T} g = A^{-1} (S^T g) = A^{-1} (-S g):
+  // the same line kernel with negated stencil weights.
+  if (d.in_dtype != d.out_dtype) return fail(CBS_ERR_UNSUPPORTED, "transpose needs in_dtype == out_dtype");
+  if (!d.cyclic) return fail(CBS_ERR_UNSUPPORTED, "transpose of acyclic plans");
+  if (grad_bands) return fail(CBS_ERR_INVALID_ARG, "Toeplitz plans have no band field");
+  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  const int R = P->r;
+  int launches = 0;
+  auto run = [&](const LineArgs& a, int ks) -> cudaError_t {
+#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, d.out_dtype, d.in_dtype, a, P->dev, s)
+    if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
+    if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
+    return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+#undef CBS_L
+  };
+  if (lambda) {
+    LineArgs a = P->args;
+    a.in = g;
+    a.out = lambda;
+    a.K = 0;
+    cudaError_t e = run(a, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "transpose solve launch");
+    launches++;
+  }
+  if (grad_in && P->ks > 0) {
+    LineArgs a = P->args;
+    a.in = g;
+    a.out = grad_in;
+    for (int q = 0; q < kMaxRhsTerms; q++) {
+      a.w[q] = -a.w[q];
+      a.wHi[q] = -a.wHi[q];
+      a.wLo[q] = -a.wLo[q];
+    }
+    cudaError_t e = run(a, P->ks);
+    if (e != cudaSuccess) return cuda_fail(e, "transpose solve launch");
+    launches++;
+  } else if (grad_in) {
+    return fail(CBS_ERR_INVALID_ARG, "grad_in needs a plan with a stencil (use lambda)");
+  }
+  g_launches = launches;
+  return CBS_OK;
+}
+
+cbs_status cbs_band_grad(cbs_plan* P, const void* lambda, const void* x, void* grad_bands, void* stream) {
+  g_launches = 0;
+  if (!P || !lambda || !x || !grad_bands) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  const cbs_desc& d = P->desc;
+  cudaError_t e = launch_band_grad(d.in_dtype == CBS_DTYPE_F64, lambda, x, grad_bands, d.dims[0], d.dims[1],
+                                   d.dims[2], d.direction, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "band gradient launch");
+  g_launches = 1;
+  return CBS_OK;
+}
+
+cbs_status cbs_status_poll(cbs_plan* P, int32_t* device_status) {
+  if (!P || !device_status) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+  e = cudaMemset(P->dstatus, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the status word");
+  *device_status = v;
+  return CBS_OK;
+}
+
+cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t count) {
+  if (!out || !descs) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (count < 1 || count > kBatchMax) return fail(CBS_ERR_INVALID_ARG, "batch count must be 1..256");
+  cbs_batch* B = new (std::nothrow) cbs_batch();
+  if (!B) return fail(CBS_ERR_NO_MEMORY, "host allocation failed");
+  const size_t pb = batch_problem_bytes();
+  std::vector<unsigned char> probs(pb * count);
+  std::vector<int4> items;
+  std::vector<double> cost;
+  for (int k = 0; k < count; k++) {
+    const cbs_desc& d = descs[k];
+    if (d.lhs_kind != CBS_LHS_TOEPLITZ || d.in_dtype != CBS_DTYPE_F64 || d.out_dtype != CBS_DTYPE_F64 ||
+        (d.precision != CBS_FP64 && d.precision != CBS_FP32_REFINE)) {
+      cbs_batch_destroy(B);
+      return fail(CBS_ERR_UNSUPPORTED, "batch problems: Toeplitz, FP64 in/out, FP64 or FP32_REFINE");
+    }
+    cbs_plan* P = nullptr;
+    cbs_status st = cbs_plan_create(&P, &d);
+    if (st) {
+      const std::string msg = "batch problem " + std::to_string(k) + ": " + g_err;
+      cbs_batch_destroy(B);
+      return fail(st, msg);
+    }
+    B->plans.push_back(P);
+    const int mode = d.precision == CBS_FP64 ? kModeF64 : kModeRefine;
+    const int variant = batch_variant_host(P->r, P->ks, P->M, mode);
+    if (variant < 0) {
+      cbs_batch_destroy(B);
+      return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": tile variant not compiled");
+    }
+    batch_fill_problem(probs.data() + pb * k, P->args, P->dev, variant);
+    const int TL = kLineThreads / P->dev.pw;
+    B->smem = std::max(B->smem, (size_t)TL * P->dev.lsz * sizeof(double));
+    const dim3 g = tile_grid(d.dims[0], d.dims[1], d.dims[2], P->nlines, d.direction, TL);
+    const double c = (double)TL * P->n * (mode == kModeRefine ? 2.0 : 1.0);
+    for (unsigned ty = 0; ty < g.y; ty++)
+      for (unsigned tx = 0; tx < g.x; tx++) {
+        items.push_back(make_int4(k, (int)tx, (int)ty, 0));
+        cost.push_back(c);
+      }
+    B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
+  }
+  // most expensive tiles first, so the static stride ends with small tiles
+  std::vector<size_t> order(items.size());
+  for (size_t q = 0; q < order.size(); q++) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  std::vector<int4> sorted(items.size());
+  for (size_t q = 0; q < order.size(); q++) sorted[q] = items[order[q]];
+  B->nitems = (int)sorted.size();
+  B->count = count;
+  cudaError_t e = batch_configure(B->smem);
+  if (e == cudaSuccess) e = cudaMalloc(&B->dprobs, probs.size());
+  if (e == cudaSuccess) e = cudaMalloc(&B->ditems, sorted.size() * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMemcpy(B->dprobs, probs.data(), probs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(B->ditems, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cbs_batch_destroy(B);
+    return cuda_fail(e, "batch setup");
+  }
+  B->grid = std::min(B->nitems, 2 * sms);
+  *out = B;
+  return CBS_OK;
+}
+
+cbs_status cbs_batch_destroy(cbs_batch* B) {
+  if (!B) return fail(CBS_ERR_INVALID_ARG, "null batch");
+  for (cbs_plan* P : B->plans) cbs_plan_destroy(P);
+  if (B->dprobs) cudaFree(B->dprobs);
+  if (B->ditems) cudaFree(B->ditems);
+  delete B;
+  return CBS_OK;
+}
+
+cbs_status cbs_batch_solve(cbs_batch* B, const void* const* ins, void* const* outs, void* stream) {
+  g_launches = 0;
+  if (!B || !ins || !outs) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < B->count; k++)
+    if (!ins[k] || !outs[k] || ins[k] == outs[k]) return fail(CBS_ERR_INVALID_ARG, "bad pointer for problem " + std::to_string(k));
+  cudaError_t e = batch_launch((const BatchProblem*)B->dprobs, (const int4*)B->ditems, B->nitems, ins, outs, B->count,
+                               B->grid, B->smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+  g_launches = 1;
+  return CBS_OK;
+}
+
+cbs_status cbs_batch_status_poll(cbs_batch* B, int32_t* st) {
+  if (!B || !st) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "batch status");
+  *st = CBS_OK;
+  return CBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// cbs_batch.cu -- ragged batches: many independent problems (own sizes,
+// direction, bandwidth, precision) solved by one persistent launch.
+//
+// Every problem is a pre-factorised plan (its DevLineTables and LineArgs live
+// in a device array); the host builds a work table with one entry per tile
+// of lines (problem, tile x, tile y).  The persistent kernel walks the work
+// table with a static stride of gridDim.x, dispatching each tile to the
+// line_tile instantiation of its problem.  Input and output pointers travel
+// by value in the kernel parameters, so a solve is exactly one launch with
+// no allocation, copy or host synchronisation, and can be captured in a CUDA
+// graph.
+#include "cbs_line_launch.cuh"
+
+namespace cbs {
+
+struct BatchProblem {
+  LineArgs args;
+  DevLineTables tab;
+  int variant;
+};
+
+constexpr int kMaxBatch = 256;
+
+struct BatchParams {
+  const BatchProblem* probs;
+  const int4* items;  // (problem, tile x, tile y, 0)
+  int nitems;
+  const void* in[kMaxBatch];
+  void* out[kMaxBatch];
+};
+
+// The tile variants compiled into the persistent kernel: (R, KS) in
+// {(1,2), (2,3), (1,0), (2,0)} x M in {8, 16} x {FP64, FP32 + refinement};
+// FP64 input and output.
+__host__ __device__ constexpr int batch_variant(int R, int KS, int M, int MODE) {
+  const int rk = (R == 1 && KS == 2) ? 0 : (R == 2 && KS == 3) ? 1 : (R == 1 && KS == 0) ? 2 : (R == 2 && KS == 0) ? 3 : -1;
+  const int mi = (M == 8) ? 0 : (M == 16) ? 1 : -1;
+  const int mo = (MODE == kModeF64) ? 0 : (MODE == kModeRefine) ? 1 : -1;
+  return (rk < 0 || mi < 0 || mo < 0) ? -1 : (rk * 2 + mi) * 2 + mo;
+}
+
+#define CBS_BV(R, KS, M, MODE)                                                                   \
+  case batch_variant(R, KS, M, MODE):                                                            \
+    line_tile<R, M, MODE, KS, double, double>(P.args, P.tab, bp.in[w.x], bp.out[w.x], w.y, w.z, \
+                                              smem_raw);                                         \
+    break;
+
+__global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int it = blockIdx.x; it < bp.nitems; it += gridDim.x) {
+    const int4 w = bp.items[it];
+    const BatchProblem& P = bp.probs[w.x];
+    switch (P.variant) {
+      CBS_BV(1, 2, 8, kModeF64)
+      CBS_BV(1, 2, 8, kModeRefine)
+      CBS_BV(1, 2, 16, kModeF64)
+      CBS_BV(1, 2, 16, kModeRefine)
+      CBS_BV(2, 3, 8, kModeF64)
+      CBS_BV(2, 3, 8, kModeRefine)
+      CBS_BV(2, 3, 16, kModeF64)
+      CBS_BV(2, 3, 16, kModeRefine)
+      CBS_BV(1, 0, 8, kModeF64)
+      CBS_BV(1, 0, 8, kModeRefine)
+      CBS_BV(1, 0, 16, kModeF64)
+      CBS_BV(1, 0, 16, kModeRefine)
+      CBS_BV(2, 0, 8, kModeF64)
+      CBS_BV(2, 0, 8, kModeRefine)
+      CBS_BV(2, 0, 16, kModeF64)
+      CBS_BV(2, 0, 16, kModeRefine)
+      default:
+        break;
+    }
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+#undef CBS_BV
+
+int batch_variant_host(int R, int KS, int M, int MODE) { return batch_variant(R, KS, M, MODE); }
+
+cudaError_t batch_configure(size_t smem) {
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitems, const void* const* ins,
+                         void* const* outs, int count, int grid, size_t smem, cudaStream_t s) {
+  BatchParams bp;
+  bp.probs = probs;
+  bp.items = items;
+  bp.nitems = nitems;
+  for (int k = 0; k < kMaxBatch; k++) {
+    bp.in[k] = k < count ? ins[k] : nullptr;
+    bp.out[k] = k < count ? outs[k] : nullptr;
+  }
+  batch_kernel<<<grid, kLineThreads, smem, s>>>(bp);
+  return cudaGetLastError();
+}
+
+size_t batch_problem_bytes() { return sizeof(BatchProblem); }
+
+void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant) {
+  BatchProblem* p = static_cast<BatchProblem*>(dst);
+  p->args = a;
+  p->tab = t;
+  p->variant = variant;
+}
+
+}  // namespace cbs

@@ -1,0 +1,771 @@
+// cbs_line.cuh -- on-chip line kernel: one warp lane per partition.
+//
+// Each line (one independent cyclic system) is handled by a group of `pw`
+// lanes of one warp; lane i owns partition i (rows start_i .. start_i+m_i-1,
+// Sec. 3, Fig. 3): its first r rows are the interface unknowns x~_i, the rest
+// the bulk block D_i.  Per line the kernel performs, without leaving the SM:
+//   a1  the periodic central stencil b = S f (Eq. 1), from a register window;
+//   a2  y_i = D_i^{-1} b_i by banded forward/backward elimination with the
+//       plan's pre-factorised LU of D_i (Eq. 17), in registers;
+//   a3  b-hat_i = b~_i - L~_i y_{i-1} - U~_i y_i (Eq. 21) and the cyclic
+//       block-PCR with detach/reattach on the interface system
+//       (Algorithms 1-4) using warp shuffles, always in FP64, with the W^{-1}
+//       products precomputed per stage (Sec. 4);
+//   a4  x_i = y_i - S_i x~_i - R_i x~_{i+1} (Eq. 22).
+// The FP32 + refinement mode runs a2-a4 in FP32 twice (or three times) and
+// evaluates the residual b - A x to FP64 accuracy with error-free FP32
+// transformations (two-sum / two-product), because the FP64 pipe of this
+// GPU issues ~1/69 as many operations per clock as the FP32 pipe.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "cbs_internal.h"
+
+namespace cbs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+enum Mode { kModeF64 = 0, kModeF32 = 1, kModeRefine = 2 };
+
+struct LineArgs {
+  const void* in;
+  void* out;
+  int64_t nx, ny, nz;
+  int64_t nlines;
+  int dir;
+  int K;                 // stencil terms actually used (<= template KS)
+  int sweeps;            // refinement sweeps (kModeRefine)
+  double w[kMaxRhsTerms];              // c_q / (2 q h)
+  float wHi[kMaxRhsTerms], wLo[kMaxRhsTerms];
+  int* status;
+};
+
+// Field geometry: (nx, ny, nz) with x contiguous, lines along `dir`.
+struct Geom {
+  int64_t nx, ny;
+  int dir;
+};
+
+// ---------------------------------------------------------------- helpers
+template <typename A>
+__device__ __forceinline__ int64_t line_base(const A& a, int64_t L, int64_t& es) {
+  if (a.dir == 0) {
+    es = 1;
+    return L * a.nx;
+  }
+  const int64_t x = L % a.nx, o = L / a.nx;
+  if (a.dir == 1) {
+    es = a.nx;
+    return x + a.nx * a.ny * o;
+  }
+  es = a.nx * a.ny;
+  return x + a.nx * o;
+}
+
+template <typename T> __device__ __forceinline__ T ld_in(const T* p) { return __ldg(p); }
+
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double fac(const DevLineTables& t, int k) { return t.fac[k]; }
+  static __device__ __forceinline__ double sr(const DevLineTables& t, bool big, int k) {
+    return big ? t.srB[k] : t.srS[k];
+  }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float fac(const DevLineTables& t, int k) { return t.facF[k]; }
+  static __device__ __forceinline__ float sr(const DevLineTables& t, bool big, int k) {
+    return big ? t.srBF[k] : t.srSF[k];
+  }
+};
+
+template <typename TI> struct ITab;
+template <> struct ITab<double> {
+  static __device__ __forceinline__ double coef(const DevLineTables& t, int k) { return __ldg(t.coef + k); }
+  static __device__ __forceinline__ double ucoef(const DevLineTables& t, int st, int k) { return t.ucoef[st][k]; }
+  static __device__ __forceinline__ double Lt(const DevLineTables& t, int q, int e) { return t.Lt[q][e]; }
+  static __device__ __forceinline__ double Ut(const DevLineTables& t, int q, int e) { return t.Ut[q][e]; }
+};
+template <> struct ITab<float> {
+  static __device__ __forceinline__ float coef(const DevLineTables& t, int k) { return __ldg(t.coefF + k); }
+  static __device__ __forceinline__ float ucoef(const DevLineTables& t, int st, int k) { return t.ucoefF[st][k]; }
+  static __device__ __forceinline__ float Lt(const DevLineTables& t, int q, int e) { return t.LtF[q][e]; }
+  static __device__ __forceinline__ float Ut(const DevLineTables& t, int q, int e) { return t.UtF[q][e]; }
+};
+
+// Error-free transformations on FP32 (Knuth two-sum, FMA two-product).
+struct f2 {
+  float hi, lo;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// FP64 <-> FP32-pair conversions with integer operations.  On this GPU the
+// f32<->f64 conversion instructions and every FP64 add issue on the FP64
+// pipe (~1/69 of the FP32 rate), so the FP32 paths build the bit patterns
+// themselves and keep the FP64 pipe for nothing but the rare special values.
+//
+// No FP64 instruction is issued by these helpers, not even for special
+// values: a rarely taken FP64 slow path gets if-converted into predicated
+// FP64 instructions that are issued for every element.  The FP32 modes work
+// in the FP32 range: magnitudes below 2^-126 are flushed to zero (below
+// 2^-103 the low part is dropped), magnitudes of 2^128 and more become inf.
+//
+// split_f64: hi = x truncated to 24 significant bits, lo = the next 23 bits
+// (|x - hi - lo| <= 2^-46 |x| for 2^-103 <= |x| < 2^128).
+__device__ __forceinline__ f2 split_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned e = (hw >> 20) & 0x7ffu;
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  if (e - 920u < 231u) {
+    const float hi = __uint_as_float(sign | ((e - 896u) << 23) | m23);
+    const unsigned E = (e - 919u) << 23;
+    const float lo = __fsub_rn(__uint_as_float(sign | E | ((lw & 0x1fffffffu) >> 6)), __uint_as_float(sign | E));
+    return {hi, lo};
+  }
+  unsigned hb;
+  if (e - 897u < 23u) hb = sign | ((e - 896u) << 23) | m23;          // 2^-126 <= |x| < 2^-103
+  else if (e < 897u) hb = sign;                                        // flushed to +-0
+  else if (e == 0x7ffu && ((hw & 0xfffffu) | lw)) hb = 0x7fc00000u;    // nan
+  else hb = sign | 0x7f800000u;                                        // inf / overflow
+  return {__uint_as_float(hb), 0.f};
+}
+// FP32 -> FP64 bit pattern (exact for every float).
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu, sign = u & 0x80000000u;
+  unsigned hw, lw;
+  if (e - 1u < 254u) {
+    hw = sign | ((e + 896u) << 20) | (m >> 3);
+    lw = m << 29;
+  } else if (e == 0u) {
+    if (m == 0u) {
+      hw = sign;
+      lw = 0u;
+    } else {  // subnormal: m * 2^-149 with its top bit at position k
+      const unsigned k = 31u - (unsigned)__clz(m);
+      const unsigned f = (m << (23u - k)) & 0x7fffffu;
+      hw = sign | ((k + 874u) << 20) | (f >> 3);
+      lw = f << 29;
+    }
+  } else {  // inf / nan
+    hw = sign | 0x7ff00000u | (m >> 3);
+    lw = m << 29;
+  }
+  return __hiloint2double((int)hw, (int)lw);
+}
+// The double at or toward zero from hi + lo (exact when the pair spans <= 53
+// bits) for |lo| <= ulp(hi) as produced by two_sum; integer arithmetic on the
+// 53-bit significand.  Outside the normal FP32 range the result is hi alone.
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+  const unsigned uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const unsigned eh = (uh >> 23) & 0xffu, el = (ul >> 23) & 0xffu;
+  if ((ul << 1) != 0u && eh - 1u < 253u && el - 1u < 253u && eh >= el + 24u) {
+    long long M = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;  // bit 52 = leading one
+    const long long Ml = (long long)((ul & 0x7fffffu) | 0x800000u);
+    const unsigned d = eh - el;                                        // >= 24
+    const long long add = (d <= 29u) ? (Ml << (29u - d)) : (Ml >> (d - 29u));
+    M += ((uh ^ ul) & 0x80000000u) ? -add : add;
+    long long E = (long long)eh + 896;
+    if (M < (1ll << 52)) {  // hi was a power of two and lo pulled it below
+      M <<= 1;
+      E -= 1;
+    }
+    const unsigned long long bits = ((unsigned long long)(uh & 0x80000000u) << 32) |
+                                    ((unsigned long long)E << 52) | ((unsigned long long)M & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+  }
+  return f32_to_f64(hi);
+}
+
+// Element conversions used by the staging and the kernels (no FP64-pipe
+// conversion instructions on the FP32 paths).
+template <typename To, typename From> struct Conv {
+  static __device__ __forceinline__ To f(From x) { return (To)x; }
+};
+template <> struct Conv<double, float> {
+  static __device__ __forceinline__ double f(float x) { return f32_to_f64(x); }
+};
+template <> struct Conv<float, double> {
+  static __device__ __forceinline__ float f(double x) {
+    const f2 s = split_f64(x);
+    return __fadd_rn(s.hi, s.lo);
+  }
+};
+template <typename To, typename From> __device__ __forceinline__ To conv(From x) { return Conv<To, From>::f(x); }
+
+// c ? a : b through an explicit PTX select, so that choosing one register
+// out of an unrolled array by a runtime index never becomes an indexed
+// (local-memory) access.
+__device__ __forceinline__ double sel(bool c, double a, double b) {
+  double r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\tselp.f64 %0, %1, %2, p;\n\t}"
+      : "=d"(r) : "d"(a), "d"(b), "r"((int)c));
+  return r;
+}
+__device__ __forceinline__ float sel(bool c, float a, float b) {
+  float r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\tselp.f32 %0, %1, %2, p;\n\t}"
+      : "=f"(r) : "f"(a), "f"(b), "r"((int)c));
+  return r;
+}
+
+// Partition of lane i (first count_big partitions have rows_big rows).
+__device__ __forceinline__ void partition_of(const DevLineTables& t, int i, int& start, int& size) {
+  if (i < t.count_big) {
+    start = i * t.rows_big;
+    size = t.rows_big;
+  } else {
+    start = t.count_big * t.rows_big + (i - t.count_big) * t.rows_small;
+    size = t.rows_small;
+  }
+}
+
+// ------------------------------------------------- per-partition solve (a2-a4)
+// v[0..size) holds b of this partition on entry and x on exit.  Must be
+// called by all 32 lanes of the warp (it shuffles).  `lane_ok` marks lanes
+// that own a partition (i < p).
+template <typename T, int R, int M, typename TI>
+__device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const int i,
+                                                const bool lane_ok, const DevLineTables& t) {
+  constexpr int F = 2 * R + 1;
+  constexpr int NB = M - R;  // max bulk rows
+  const int N = size - R;
+  const bool big = i < t.count_big;
+  const int pw = t.pw, p = t.p;
+
+  // a2: forward elimination of the bulk block
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    if (j < N) {
+      T s = v[R + j];
+#pragma unroll
+      for (int q = 1; q <= R; q++)
+        if (j - q >= 0) s -= Tab<T>::fac(t, j * F + q - 1) * v[R + j - q];
+      v[R + j] = s;
+    }
+  }
+  // a2: backward substitution -> y_i
+#pragma unroll
+  for (int j = NB - 1; j >= 0; j--) {
+    if (j < N) {
+      T s = Tab<T>::fac(t, j * F + R) * v[R + j];
+#pragma unroll
+      for (int q = 1; q <= R; q++)
+        if (R + j + q < M) {
+          if (j + q < N) s -= Tab<T>::fac(t, j * F + R + q) * v[R + j + q];
+        }
+      v[R + j] = s;
+    }
+  }
+
+  // a3: b-hat_i = b~_i - L~_i y_{i-1}[last r] - U~_i y_i[first r]   (Eq. 21)
+  T ylast[R];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    T val = T(0);
+#pragma unroll
+    for (int u = R; u < M; u++) val = sel(u == N + e, v[u], val);
+    ylast[e] = val;
+  }
+  const int prev = (i == 0) ? p - 1 : i - 1;
+  const int next = (i + 1 >= p) ? 0 : i + 1;
+  const bool has_prev = t.cyclic || i > 0;
+  const bool has_next = t.cyclic || i + 1 < p;
+  TI xt[R];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    const T yp = __shfl_sync(kFull, ylast[e], prev, pw);
+    ylast[e] = yp;  // now y_{i-1}[N_{i-1} - r + e]
+  }
+#pragma unroll
+  for (int q = 0; q < R; q++) {
+    TI b = (TI)v[q];
+#pragma unroll
+    for (int e = 0; e < R; e++) {
+      if (has_prev) b -= ITab<TI>::Lt(t, q, e) * (TI)ylast[e];
+      b -= ITab<TI>::Ut(t, q, e) * (TI)v[R + e];
+    }
+    xt[q] = b;
+  }
+
+  // a3: interface system by block PCR with detach / reattach (Alg. 1-4),
+  // with the W^{-1} products of every stage precomputed in the plan
+  constexpr int rr = R * R;
+  for (int st = 0; st < t.nstage; st++) {
+    int sm = i, sp = i;
+    TI C[rr], KM[rr], KP[rr];
+    if (t.uniform) {
+      const int s = t.ustage_s[st];
+      sp = (i + s) & (p - 1);
+      sm = (i - s) & (p - 1);
+#pragma unroll
+      for (int e = 0; e < rr; e++) {
+        C[e] = ITab<TI>::ucoef(t, st, e);
+        KM[e] = ITab<TI>::ucoef(t, st, rr + e);
+        KP[e] = ITab<TI>::ucoef(t, st, 2 * rr + e);
+      }
+    } else if (lane_ok) {
+      sm = __ldg(t.src + (st * 2 + 0) * p + i);
+      sp = __ldg(t.src + (st * 2 + 1) * p + i);
+#pragma unroll
+      for (int e = 0; e < rr; e++) {
+        C[e] = ITab<TI>::coef(t, ((st * 3 + 0) * rr + e) * p + i);
+        KM[e] = ITab<TI>::coef(t, ((st * 3 + 1) * rr + e) * p + i);
+        KP[e] = ITab<TI>::coef(t, ((st * 3 + 2) * rr + e) * p + i);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < rr; e++) C[e] = KM[e] = KP[e] = TI(0);
+    }
+    TI xm[R], xp[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      xm[q] = __shfl_sync(kFull, xt[q], sm, pw);
+      xp[q] = __shfl_sync(kFull, xt[q], sp, pw);
+    }
+    TI nxt[R];
+    const bool hc = t.stage_has_c[st] != 0;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      TI acc;
+      if (hc) {
+        acc = TI(0);
+#pragma unroll
+        for (int e = 0; e < R; e++) acc += C[q * R + e] * xt[e];
+      } else {
+        acc = xt[q];
+      }
+#pragma unroll
+      for (int e = 0; e < R; e++) acc -= KM[q * R + e] * xm[e] + KP[q * R + e] * xp[e];
+      nxt[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; q++) xt[q] = nxt[q];
+  }
+
+  // a4: back-substitution x_i = y_i - S_i x~_i - R_i x~_{i+1}   (Eq. 22)
+  T xa[R], xb[R];
+#pragma unroll
+  for (int q = 0; q < R; q++) {
+    const TI xn = __shfl_sync(kFull, xt[q], next, pw);
+    xa[q] = (T)xt[q];
+    xb[q] = has_next ? (T)xn : T(0);
+  }
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    if (j < N) {
+      T s = v[R + j];
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        s -= Tab<T>::sr(t, big, j * 2 * R + q) * xa[q];
+        s -= Tab<T>::sr(t, big, j * 2 * R + R + q) * xb[q];
+      }
+      v[R + j] = s;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; q++) v[q] = xa[q];
+}
+
+// Residual r = b - A x for this partition's rows, to FP64 accuracy, with x
+// given as an unevaluated sum xh + xl of floats and b as bh + bl.  Neighbour
+// rows of x come from the adjacent lanes.  Result rounded to FP32.
+template <int R, int M, bool XLO>
+__device__ __forceinline__ void residual_df(const float (&bh)[M], const float (&bl)[M],
+                                            const float (&xh)[M], const float (&xl)[M],
+                                            float (&res)[M], const int size, const int i,
+                                            const DevLineTables& t) {
+  const int p = t.p, pw = t.pw;
+  const int prev = (i == 0) ? p - 1 : i - 1;
+  const int next = (i + 1 >= p) ? 0 : i + 1;
+  // halo: last R rows of the previous partition, first R rows of the next
+  float hh_prev[R], hl_prev[R], hh_next[R], hl_next[R];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    float lh = 0.f, ll = 0.f;
+#pragma unroll
+    for (int u = 0; u < M; u++) {
+      lh = sel(u == size - R + e, xh[u], lh);
+      ll = sel(u == size - R + e, xl[u], ll);
+    }
+    hh_prev[e] = __shfl_sync(kFull, lh, prev, pw);
+    hh_next[e] = __shfl_sync(kFull, xh[e], next, pw);
+    if (XLO) {
+      hl_prev[e] = __shfl_sync(kFull, ll, prev, pw);
+      hl_next[e] = __shfl_sync(kFull, xl[e], next, pw);
+    } else {
+      hl_prev[e] = 0.f;
+      hl_next[e] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < M; k++) {
+    if (k < size) {
+      float ah = bh[k], al = bl[k];
+#pragma unroll
+      for (int tt = -R; tt <= R; tt++) {
+        float vh = 0.f, vl = 0.f;
+        const int kk = k + tt;
+        if (kk < 0) {
+          vh = hh_prev[R + kk];
+          vl = hl_prev[R + kk];
+        } else {
+          if (kk < M) {
+            vh = xh[kk];
+            vl = XLO ? xl[kk] : 0.f;
+          }
+          // rows past the end of this partition belong to the next one
+#pragma unroll
+          for (int e = 0; e < R; e++) {
+            vh = sel(kk == size + e, hh_next[e], vh);
+            vl = sel(kk == size + e, hl_next[e], vl);
+          }
+        }
+        const float bH = t.bandHi[tt + R], bL = t.bandLo[tt + R];
+        const f2 pr = two_prod(bH, vh);
+        const f2 s = two_sum(ah, -pr.hi);
+        ah = s.hi;
+        float lo = s.lo - pr.lo - bL * vh;
+        if (XLO) lo -= bH * vl;
+        al += lo;
+      }
+      res[k] = ah + al;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- staging
+// Shared-memory tile: line l of the tile owns S[l*lsz ...]; row k of
+// partition i sits at k*sp + i (sp = pw + 1).  Lanes of a line read
+// consecutive words for the same k (conflict-free sweeps) and the cooperative
+// copies write consecutive rows of one partition at stride sp (odd), which is
+// conflict-free too.
+__device__ __forceinline__ int fdiv(int x, int d, unsigned mag) {
+  return d == 1 ? x : (int)__umulhi((unsigned)x, mag);
+}
+__device__ __forceinline__ unsigned magic_of(int d) {
+  return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d);
+}
+__device__ __forceinline__ int slot_of(const DevLineTables& t, int row) {
+  if (t.rows_lg >= 0) return (row & ((1 << t.rows_lg) - 1)) * t.sp + (row >> t.rows_lg);
+  if (row < t.bound) {
+    const int i = fdiv(row, t.rows_big, t.mag_b);
+    return (row - i * t.rows_big) * t.sp + i;
+  }
+  const int r2 = row - t.bound;
+  const int j = fdiv(r2, t.rows_small, t.mag_s);
+  return (r2 - j * t.rows_small) * t.sp + t.count_big + j;
+}
+
+template <typename T, int V> struct V16;
+template <> struct V16<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&v)[2]) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = x.x; v[1] = x.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <> struct V16<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&v)[4]) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+// A tile of nl lines: dir 0 -> nl consecutive x-lines starting at `base`
+// (line l at base + l*n, contiguous); dir 1/2 -> nl consecutive x positions,
+// row `row` of line l at base + l + row*es.
+struct TileRef {
+  int64_t base, es;
+  int nl, dir;
+};
+
+// Tile of the CTA.  dir 0: tile tx covers lines tx*TL ...; dir 1/2: tile
+// (tx, to) covers x = tx*TL ... at z = to (dir 1) or y = to (dir 2).  No
+// integer division: the launch grid is 2-D for y/z lines.
+template <typename A>
+__device__ __forceinline__ TileRef tile_of(const A& a, int n, int TL, int tx, int to) {
+  TileRef r;
+  r.dir = a.dir;
+  if (a.dir == 0) {
+    const int64_t L0 = (int64_t)tx * TL;
+    r.base = L0 * n;
+    r.es = 1;
+    r.nl = (int)((a.nlines - L0) < TL ? (a.nlines - L0) : TL);
+  } else {
+    const int64_t x0 = (int64_t)tx * TL;
+    r.base = x0 + (int64_t)to * (a.dir == 1 ? a.nx * a.ny : a.nx);
+    r.es = (a.dir == 1) ? a.nx : a.nx * a.ny;
+    r.nl = (int)((a.nx - x0) < TL ? (a.nx - x0) : TL);
+  }
+  return r;
+}
+
+// Global <-> shared copy of a tile (LOAD: global -> S, else S -> global).
+template <bool LOAD, typename TG, typename TT>
+__device__ __forceinline__ void tile_copy(const TileRef& tr, const DevLineTables& t, TT* S, TG* g0) {
+  using TB = typename std::remove_const<TG>::type;
+  constexpr int V = 16 / sizeof(TB);
+  const int n = t.n, tid = threadIdx.x, nth = blockDim.x, nl = tr.nl;
+  TG* g = g0 + tr.base;
+  if (tr.dir == 0) {
+    const int total = nl * n;
+    if ((n % V) == 0 && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+      for (int c = tid; c < total / V; c += nth) {
+        const int e = c * V, l = fdiv(e, n, t.mag_n), row = e - l * n;
+        TB v[V];
+        if constexpr (LOAD) {
+          V16<TB, V>::ld(g + e, v);
+#pragma unroll
+          for (int u = 0; u < V; u++) S[l * t.lsz + slot_of(t, row + u)] = conv<TT>(v[u]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < V; u++) v[u] = conv<TB>(S[l * t.lsz + slot_of(t, row + u)]);
+          V16<TB, V>::st(g + e, v);
+        }
+      }
+    } else {
+      for (int e = tid; e < total; e += nth) {
+        const int l = fdiv(e, n, t.mag_n), row = e - l * n;
+        if constexpr (LOAD) S[l * t.lsz + slot_of(t, row)] = conv<TT>(__ldg(g + e));
+        else g[e] = conv<TB>(S[l * t.lsz + slot_of(t, row)]);
+      }
+    }
+    return;
+  }
+  const int64_t es = tr.es;
+  if ((nl % V) == 0 && (es % V) == 0 && (reinterpret_cast<uintptr_t>(g) & 15) == 0 && ((nl / V) & (nl / V - 1)) == 0) {
+    const int cpr = nl / V;  // 16-byte chunks per row, a power of two
+    const int lg = __ffs(cpr) - 1;
+    for (int c = tid; c < n * cpr; c += nth) {
+      const int row = c >> lg, ch = c & (cpr - 1);
+      const int so = slot_of(t, row);
+      TB v[V];
+      if constexpr (LOAD) {
+        V16<TB, V>::ld(g + row * es + ch * V, v);
+#pragma unroll
+        for (int u = 0; u < V; u++) S[(ch * V + u) * t.lsz + so] = conv<TT>(v[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < V; u++) v[u] = conv<TB>(S[(ch * V + u) * t.lsz + so]);
+        V16<TB, V>::st(g + row * es + ch * V, v);
+      }
+    }
+  } else {
+    for (int e = tid; e < n * nl; e += nth) {
+      const int row = e / nl, l = e - row * nl;
+      if constexpr (LOAD) S[l * t.lsz + slot_of(t, row)] = conv<TT>(__ldg(g + row * es + l));
+      else g[row * es + l] = conv<TB>(S[l * t.lsz + slot_of(t, row)]);
+    }
+  }
+}
+
+// h[idx] for a small register array and a runtime idx in [0, K), written as a
+// select chain so the array stays in registers.
+template <typename T, int K>
+__device__ __forceinline__ T pick(const T (&h)[K], int idx) {
+  T r = h[0];
+#pragma unroll
+  for (int e = 1; e < K; e++) r = sel(idx == e, h[e], r);
+  return r;
+}
+
+// ---------------------------------------------------------------- kernel
+// One tile = blockDim / pw consecutive lines starting at line L0, processed by
+// the whole CTA: copy-in, per-lane stencil + solve, copy-out.  KS: stencil
+// terms compiled in (0 = the input already is b).  Used by the per-plan
+// kernel (one tile per CTA) and by the persistent batch kernel (many tiles).
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut>
+__device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables& t, const void* in_ptr,
+                                          void* out_ptr, const int tx, const int to, unsigned char* smem_raw) {
+  using T = typename std::conditional<MODE == kModeF64, double, float>::type;
+  using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
+  constexpr int KA = KS > 0 ? KS : 1;  // halo array size (KS = 0 compiles no stencil)
+  TT* S = reinterpret_cast<TT*>(smem_raw);
+  const int pw = t.pw;
+  const int TL = blockDim.x / pw;
+  const TileRef tr = tile_of(a, t.n, TL, tx, to);
+  const int nl = tr.nl;
+  const int g = threadIdx.x / pw, i = threadIdx.x % pw;
+  const bool lane_ok = i < t.p;
+  const bool ok = lane_ok && g < nl;
+  int start = 0, size = R * 2;
+  if (lane_ok) partition_of(t, i, start, size);
+  const int n = t.n;
+  TT* SL = S + g * t.lsz;
+
+  tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
+  __syncthreads();
+
+  if (MODE != kModeRefine) {
+    T v[M];
+    if (KS == 0) {
+#pragma unroll
+      for (int k = 0; k < M; k++) v[k] = (ok && k < size) ? conv<T>(SL[k * t.sp + i]) : T(0);
+    } else {
+      // a1: stencil from rows start-KS .. start+size-1+KS (halo rows of the
+      // neighbouring partitions, periodic in the line)
+      T fw[M + KS], hh[KA];
+#pragma unroll
+      for (int q = 0; q < KS; q++) {
+        int rlo = start - KS + q;
+        rlo += (rlo < 0) ? n : 0;
+        fw[q] = ok ? conv<T>(SL[slot_of(t, rlo)]) : T(0);
+        int rhi = start + size + q;
+        rhi -= (rhi >= n) ? n : 0;
+        hh[q] = ok ? conv<T>(SL[slot_of(t, rhi)]) : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < M; k++) fw[KS + k] = (ok && k < size) ? conv<T>(SL[k * t.sp + i]) : T(0);
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        T s = T(0);
+#pragma unroll
+        for (int q = 1; q <= KS; q++) {
+          T up;
+          const int kq = (k + q < M) ? k + q : M - 1;  // compile-time clamp
+          if (k + q < M) up = (k + q < size) ? fw[KS + kq] : pick<T, KA>(hh, k + q - size);
+          else up = pick<T, KA>(hh, k + q - size);
+          s += (T)a.w[q - 1] * (up - fw[KS + k - q]);
+        }
+        v[k] = s;
+      }
+    }
+    solve_partition<T, R, M, T>(v, size, i, lane_ok, t);
+    __syncwarp();
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < M; k++)
+        if (k < size) SL[k * t.sp + i] = conv<TT>(v[k]);
+    }
+  } else {
+    // FP32 bulk + FP64-accurate residual refinement.
+    float bh[M], bl[M];
+    if (KS == 0) {
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        f2 sv = {0.f, 0.f};
+        if (ok && k < size) {
+          const TT x = SL[k * t.sp + i];
+          if (sizeof(TT) == 8) sv = split_f64((double)x);
+          else sv = {(float)x, 0.f};
+        }
+        bh[k] = sv.hi;
+        bl[k] = sv.lo;
+      }
+    } else {
+      float fh[M + KS], fl[M + KS], hh[KA], hl[KA];
+#pragma unroll
+      for (int q = 0; q < KS; q++) {
+        int rlo = start - KS + q;
+        rlo += (rlo < 0) ? n : 0;
+        const TT x = ok ? SL[slot_of(t, rlo)] : TT(0);
+        const f2 sv = (sizeof(TT) == 8) ? split_f64((double)x) : f2{(float)x, 0.f};
+        fh[q] = sv.hi;
+        fl[q] = sv.lo;
+        int rhi = start + size + q;
+        rhi -= (rhi >= n) ? n : 0;
+        const TT y = ok ? SL[slot_of(t, rhi)] : TT(0);
+        const f2 sy = (sizeof(TT) == 8) ? split_f64((double)y) : f2{(float)y, 0.f};
+        hh[q] = sy.hi;
+        hl[q] = sy.lo;
+      }
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const TT x = (ok && k < size) ? SL[k * t.sp + i] : TT(0);
+        const f2 sv = (sizeof(TT) == 8) ? split_f64((double)x) : f2{(float)x, 0.f};
+        fh[KS + k] = sv.hi;
+        fl[KS + k] = sv.lo;
+      }
+      // a1 in double-float: b = sum_q w_q (f_{k+q} - f_{k-q})
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        float dh = 0.f, dl = 0.f;
+#pragma unroll
+        for (int q = 1; q <= KS; q++) {
+          float uh, ul;
+          const int kq = (k + q < M) ? k + q : M - 1;  // compile-time clamp
+          if (k + q < M && k + q < size) {
+            uh = fh[KS + kq];
+            ul = fl[KS + kq];
+          } else {
+            uh = pick<float, KA>(hh, k + q - size);
+            ul = pick<float, KA>(hl, k + q - size);
+          }
+          const f2 df = two_sum(uh, -fh[KS + k - q]);
+          const float dlo = df.lo + (ul - fl[KS + k - q]);
+          const f2 pr = two_prod(a.wHi[q - 1], df.hi);
+          const float plo = pr.lo + __fmaf_rn(a.wHi[q - 1], dlo, a.wLo[q - 1] * df.hi);
+          const f2 sm = two_sum(dh, pr.hi);
+          dh = sm.hi;
+          dl += sm.lo + plo;
+        }
+        const f2 nrm = two_sum(dh, dl);
+        bh[k] = nrm.hi;
+        bl[k] = nrm.lo;
+      }
+    }
+    // sweep 0: x0 = A^{-1} round(b)
+    float xh[M], xl[M], v[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) v[k] = bh[k];
+    solve_partition<float, R, M, float>(v, size, i, lane_ok, t);
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      xh[k] = v[k];
+      xl[k] = 0.f;
+    }
+    // refinement sweeps: x <- x + A^{-1}(b - A x), residual to FP64 accuracy
+    for (int sw = 0; sw < a.sweeps; sw++) {
+      if (sw == 0) residual_df<R, M, false>(bh, bl, xh, xl, v, size, i, t);
+      else residual_df<R, M, true>(bh, bl, xh, xl, v, size, i, t);
+      solve_partition<float, R, M, float>(v, size, i, lane_ok, t);
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const f2 sm = two_sum(xh[k], v[k]);
+        xh[k] = sm.hi;
+        xl[k] = xl[k] + sm.lo;
+      }
+    }
+    __syncwarp();
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < M; k++)
+        if (k < size) {
+          const f2 nrm = fast_two_sum(xh[k], xl[k]);
+          SL[k * t.sp + i] = (sizeof(TT) == 8) ? (TT)df_to_double(nrm.hi, nrm.lo) : (TT)nrm.hi;
+        }
+    }
+  }
+  __syncthreads();
+  tile_copy<false, TOut, TT>(tr, t, S, (TOut*)out_ptr);
+}
+
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut>
+__global__ void __launch_bounds__(256, (MODE == kModeRefine) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  line_tile<R, M, MODE, KS, TIn, TOut>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+}  // namespace cbs

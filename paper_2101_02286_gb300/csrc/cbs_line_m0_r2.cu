@@ -1,0 +1,5 @@
+// Instantiations of the on-chip line kernel for mode 0, half bandwidth 2.
+#include "cbs_line_launch.cuh"
+namespace cbs {
+CBS_DEFINE_LINE_LAUNCH(0, 2)
+}  // namespace cbs

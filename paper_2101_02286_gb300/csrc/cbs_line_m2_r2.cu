@@ -1,0 +1,5 @@
+// Instantiations of the on-chip line kernel for mode 2, half bandwidth 2.
+#include "cbs_line_launch.cuh"
+namespace cbs {
+CBS_DEFINE_LINE_LAUNCH(2, 2)
+}  // namespace cbs

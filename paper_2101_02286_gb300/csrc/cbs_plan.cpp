@@ -1,0 +1,402 @@
+// cbs_plan.cpp -- host-side pre-factorisation of the partitioned system.
+//
+// For a Toeplitz line matrix A (half bandwidth r, cyclic or not) split into
+// p partitions this computes, in FP64, everything the per-solve kernels need
+// that does not depend on the right-hand side (paper Sec. 4, last paragraph):
+//   - the banded LU factors of the bulk blocks D_i (Sec. 3, Fig. 3);
+//   - S_i = D_i^{-1} L_i and R_i = D_i^{-1} U_i (Eq. 15-16);
+//   - the reduced blocks D-hat, L-hat, U-hat of the interface system (Eq. 18-20);
+//   - the interface schedule (Algorithm 1) and, for every stage, the
+//     coefficient blocks acting on x~ (Algorithms 2-4 with the W^{-1}
+//     products precomputed), so a solve only updates x~.
+#include <cmath>
+#include <cstring>
+
+#include "cbs_internal.h"
+
+namespace cbs {
+
+std::vector<Stage> build_schedule(int p, bool cyclic) {
+  std::vector<Stage> st;
+  if (p < 1) return st;
+  if (!cyclic) {
+    // Classic block PCR on an acyclic system: ceil(log2 p) steps (Sec. 4).
+    int s = 1;
+    while (s < p) {
+      st.push_back({kPcr, s, p});
+      s *= 2;
+    }
+    st.push_back({kFinal, s, p});
+    return st;
+  }
+  // Algorithm 1: detach the last row of each sub-system whenever the
+  // sub-system dimension is odd, then one block PCR step.
+  int s = 1, n0 = p, na = p;
+  std::vector<int> stack;
+  while (n0 > 1) {
+    int odd = n0 % 2;
+    stack.push_back(odd);
+    if (odd) {
+      n0 -= 1;
+      na -= s;
+      st.push_back({kDetach, s, na});
+    }
+    st.push_back({kPcr, s, na});
+    s *= 2;
+    n0 /= 2;
+  }
+  st.push_back({kFinal, s, na});
+  while (!stack.empty()) {
+    n0 *= 2;
+    s /= 2;
+    int odd = stack.back();
+    stack.pop_back();
+    if (odd) {
+      st.push_back({kReattach, s, na});
+      na += s;
+      n0 += 1;
+    }
+  }
+  return st;
+}
+
+namespace {
+
+// r x r row-major blocks, r <= 2.
+struct Blk {
+  int r;
+  double a[kMaxR * kMaxR];
+  explicit Blk(int r_ = 1) : r(r_) { std::memset(a, 0, sizeof(a)); }
+  double& operator()(int i, int j) { return a[i * r + j]; }
+  double operator()(int i, int j) const { return a[i * r + j]; }
+  static Blk eye(int r) {
+    Blk b(r);
+    for (int i = 0; i < r; i++) b(i, i) = 1.0;
+    return b;
+  }
+};
+Blk operator*(const Blk& x, const Blk& y) {
+  Blk z(x.r);
+  for (int i = 0; i < x.r; i++)
+    for (int j = 0; j < x.r; j++) {
+      double s = 0;
+      for (int k = 0; k < x.r; k++) s += x(i, k) * y(k, j);
+      z(i, j) = s;
+    }
+  return z;
+}
+Blk operator+(const Blk& x, const Blk& y) {
+  Blk z(x.r);
+  for (int i = 0; i < x.r * x.r; i++) z.a[i] = x.a[i] + y.a[i];
+  return z;
+}
+Blk operator-(const Blk& x, const Blk& y) {
+  Blk z(x.r);
+  for (int i = 0; i < x.r * x.r; i++) z.a[i] = x.a[i] - y.a[i];
+  return z;
+}
+Blk neg(const Blk& x) {
+  Blk z(x.r);
+  for (int i = 0; i < x.r * x.r; i++) z.a[i] = -x.a[i];
+  return z;
+}
+double maxabs(const Blk& x) {
+  double m = 0.0;
+  for (int i = 0; i < x.r * x.r; i++) m = std::fmax(m, std::fabs(x.a[i]));
+  return m;
+}
+// Inverse; returns false when non-finite or numerically singular, i.e. when
+// |det| <= 1e-12 * scale^r with `scale` the magnitude of the blocks that were
+// combined into x (so rounding residue of an exactly singular block counts).
+bool inv(const Blk& x, Blk& out, double scale = 0.0) {
+  out = Blk(x.r);
+  scale = std::fmax(scale, maxabs(x));
+  if (x.r == 1) {
+    if (!std::isfinite(x.a[0]) || !(std::fabs(x.a[0]) > 1e-12 * scale)) return false;
+    out.a[0] = 1.0 / x.a[0];
+    return true;
+  }
+  double det = x(0, 0) * x(1, 1) - x(0, 1) * x(1, 0);
+  if (!std::isfinite(det) || !(std::fabs(det) > 1e-12 * scale * scale)) return false;
+  out(0, 0) = x(1, 1) / det;
+  out(1, 1) = x(0, 0) / det;
+  out(0, 1) = -x(0, 1) / det;
+  out(1, 0) = -x(1, 0) / det;
+  return true;
+}
+
+}  // namespace
+
+std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool cyclic,
+                              bool* singular, int max_lanes) {
+  *singular = false;
+  const int r = A.r;
+  T = LineTables();
+  T.n = n;
+  T.r = r;
+  T.p = p;
+  T.cyclic = cyclic;
+  if (p < 1 || p > max_lanes) return "segments out of range";
+  T.rows_small = n / p;
+  T.count_big = n % p;
+  T.rows_big = T.rows_small + (T.count_big ? 1 : 0);
+  if (T.count_big == 0) T.count_big = p;  // all partitions equal
+  if (T.rows_small < 2 * r) return "partitions need at least 2r rows (n >= 2 r p)";
+  T.start.resize(p);
+  T.size.resize(p);
+  int acc = 0;
+  for (int i = 0; i < p; i++) {
+    T.size[i] = (i < T.count_big) ? T.rows_big : T.rows_small;
+    T.start[i] = acc;
+    acc += T.size[i];
+  }
+  const int nmax = T.rows_big - r;
+  T.nmax = nmax;
+
+  // ---- banded LU of the bulk block (rows from the top; Toeplitz rows) ----
+  // Work arrays Ub[j][t] = U[j][j+t] (t = 0..r), Lb[j][q] = L[j][j-q].
+  std::vector<double> Ub((size_t)nmax * (r + 1)), Lb((size_t)nmax * (r + 1), 0.0);
+  // start from D's rows
+  std::vector<double> work((size_t)nmax * (2 * r + 1));
+  for (int j = 0; j < nmax; j++)
+    for (int t = -r; t <= r; t++) work[(size_t)j * (2 * r + 1) + t + r] = A.at(t);
+  for (int j = 0; j < nmax; j++) {
+    double piv = work[(size_t)j * (2 * r + 1) + r];
+    double bscale = 0.0;
+    for (int t = -r; t <= r; t++) bscale = std::fmax(bscale, std::fabs(A.at(t)));
+    if (!(std::fabs(piv) > 1e-12 * bscale) || !std::isfinite(piv)) {
+      *singular = true;
+      return "zero pivot in a bulk block D_i";
+    }
+    for (int t = 0; t <= r; t++) Ub[(size_t)j * (r + 1) + t] = (j + t < nmax) ? work[(size_t)j * (2 * r + 1) + r + t] : 0.0;
+    for (int q = 1; q <= r && j + q < nmax; q++) {
+      // row j+q, column j: offset -q
+      double l = work[(size_t)(j + q) * (2 * r + 1) + r - q] / piv;
+      Lb[(size_t)(j + q) * (r + 1) + q] = l;
+      work[(size_t)(j + q) * (2 * r + 1) + r - q] = 0.0;
+      for (int t = 1; t <= r; t++) {
+        int off = t - q;  // column j+t seen from row j+q
+        if (off > r) continue;
+        work[(size_t)(j + q) * (2 * r + 1) + r + off] -= l * work[(size_t)j * (2 * r + 1) + r + t];
+      }
+    }
+  }
+  const int F = 2 * r + 1;
+  T.fac.assign((size_t)nmax * F, 0.0);
+  for (int j = 0; j < nmax; j++) {
+    double ip = 1.0 / Ub[(size_t)j * (r + 1)];
+    for (int q = 1; q <= r; q++) T.fac[(size_t)j * F + q - 1] = Lb[(size_t)j * (r + 1) + q];
+    T.fac[(size_t)j * F + r] = ip;
+    for (int q = 1; q <= r; q++) T.fac[(size_t)j * F + r + q] = Ub[(size_t)j * (r + 1) + q] * ip;
+  }
+  auto solveD = [&](int N, const double* b, double* y) {
+    for (int j = 0; j < N; j++) {
+      double s = b[j];
+      for (int q = 1; q <= r && j - q >= 0; q++) s -= T.fac[(size_t)j * F + q - 1] * y[j - q];
+      y[j] = s;
+    }
+    for (int j = N - 1; j >= 0; j--) {
+      double s = T.fac[(size_t)j * F + r] * y[j];
+      for (int q = 1; q <= r && j + q < N; q++) s -= T.fac[(size_t)j * F + r + q] * y[j + q];
+      y[j] = s;
+    }
+  };
+
+  // ---- S_i, R_i (Eq. 15-16) per partition ----
+  T.sr.assign((size_t)nmax * 2 * r * p, 0.0);
+  std::vector<std::vector<double>> S(p), R(p);  // [j*r + q]
+  std::vector<double> col(nmax), sol(nmax);
+  for (int i = 0; i < p; i++) {
+    const int m = T.size[i], N = m - r;
+    S[i].assign((size_t)N * r, 0.0);
+    R[i].assign((size_t)N * r, 0.0);
+    for (int q = 0; q < r; q++) {
+      // L_i[:, q]: bulk row j couples to own interface column q at offset q - r - j
+      for (int j = 0; j < N; j++) col[j] = A.at(q - r - j);
+      solveD(N, col.data(), sol.data());
+      for (int j = 0; j < N; j++) S[i][(size_t)j * r + q] = sol[j];
+      // U_i[:, q]: bulk row j couples to next interface column q at offset m + q - r - j
+      bool has_next = cyclic || i + 1 < p;
+      for (int j = 0; j < N; j++) col[j] = has_next ? A.at(m + q - r - j) : 0.0;
+      solveD(N, col.data(), sol.data());
+      for (int j = 0; j < N; j++) R[i][(size_t)j * r + q] = sol[j];
+    }
+    for (int j = 0; j < N; j++)
+      for (int q = 0; q < r; q++) {
+        T.sr[((size_t)j * 2 * r + q) * p + i] = S[i][(size_t)j * r + q];
+        T.sr[((size_t)j * 2 * r + r + q) * p + i] = R[i][(size_t)j * r + q];
+      }
+  }
+
+  // ---- b-hat assembly blocks (Eq. 21) ----
+  for (int q = 0; q < r; q++)
+    for (int e = 0; e < r; e++) {
+      T.Lt[q][e] = (e >= q) ? A.at(e - r - q) : 0.0;
+      T.Ut[q][e] = (e <= q) ? A.at(r + e - q) : 0.0;
+    }
+
+  // ---- reduced blocks (Eq. 18-20) ----
+  std::vector<Blk> W(p, Blk(r)), Lh(p, Blk(r)), Uh(p, Blk(r));
+  for (int i = 0; i < p; i++) {
+    const int im = (i + p - 1) % p;
+    const bool has_prev = cyclic || i > 0;
+    const int Nm = T.size[im] - r, N = T.size[i] - r;
+    Blk Dt(r), LRm(r), USi(r), LSm(r), URi(r);
+    for (int q = 0; q < r; q++)
+      for (int qq = 0; qq < r; qq++) Dt(q, qq) = A.at(qq - q);
+    for (int q = 0; q < r; q++)
+      for (int qq = 0; qq < r; qq++) {
+        double a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+        for (int e = 0; e < r; e++) {
+          if (has_prev) {
+            a1 += T.Lt[q][e] * R[im][(size_t)(Nm - r + e) * r + qq];
+            a3 += T.Lt[q][e] * S[im][(size_t)(Nm - r + e) * r + qq];
+          }
+          a2 += T.Ut[q][e] * S[i][(size_t)e * r + qq];
+          a4 += T.Ut[q][e] * R[i][(size_t)e * r + qq];
+        }
+        (void)N;
+        LRm(q, qq) = a1;
+        USi(q, qq) = a2;
+        LSm(q, qq) = a3;
+        URi(q, qq) = a4;
+      }
+    W[i] = Dt - LRm - USi;
+    Lh[i] = neg(LSm);
+    Uh[i] = neg(URi);
+  }
+  T.Dhat.resize((size_t)p * r * r);
+  T.Lhat.resize((size_t)p * r * r);
+  T.Uhat.resize((size_t)p * r * r);
+  for (int i = 0; i < p; i++)
+    for (int e = 0; e < r * r; e++) {
+      T.Dhat[(size_t)i * r * r + e] = W[i].a[e];
+      T.Lhat[(size_t)i * r * r + e] = Lh[i].a[e];
+      T.Uhat[(size_t)i * r * r + e] = Uh[i].a[e];
+    }
+
+  // ---- interface schedule and per-stage coefficients (Algorithms 1-4) ----
+  T.stages = build_schedule(p, cyclic);
+  const int ns = (int)T.stages.size();
+  if (ns > kMaxStages && max_lanes <= kMaxLanes) return "interface schedule too long";
+  const int rr = r * r;
+  T.coef.assign((size_t)ns * 3 * rr * p, 0.0);
+  T.src.assign((size_t)ns * 2 * p, 0);
+  T.stage_has_c.assign(ns, 0);
+  auto put = [&](int st, int mat, int i, const Blk& b) {
+    for (int e = 0; e < rr; e++) T.coef[((size_t)(st * 3 + mat) * rr + e) * p + i] = b.a[e];
+  };
+  for (int st = 0; st < ns; st++)
+    for (int i = 0; i < p; i++) {
+      put(st, 0, i, Blk::eye(r));
+      T.src[(size_t)(st * 2 + 0) * p + i] = i;
+      T.src[(size_t)(st * 2 + 1) * p + i] = i;
+    }
+  for (int st = 0; st < ns; st++) {
+    const Stage S_ = T.stages[st];
+    const int s = S_.s, na = S_.na;
+    Blk Wi(r);
+    if (S_.type == kDetach) {
+      T.detach_steps++;
+      T.detached_rows += s;
+      std::vector<Blk> W2 = W, L2 = Lh, U2 = Uh;
+      for (int i = na - s; i < na; i++) {  // receives from detached row i + s
+        const int j = i + s;
+        if (!inv(W[j], Wi)) { *singular = true; return "singular interface block (detach)"; }
+        Blk KP = Uh[i] * Wi;
+        W2[i] = W[i] - KP * Lh[j];
+        U2[i] = neg(KP * Uh[j]);
+        put(st, 2, i, KP);
+        T.src[(size_t)(st * 2 + 1) * p + i] = j;
+      }
+      for (int i = 0; i < s; i++) {  // receives from detached row i + na
+        const int j = i + na;
+        if (!inv(W[j], Wi)) { *singular = true; return "singular interface block (detach)"; }
+        Blk KM = Lh[i] * Wi;
+        W2[i] = W2[i] - KM * Uh[j];
+        L2[i] = neg(KM * Lh[j]);
+        put(st, 1, i, KM);
+        T.src[(size_t)(st * 2 + 0) * p + i] = j;
+      }
+      W = W2;
+      Lh = L2;
+      Uh = U2;
+    } else if (S_.type == kPcr) {
+      T.pcr_steps++;
+      std::vector<Blk> W2 = W, L2 = Lh, U2 = Uh;
+      for (int i = 0; i < na; i++) {
+        int jp, jm;
+        bool hp = true, hm = true;
+        if (cyclic) {
+          jp = (i + s) % na;
+          jm = (i - s + na) % na;
+        } else {
+          jp = i + s;
+          jm = i - s;
+          hp = jp < na;
+          hm = jm >= 0;
+        }
+        Blk KP(r), KM(r);
+        Blk acc = W[i];
+        if (hp) {
+          if (!inv(W[jp], Wi)) { *singular = true; return "singular interface block (PCR)"; }
+          KP = Uh[i] * Wi;
+          acc = acc - KP * Lh[jp];
+          U2[i] = neg(KP * Uh[jp]);
+          T.src[(size_t)(st * 2 + 1) * p + i] = jp;
+        } else {
+          U2[i] = Blk(r);
+        }
+        if (hm) {
+          if (!inv(W[jm], Wi)) { *singular = true; return "singular interface block (PCR)"; }
+          KM = Lh[i] * Wi;
+          acc = acc - KM * Uh[jm];
+          L2[i] = neg(KM * Lh[jm]);
+          T.src[(size_t)(st * 2 + 0) * p + i] = jm;
+        } else {
+          L2[i] = Blk(r);
+        }
+        W2[i] = acc;
+        put(st, 1, i, KM);
+        put(st, 2, i, KP);
+      }
+      W = W2;
+      Lh = L2;
+      Uh = U2;
+    } else if (S_.type == kFinal) {
+      T.stage_has_c[st] = 1;
+      for (int i = 0; i < na; i++) {
+        // Cyclic: after the last PCR step every sub-system is one row whose
+        // L-hat and U-hat couple the row to itself, so the block to invert is
+        // W + L-hat + U-hat (this also covers p = 1 and p = 2).
+        Blk M = cyclic ? (W[i] + Lh[i] + Uh[i]) : W[i];
+        const double sc = std::fmax(maxabs(W[i]), std::fmax(maxabs(Lh[i]), maxabs(Uh[i])));
+        if (!inv(M, Wi, sc)) { *singular = true; return "singular interface block (final)"; }
+        put(st, 0, i, Wi);
+      }
+    } else {  // kReattach: rows na .. na+s-1, neighbours j - s and j - na
+      T.stage_has_c[st] = 1;
+      for (int j = na; j < na + s; j++) {
+        if (!inv(W[j], Wi)) { *singular = true; return "singular interface block (reattach)"; }
+        put(st, 0, j, Wi);
+        put(st, 1, j, Wi * Lh[j]);
+        put(st, 2, j, Wi * Uh[j]);
+        T.src[(size_t)(st * 2 + 0) * p + j] = j - s;
+        T.src[(size_t)(st * 2 + 1) * p + j] = j - na;
+      }
+    }
+  }
+  for (double v : T.coef)
+    if (!std::isfinite(v)) {
+      *singular = true;
+      return "non-finite interface coefficient";
+    }
+  for (double v : T.sr)
+    if (!std::isfinite(v)) {
+      *singular = true;
+      return "non-finite S/R entry";
+    }
+  return "";
+}
+
+}  // namespace cbs

@@ -1,0 +1,132 @@
+"""Torch-facing wrapper over the C-ABI: builds a cbs_desc and passes pointers.
+
+Tensors are (nz, ny, nx) C-contiguous (x fastest), on the current CUDA
+device.  Nothing here computes: every step of a solve runs in libcbs.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import abi
+
+_PREC = {"fp64": abi.CBS_FP64, "fp32": abi.CBS_FP32, "fp32_refine": abi.CBS_FP32_REFINE}
+_DT = {torch.float64: abi.CBS_DTYPE_F64, torch.float32: abi.CBS_DTYPE_F32}
+
+
+def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 1.0, segments: int = 0,
+              precision: str = "fp64", sweeps: int = 1, in_dtype=torch.float64, out_dtype=None,
+              cyclic: bool = True, bands_ptr: int | None = None) -> abi.cbs_desc:
+    """Descriptor for lines along `direction` of a (nz, ny, nx) field.
+
+    lhs: (alpha,) tridiagonal or (alpha, beta) pentadiagonal Toeplitz bands
+    (diagonal 1), or "variable" with bands_ptr pointing at a per-point alpha
+    field.  rhs: None (input is b) or Lele coefficients (c_1, .., c_K) of the
+    periodic central stencil with spacing h.
+    """
+    nz, ny, nx = (int(s) for s in shape_zyx)
+    d = abi.cbs_desc()
+    d.dims[0], d.dims[1], d.dims[2] = nx, ny, nz
+    d.direction = int(direction)
+    if lhs == "variable":
+        d.bandwidth = 3
+        d.lhs_kind = abi.CBS_LHS_VARIABLE
+        d.bands = bands_ptr
+    else:
+        lhs = tuple(lhs)
+        d.bandwidth = 2 * len(lhs) + 1
+        d.lhs_kind = abi.CBS_LHS_TOEPLITZ
+        d.alpha = float(lhs[0])
+        d.beta = float(lhs[1]) if len(lhs) > 1 else 0.0
+    d.cyclic = int(bool(cyclic))
+    if rhs is None:
+        d.rhs_kind = abi.CBS_RHS_NONE
+        d.rhs_terms = 0
+    else:
+        d.rhs_kind = abi.CBS_RHS_CENTRAL
+        d.rhs_terms = len(rhs)
+        for q, c in enumerate(rhs):
+            d.rhs_coef[q] = float(c)
+    d.h = float(h)
+    d.segments = int(segments)
+    d.precision = _PREC[precision]
+    d.refine_sweeps = int(sweeps)
+    d.in_dtype = _DT[in_dtype]
+    if out_dtype is None:
+        out_dtype = torch.float64 if precision != "fp32" else in_dtype
+    d.out_dtype = _DT[out_dtype]
+    return d
+
+
+class Plan:
+    """A pre-factorised solver for one (shape, direction, operator, precision)."""
+
+    def __init__(self, shape_zyx, direction: int, **kw):
+        self.shape = tuple(int(s) for s in shape_zyx)
+        self.direction = int(direction)
+        self.in_dtype = kw.get("in_dtype", torch.float64)
+        prec = kw.get("precision", "fp64")
+        self.out_dtype = kw.get("out_dtype") or (torch.float64 if prec != "fp32" else self.in_dtype)
+        self.desc = make_desc(self.shape, direction, **kw)
+        self.handle = abi.cbs_plan_create(self.desc)
+
+    def info(self) -> dict:
+        return abi.cbs_plan_info_get(self.handle)
+
+    def solve(self, inp: torch.Tensor, out: torch.Tensor | None = None,
+              stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        if inp.shape != self.shape or inp.dtype != self.in_dtype or not inp.is_contiguous() or not inp.is_cuda:
+            raise ValueError("input must be a contiguous CUDA tensor of shape %s and dtype %s"
+                             % (self.shape, self.in_dtype))
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.out_dtype, device=inp.device)
+        s = stream if stream is not None else torch.cuda.current_stream(inp.device)
+        abi.cbs_solve(self.handle, inp.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def status(self) -> int:
+        return abi.cbs_status_poll(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.cbs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A ragged batch of independent problems solved by one persistent launch.
+
+    specs: list of (shape_zyx, direction, kwargs for make_desc).  FP64 input
+    and output, Toeplitz bands, precision "fp64" or "fp32_refine".
+    """
+
+    def __init__(self, specs):
+        self.shapes = [tuple(int(v) for v in sh) for sh, _, _ in specs]
+        descs = [make_desc(sh, d, **kw) for sh, d, kw in specs]
+        self.handle = abi.cbs_batch_create(descs)
+
+    def solve(self, ins, outs=None, stream: torch.cuda.Stream | None = None):
+        if outs is None:
+            outs = [torch.empty_like(x) for x in ins]
+        for x, y, sh in zip(ins, outs, self.shapes):
+            if x.shape != sh or y.shape != sh or x.dtype != torch.float64 or not x.is_contiguous():
+                raise ValueError("batch inputs/outputs must be contiguous FP64 tensors of the planned shapes")
+        s = stream if stream is not None else torch.cuda.current_stream(ins[0].device)
+        abi.cbs_batch_solve(self.handle, [x.data_ptr() for x in ins], [y.data_ptr() for y in outs], s.cuda_stream)
+        return outs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.cbs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

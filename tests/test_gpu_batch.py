@@ -1,0 +1,97 @@
+"""GPU parity of the ragged batch (one persistent launch) and its CUDA-graph
+capture, against the FP64 oracle problem by problem."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2101_02286_gb300 import abi
+from paper_2101_02286_gb300 import workloads as W
+from paper_2101_02286_gb300.solver import Batch
+
+pytestmark = pytest.mark.gpu
+SCH = {"tri6": W.LELE6_TRI, "penta10": W.PENTA10}
+
+
+def _specs(items):
+    specs = []
+    for it in items:
+        n = it.shape_zyx[2 - it.direction]
+        sch = SCH[it.scheme]
+        specs.append((it.shape_zyx, it.direction,
+                      dict(lhs=sch["lhs"], rhs=sch["rhs"], h=W.grid_spacing(n), precision=it.precision,
+                           sweeps=2 if (it.scheme == "penta10" and it.precision == "fp32_refine") else 1)))
+    return specs
+
+
+def _ref(it, f):
+    n = it.shape_zyx[2 - it.direction]
+    sch = SCH[it.scheme]
+    return oracle.derivative(f, sch["lhs"], sch["rhs"], W.grid_spacing(n), axis=2 - it.direction)
+
+
+def test_ragged_batch_small(cuda):
+    items = W.ragged_batch(count=24, seed=123, sizes=(32, 48, 64, 96))
+    b = Batch(_specs(items))
+    ins = [torch.from_numpy(it.f).cuda() for it in items]
+    outs = b.solve(ins)
+    assert abi.cbs_last_launch_count() == 1
+    torch.cuda.synchronize()
+    for it, y in zip(items, outs):
+        assert oracle.rel_err(y.cpu().numpy(), _ref(it, it.f)) < 1e-12, it
+    b.close()
+
+
+def test_ragged_batch_cuda_graph(cuda):
+    items = W.ragged_batch(count=16, seed=321, sizes=(32, 64, 128))
+    b = Batch(_specs(items))
+    ins = [torch.from_numpy(it.f).cuda() for it in items]
+    outs = [torch.empty_like(x) for x in ins]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.solve(ins, outs, s)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.solve(ins, outs)
+    # new data in the same buffers, then replay twice
+    rng = np.random.default_rng(5)
+    fresh = [rng.uniform(-1, 1, size=it.shape_zyx) for it in items]
+    for x, f in zip(ins, fresh):
+        x.copy_(torch.from_numpy(f))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    for it, f, y in zip(items, fresh, outs):
+        assert oracle.rel_err(y.cpu().numpy(), _ref(it, f)) < 1e-12
+    b.close()
+
+
+def test_batch_rejects_unsupported(cuda):
+    from paper_2101_02286_gb300.solver import make_desc
+    d = make_desc((4, 4, 64), 0, lhs=(1 / 3,), precision="fp32", in_dtype=torch.float32)
+    with pytest.raises(abi.CbsError):
+        abi.cbs_batch_create([d])
+
+
+@pytest.mark.slow
+def test_ragged_batch_full_workload_sampled(cuda):
+    # the 48-grid ragged batch (sizes up to 384 per axis), sampled lines
+    items = W.ragged_batch()
+    b = Batch(_specs(items))
+    ins = [torch.from_numpy(it.f).cuda() for it in items]
+    outs = b.solve(ins)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for it, y in zip(items, outs):
+        ax = 2 - it.direction
+        fl = np.moveaxis(it.f, ax, -1)
+        yl = np.moveaxis(y.cpu().numpy(), ax, -1)
+        i0 = rng.integers(0, fl.shape[0], 4)
+        i1 = rng.integers(0, fl.shape[1], 4)
+        n = fl.shape[-1]
+        sch = SCH[it.scheme]
+        ref = oracle.derivative(fl[i0, i1], sch["lhs"], sch["rhs"], W.grid_spacing(n))
+        assert oracle.rel_err(yl[i0, i1], ref) < 1e-12
+    b.close()

@@ -1,0 +1,136 @@
+"""GPU parity of the on-chip line kernel against the FP64 oracle.
+
+Every case feeds the same seeded input to both sides and compares the whole
+output element by element (norm-wise infinity relative error):
+  FP64 and FP32 + refinement: <= 1e-12;  unrefined FP32: <= 2e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2101_02286_gb300 import abi
+from paper_2101_02286_gb300 import workloads as W
+from paper_2101_02286_gb300.solver import Plan
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32_refine": 1e-12, "fp32": 2e-5}
+SCHEMES = {"tri6": W.LELE6_TRI, "penta10": W.PENTA10}
+
+
+def gpu_derivative(f, direction, scheme, precision="fp64", segments=0, sweeps=1, in_dtype=torch.float64,
+                   rhs=True, out_dtype=None):
+    n = f.shape[2 - direction]
+    sch = SCHEMES[scheme]
+    plan = Plan(f.shape, direction, lhs=sch["lhs"], rhs=sch["rhs"] if rhs else None, h=W.grid_spacing(n),
+                segments=segments, precision=precision, sweeps=sweeps, in_dtype=in_dtype, out_dtype=out_dtype)
+    x = torch.from_numpy(np.ascontiguousarray(f)).to("cuda", in_dtype)
+    y = plan.solve(x)
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert plan.status() == 0
+    plan.close()
+    return y.double().cpu().numpy(), info
+
+
+def oracle_derivative(f, direction, scheme, rhs=True):
+    sch = SCHEMES[scheme]
+    n = f.shape[2 - direction]
+    if rhs:
+        return oracle.derivative(f, sch["lhs"], sch["rhs"], W.grid_spacing(n), axis=2 - direction)
+    return oracle.solve_cyclic(oracle.toeplitz_bands(n, sch["lhs"]), f, axis=2 - direction)
+
+
+def test_fourier_cube_config(cuda):
+    # 64^3, 8 seeded modes, 6th-order tri along x, 4 partitions per line
+    f, modes = W.fourier_cube(64, 8)
+    got, info = gpu_derivative(f, 0, "tri6", segments=4)
+    assert info["segments"] == 4 and info["lines"] == 64 * 64
+    ref = oracle_derivative(f, 0, "tri6")
+    assert oracle.rel_err(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+@pytest.mark.parametrize("scheme", ["tri6", "penta10"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine", "fp32"])
+def test_directions_schemes_precisions(cuda, direction, scheme, precision):
+    rng = np.random.default_rng(11 + direction)
+    f = rng.uniform(-1, 1, size=(40, 48, 64))  # (nz, ny, nx): ragged-ish line counts
+    sweeps = 2 if (scheme == "penta10" and precision == "fp32_refine") else 1
+    got, _ = gpu_derivative(f, direction, scheme, precision=precision, sweeps=sweeps)
+    ref = oracle_derivative(f, direction, scheme)
+    assert oracle.rel_err(got, ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("scheme", ["tri6", "penta10"])
+@pytest.mark.parametrize("n,p", [(64, 1), (64, 2), (64, 3), (64, 5), (61, 4), (97, 7), (96, 11), (100, 13),
+                                 (128, 8), (256, 16), (250, 31), (512, 32), (384, 32), (32, 8), (20, 5)])
+def test_segment_counts_and_ragged(cuda, scheme, n, p):
+    r = len(SCHEMES[scheme]["lhs"])
+    if n < 2 * r * p or (n + p - 1) // p > 32:
+        pytest.skip("outside the on-chip kernel's partition sizes")
+    rng = np.random.default_rng(n * 7 + p)
+    f = rng.uniform(-1, 1, size=(3, 5, n))
+    got, info = gpu_derivative(f, 0, scheme, segments=p)
+    assert info["segments"] == p
+    assert oracle.rel_err(got, oracle_derivative(f, 0, scheme)) < 1e-12
+
+
+@pytest.mark.parametrize("n,p", [(64, 3), (96, 11), (128, 8), (256, 16)])
+def test_refine_segment_counts(cuda, n, p):
+    rng = np.random.default_rng(n + p)
+    f = rng.uniform(-1, 1, size=(2, 9, n))
+    if (n + p - 1) // p > 16:
+        pytest.skip("refine kernel holds <= 16 rows per lane")
+    got, _ = gpu_derivative(f, 0, "tri6", precision="fp32_refine", segments=p)
+    assert oracle.rel_err(got, oracle_derivative(f, 0, "tri6")) < 1e-12
+
+
+@pytest.mark.parametrize("in_dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_rhs_given(cuda, in_dtype, precision):
+    # b given directly (no stencil); FP32 input is promoted exactly
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal(size=(4, 4, 256))
+    if in_dtype == torch.float32:
+        d = d.astype(np.float32).astype(np.float64)
+    got, _ = gpu_derivative(d, 0, "penta10", precision=precision, rhs=False, in_dtype=in_dtype, sweeps=2)
+    ref = oracle_derivative(d, 0, "penta10", rhs=False)
+    assert oracle.rel_err(got, ref) < 1e-12
+
+
+def test_minimal_partitions_and_single_line(cuda):
+    # n = 2 r p exactly, one line in the field
+    f = np.random.default_rng(0).uniform(-1, 1, size=(1, 1, 16))
+    got, _ = gpu_derivative(f, 0, "penta10", segments=4)
+    assert oracle.rel_err(got, oracle_derivative(f, 0, "penta10")) < 1e-12
+    got, _ = gpu_derivative(f, 0, "tri6", segments=8)
+    assert oracle.rel_err(got, oracle_derivative(f, 0, "tri6")) < 1e-12
+
+
+def test_closed_form_mode_512(cuda):
+    # the one known plane wave of the 512^3 workload, evaluated on a 512 x 8 x 8 box
+    _, modes = W.noisy_cube(8, with_mode=False)
+    n = 512
+    x = np.arange(n) * W.grid_spacing(n)
+    kx = int(modes.k[0, 0])
+    f = np.broadcast_to(modes.amp[0] * np.sin(kx * x), (8, 8, n)).copy()
+    got, _ = gpu_derivative(f, 0, "tri6", precision="fp32_refine")
+    th = 2 * np.pi * kx / n
+    kp = (14 / 9 * np.sin(th) + (1 / 18) * np.sin(2 * th)) / (1 + 2 / 3 * np.cos(th)) / W.grid_spacing(n)
+    want = modes.amp[0] * kp * np.cos(kx * x)
+    assert oracle.rel_err(got[0, 0], want) < 1e-12
+
+
+def test_invalid_arguments(cuda):
+    with pytest.raises(abi.CbsError) as e:
+        Plan((1, 1, 8), 0, lhs=(1 / 3,), segments=5)
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG
+    plan = Plan((1, 1, 64), 0, lhs=(1 / 3,))
+    x = torch.zeros((1, 1, 64), dtype=torch.float64, device="cuda")
+    with pytest.raises(abi.CbsError):
+        abi.cbs_solve(plan.handle, x.data_ptr(), x.data_ptr(), 0)  # aliasing
+    with pytest.raises(abi.CbsError):
+        abi.cbs_solve(plan.handle, 0, x.data_ptr(), 0)
+    plan.close()
