@@ -18,6 +18,7 @@ class VariableCompactDerivative(torch.autograd.Function):
         f = f.contiguous()
         alpha = alpha.contiguous()
         abi.cbs_plan_set_bands(plan.handle, alpha.data_ptr())
+        plan.bands = alpha
         x = plan.solve(f)
         ctx.save_for_backward(alpha, x)
         ctx.plan = plan
@@ -59,7 +60,10 @@ class CompactDerivative(torch.autograd.Function):
 
 def variable_plan(shape_zyx, direction: int, alpha: torch.Tensor, rhs, h: float, precision: str = "fp64",
                   segments: int = 0) -> Plan:
-    """Plan for a variable-alpha operator bound to `alpha` (rebindable)."""
+    """Plan for a variable-alpha operator bound to `alpha` (rebindable).  The
+    plan keeps a reference to `alpha`: the library reads it at every solve."""
     dt = torch.float64 if precision == "fp64" else torch.float32
-    return Plan(shape_zyx, direction, lhs="variable", bands_ptr=alpha.data_ptr(), rhs=rhs, h=h,
+    plan = Plan(shape_zyx, direction, lhs="variable", bands_ptr=alpha.data_ptr(), rhs=rhs, h=h,
                 precision=precision, segments=segments, in_dtype=dt, out_dtype=dt)
+    plan.bands = alpha
+    return plan

@@ -11,20 +11,18 @@
 
 #include "cbs_line_launch.cuh"
 #include "cbs_var.cuh"
+#include "cbs_long.cuh"
 
 using namespace cbs;
 
 namespace cbs {
-template <> cudaError_t launch_line_mode_r<0, 1>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
-template <> cudaError_t launch_line_mode_r<0, 2>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
-template <> cudaError_t launch_line_mode_r<1, 1>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
-template <> cudaError_t launch_line_mode_r<1, 2>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
-template <> cudaError_t launch_line_mode_r<2, 1>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
-template <> cudaError_t launch_line_mode_r<2, 2>(int, int, int, int, const LineArgs&, const DevLineTables&, cudaStream_t);
 cudaError_t launch_var(int M, int KS, bool adj, bool f64, const VarArgs& a, const DevLineTables& t,
                        cudaStream_t s);
 cudaError_t launch_band_grad(bool f64, const void* lam, const void* x, void* ga, int64_t nx, int64_t ny,
                              int64_t nz, int dir, cudaStream_t s);
+struct LongArgs;
+cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
+                        const DevLineTables& inner, cudaStream_t s, int* launches);
 struct BatchProblem;
 int batch_variant_host(int R, int KS, int M, int MODE);
 cudaError_t batch_configure(size_t smem);
@@ -77,6 +75,13 @@ struct cbs_plan {
   LineArgs args;
   bool var = false;
   VarArgs vargs;
+  // long lines (kind 1): segments across CTAs
+  LineTables inner;
+  DevLineTables dev_inner;
+  LongArgs largs;
+  void* lbuf = nullptr;
+  void* sbuf = nullptr;
+  int inner_threads = 0;
 };
 
 namespace {
@@ -104,6 +109,10 @@ cbs_status validate(const cbs_desc* d) {
   if (d->precision != CBS_FP32 && d->out_dtype != CBS_DTYPE_F64)
     return fail(CBS_ERR_INVALID_ARG, "FP64 and FP32_REFINE write FP64 output");
   if (!std::isfinite(d->alpha) || !std::isfinite(d->beta)) return fail(CBS_ERR_INVALID_ARG, "non-finite bands");
+  if (d->precision == CBS_FP32 && d->in_dtype != d->out_dtype)
+    return fail(CBS_ERR_UNSUPPORTED, "FP32 mode: input and output share the element type");
+  if (d->precision != CBS_FP32 && d->in_dtype == CBS_DTYPE_F32 && d->rhs_kind != CBS_RHS_NONE)
+    return fail(CBS_ERR_UNSUPPORTED, "FP32 input with an FP64 output: right-hand side given (no stencil)");
   if (d->segments < 0) return fail(CBS_ERR_INVALID_ARG, "segments must be >= 0");
   if ((d->direction == 1 && d->dims[2] > 65535) || (d->direction == 2 && d->dims[1] > 65535))
     return fail(CBS_ERR_UNSUPPORTED, "y/z lines: the remaining grid extent must be <= 65535");
@@ -129,6 +138,212 @@ int default_segments(int n, int r, int precision) {
   for (int p = kMaxLanes; p >= 1; p /= 2)
     if (n / p >= 2 * r && (n + p - 1) / p <= 32) return p;
   return 0;
+}
+
+}  // namespace
+
+namespace {
+// Fill the kernel-side tables of plan tables T (fac, S/R, b-hat blocks,
+// bands, interface coefficients, shared-memory tile geometry) and upload the
+// per-lane interface coefficients to a new device buffer *dbuf.
+cbs_status fill_dev_tables(DevLineTables& D, const LineTables& T, const Bands& A, const cbs_desc* d, int pw_override,
+                           void** dbuf, bool with_bulk = true) {
+  const int r = T.r, F = 2 * r + 1, p = T.p;
+  std::memset(&D, 0, sizeof(D));
+  if (with_bulk && T.nmax > kMaxBulk) return fail(CBS_ERR_UNSUPPORTED, "partitions too long");
+  for (int j = 0; j < T.nmax && with_bulk; j++)
+    for (int c = 0; c < F; c++) {
+      D.fac[j * F + c] = T.fac[(size_t)j * F + c];
+      D.facF[j * F + c] = (float)T.fac[(size_t)j * F + c];
+    }
+  for (int j = 0; j < T.rows_big - r && with_bulk; j++)
+    for (int c = 0; c < 2 * r; c++) {
+      D.srB[j * 2 * r + c] = T.srB[(size_t)j * 2 * r + c];
+      D.srBF[j * 2 * r + c] = (float)D.srB[j * 2 * r + c];
+    }
+  for (int j = 0; j < T.rows_small - r && with_bulk; j++)
+    for (int c = 0; c < 2 * r; c++) {
+      D.srS[j * 2 * r + c] = T.srS[(size_t)j * 2 * r + c];
+      D.srSF[j * 2 * r + c] = (float)D.srS[j * 2 * r + c];
+    }
+  for (int q = 0; q < r; q++)
+    for (int e = 0; e < r; e++) {
+      D.Lt[q][e] = T.Lt[q][e];
+      D.Ut[q][e] = T.Ut[q][e];
+      D.LtF[q][e] = (float)T.Lt[q][e];
+      D.UtF[q][e] = (float)T.Ut[q][e];
+    }
+  const int ns = (int)T.stages.size();
+  // uniform interface: p a power of two, cyclic, only PCR / final stages and
+  // identical blocks on every lane (then sources are (i -+ s) mod p)
+  {
+    const int rr = r * r;
+    bool uni = T.cyclic && (p & (p - 1)) == 0 && ns <= kMaxStages;
+    for (int st = 0; st < ns && uni; st++) {
+      const Stage& S_ = T.stages[st];
+      if (S_.type != kPcr && S_.type != kFinal) uni = false;
+      for (int i = 0; i < p && uni; i++) {
+        for (int m = 0; m < 3 * rr; m++)
+          if (T.coef[((size_t)st * 3 * rr + m) * p + i] != T.coef[((size_t)st * 3 * rr + m) * p]) uni = false;
+        if (S_.type == kPcr) {
+          if (T.src[(size_t)(st * 2 + 0) * p + i] != ((i - S_.s) & (p - 1)) ||
+              T.src[(size_t)(st * 2 + 1) * p + i] != ((i + S_.s) & (p - 1)))
+            uni = false;
+        }
+      }
+    }
+    D.uniform = uni ? 1 : 0;
+    if (uni)
+      for (int st = 0; st < ns; st++) {
+        D.ustage_s[st] = (T.stages[st].type == kPcr) ? T.stages[st].s : 0;
+        for (int m = 0; m < 3 * rr; m++) {
+          D.ucoef[st][m] = T.coef[((size_t)st * 3 * rr + m) * p];
+          D.ucoefF[st][m] = (float)D.ucoef[st][m];
+        }
+      }
+  }
+  for (int k = 0; k < F; k++) {
+    D.band[k] = A.v[k];
+    D.bandHi[k] = (float)A.v[k];
+    D.bandLo[k] = (float)(A.v[k] - (double)D.bandHi[k]);
+  }
+  D.n = T.n;
+  D.r = r;
+  D.p = p;
+  D.pw = pw_override ? pw_override : next_pow2(p);
+  D.rows_big = T.rows_big;
+  D.rows_small = T.rows_small;
+  D.count_big = T.count_big;
+  D.nstage = ns;
+  D.cyclic = T.cyclic ? 1 : 0;
+  for (int st = 0; st < ns && st < kMaxStages; st++) D.stage_has_c[st] = T.stage_has_c[st];
+  // shared-memory tile geometry (see tile_copy): sp odd, lsz chosen so the
+  // lanes of different lines in one wavefront hit different banks
+  {
+    const bool wide = (d->in_dtype == CBS_DTYPE_F64 || d->out_dtype == CBS_DTYPE_F64);
+    const int mod = wide ? 16 : 32;
+    const int pw = D.pw;
+    D.sp = pw + 1;
+    const int target = (pw < mod) ? pw : 1;
+    int lsz = T.rows_big * D.sp;
+    while (lsz % mod != target % mod) lsz++;
+    D.lsz = lsz;
+    D.bound = T.count_big * T.rows_big;
+    auto mag = [](int dd) -> unsigned {
+      return dd <= 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + (unsigned)dd - 1) / (unsigned)dd);
+    };
+    D.mag_b = mag(T.rows_big);
+    D.mag_s = mag(T.rows_small);
+    D.mag_n = mag(T.n);
+    D.rows_lg = -1;
+    if (T.count_big == p && (T.rows_big & (T.rows_big - 1)) == 0) {
+      int lg = 0;
+      while ((1 << lg) < T.rows_big) lg++;
+      D.rows_lg = lg;
+    }
+  }
+  const size_t ncoef = T.coef.size(), nsrc = T.src.size();
+  const size_t bytes = ncoef * sizeof(double) + ncoef * sizeof(float) + nsrc * sizeof(int) + 256;
+  std::vector<float> coefF(T.coef.begin(), T.coef.end());
+  cudaError_t e = cudaMalloc(dbuf, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan tables)");
+  char* base = (char*)*dbuf;
+  e = cudaMemcpy(base, T.coef.data(), ncoef * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + ncoef * sizeof(double), coefF.data(), ncoef * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + ncoef * (sizeof(double) + sizeof(float)), T.src.data(), nsrc * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(*dbuf);
+    *dbuf = nullptr;
+    return cuda_fail(e, "uploading plan tables");
+  }
+  D.coef = (const double*)base;
+  D.coefF = (const float*)(base + ncoef * sizeof(double));
+  D.src = (const int*)(base + ncoef * (sizeof(double) + sizeof(float)));
+  return CBS_OK;
+}
+
+// Long lines: p segments per line, one CTA per segment (cbs_long.cu).
+cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
+  if (d->direction != 0 || d->rhs_kind != CBS_RHS_NONE || !d->cyclic || d->lhs_kind != CBS_LHS_TOEPLITZ)
+    return fail(CBS_ERR_UNSUPPORTED, "long lines: x-lines, right-hand side given, cyclic Toeplitz bands");
+  const int n = P->n, r = P->r;
+  int p = d->segments;
+  if (!p) {  // segments of about 4096 rows that divide the line
+    p = (n + 4095) / 4096;
+    while (p < n && n % p) p++;
+  }
+  if (n % p) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments must divide n");
+  const int m = n / p, N = m - r;
+  const int pin = (N + 15) / 16;
+  if (pin > 512) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments above 8192 rows (raise segments)");
+  if (N < 2 * r * pin || m < 4 * r) return fail(CBS_ERR_INVALID_ARG, "long lines: segments too short");
+  Bands A;
+  A.r = r;
+  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
+  A.v[r] = 1.0;
+  A.v[r - 1] = A.v[r + 1] = d->alpha;
+  if (r == 2) A.v[0] = A.v[4] = d->beta;
+  bool singular = false;
+  std::string msg = build_line_tables(P->host, n, A, p, true, &singular, 1 << 30);
+  if (msg.empty()) msg = build_line_tables(P->inner, N, A, pin, false, &singular, 1 << 30);
+  if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
+  // leading entries of the first r rows of D^{-1}: keep K with a tail below
+  // 2^-60 of each row's l1 norm (all K = N when the rows do not decay)
+  std::vector<double> Gfull = bulk_inverse_rows(P->host, N, r);
+  int K = 1;
+  for (int q = 0; q < r; q++) {
+    double tot = 0.0;
+    for (int j = 0; j < N; j++) tot += std::fabs(Gfull[(size_t)q * N + j]);
+    double tail = 0.0;
+    int kq = N;
+    for (int j = N - 1; j >= 0; j--) {
+      tail += std::fabs(Gfull[(size_t)q * N + j]);
+      if (tail > std::ldexp(tot, -60)) {
+        kq = j + 1;
+        break;
+      }
+    }
+    K = std::max(K, kq);
+  }
+  std::vector<double> G((size_t)r * K);
+  for (int q = 0; q < r; q++)
+    for (int j = 0; j < K; j++) G[(size_t)q * K + j] = Gfull[(size_t)q * N + j];
+  cbs_status st = fill_dev_tables(P->dev, P->host, A, d, 0, &P->dbuf, false);
+  if (st) return st;
+  const int threads = ((pin + 31) / 32) * 32;
+  st = fill_dev_tables(P->dev_inner, P->inner, A, d, threads, &P->lbuf, true);
+  if (st) return st;
+  // scratch: yb, cc (2r per segment), xt (r per segment), then G
+  const size_t nseg = (size_t)P->nlines * p;
+  const size_t bytes = (nseg * (5 * r) + G.size()) * sizeof(double);
+  cudaError_t e = cudaMalloc(&P->sbuf, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&P->dstatus, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
+  double* sb = (double*)P->sbuf;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sb + nseg * 5 * r, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "long-line scratch");
+  LongArgs& a = P->largs;
+  std::memset(&a, 0, sizeof(a));
+  a.yb = sb;
+  a.cc = sb + nseg * 2 * r;
+  a.xt = sb + nseg * 4 * r;
+  a.G = sb + nseg * 5 * r;
+  a.K = K;
+  a.lines = P->nlines;
+  a.n = n;
+  a.p = p;
+  a.m = m;
+  a.r = r;
+  a.sweeps = d->refine_sweeps;
+  for (int k = 0; k < 2 * kMaxR + 1; k++) a.band[k] = A.v[k];
+  P->kind = 1;
+  P->M = 16;
+  P->inner_threads = threads;
+  return CBS_OK;
 }
 
 }  // namespace
@@ -223,6 +438,25 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
       p = default_segments(P->n, P->r, d->precision);
     }
   }
+  {
+    const int maxM0 = (d->precision == CBS_FP32_REFINE || P->var) ? 16 : 32;
+    // a line whose partitions do not fit one lane's registers goes to the
+    // segment-per-CTA path
+    const bool use_long = !P->var && (d->segments > kMaxLanes || p < 1 || (P->n + p - 1) / p > maxM0);
+    if (use_long) {
+      st = create_long(P, d);
+      if (st) {
+        if (P->dbuf) cudaFree(P->dbuf);
+        if (P->lbuf) cudaFree(P->lbuf);
+        if (P->sbuf) cudaFree(P->sbuf);
+        if (P->dstatus) cudaFree(P->dstatus);
+        delete P;
+        return st;
+      }
+      *out = P;
+      return CBS_OK;
+    }
+  }
   if (p < 1) {
     delete P;
     return fail(CBS_ERR_UNSUPPORTED, "line too long for the on-chip kernel");
@@ -260,126 +494,17 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   if (d->rhs_kind == CBS_RHS_CENTRAL) P->ks = d->rhs_terms <= 2 ? 2 : 3;
 
   // ---- device tables ----
-  DevLineTables& D = P->dev;
-  std::memset(&D, 0, sizeof(D));
-  const int r = P->r, F = 2 * r + 1;
-  for (int j = 0; j < T.nmax; j++)
-    for (int c = 0; c < F; c++) {
-      D.fac[j * F + c] = T.fac[(size_t)j * F + c];
-      D.facF[j * F + c] = (float)T.fac[(size_t)j * F + c];
-    }
-  const int iB = 0, iS = (T.count_big < p) ? T.count_big : 0;
-  for (int j = 0; j < T.rows_big - r; j++)
-    for (int c = 0; c < 2 * r; c++) {
-      D.srB[j * 2 * r + c] = T.sr[((size_t)j * 2 * r + c) * p + iB];
-      D.srBF[j * 2 * r + c] = (float)D.srB[j * 2 * r + c];
-    }
-  for (int j = 0; j < T.rows_small - r; j++)
-    for (int c = 0; c < 2 * r; c++) {
-      D.srS[j * 2 * r + c] = T.sr[((size_t)j * 2 * r + c) * p + iS];
-      D.srSF[j * 2 * r + c] = (float)D.srS[j * 2 * r + c];
-    }
-  for (int q = 0; q < r; q++)
-    for (int e = 0; e < r; e++) {
-      D.Lt[q][e] = T.Lt[q][e];
-      D.Ut[q][e] = T.Ut[q][e];
-      D.LtF[q][e] = (float)T.Lt[q][e];
-      D.UtF[q][e] = (float)T.Ut[q][e];
-    }
-  // uniform interface: p a power of two, cyclic, only PCR / final stages and
-  // identical blocks on every lane (then sources are (i -+ s) mod p)
-  {
-    const int rr = r * r, ns = (int)T.stages.size();
-    bool uni = d->cyclic && (p & (p - 1)) == 0;
-    for (int st = 0; st < ns && uni; st++) {
-      const Stage& S_ = T.stages[st];
-      if (S_.type != kPcr && S_.type != kFinal) uni = false;
-      for (int i = 0; i < p && uni; i++) {
-        for (int m = 0; m < 3 * rr; m++)
-          if (T.coef[((size_t)st * 3 * rr + m) * p + i] != T.coef[((size_t)st * 3 * rr + m) * p]) uni = false;
-        if (S_.type == kPcr) {
-          if (T.src[(size_t)(st * 2 + 0) * p + i] != ((i - S_.s) & (p - 1)) ||
-              T.src[(size_t)(st * 2 + 1) * p + i] != ((i + S_.s) & (p - 1)))
-            uni = false;
-        }
-      }
-    }
-    D.uniform = uni ? 1 : 0;
-    if (uni)
-      for (int st = 0; st < ns; st++) {
-        D.ustage_s[st] = (T.stages[st].type == kPcr) ? T.stages[st].s : 0;
-        for (int m = 0; m < 3 * rr; m++) {
-          D.ucoef[st][m] = T.coef[((size_t)st * 3 * rr + m) * p];
-          D.ucoefF[st][m] = (float)D.ucoef[st][m];
-        }
-      }
-  }
-  for (int k = 0; k < F; k++) {
-    D.band[k] = A.v[k];
-    D.bandHi[k] = (float)A.v[k];
-    D.bandLo[k] = (float)(A.v[k] - (double)D.bandHi[k]);
-  }
-  D.n = P->n;
-  D.r = r;
-  D.p = p;
-  D.pw = next_pow2(p);
-  D.rows_big = T.rows_big;
-  D.rows_small = T.rows_small;
-  D.count_big = T.count_big;
-  // shared-memory tile geometry (see tile_copy): sp odd, lsz chosen so the
-  // lanes of different lines in one wavefront hit different banks
-  {
-    const bool wide = (d->in_dtype == CBS_DTYPE_F64 || d->out_dtype == CBS_DTYPE_F64);
-    const int mod = wide ? 16 : 32;
-    const int pw = next_pow2(p);
-    D.sp = pw + 1;
-    const int target = (pw < mod) ? pw : 1;
-    int lsz = T.rows_big * D.sp;
-    while (lsz % mod != target % mod) lsz++;
-    D.lsz = lsz;
-    D.bound = T.count_big * T.rows_big;
-    auto mag = [](int dd) -> unsigned {
-      return dd <= 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + (unsigned)dd - 1) / (unsigned)dd);
-    };
-    D.mag_b = mag(T.rows_big);
-    D.mag_s = mag(T.rows_small);
-    D.mag_n = mag(P->n);
-    D.rows_lg = -1;
-    if (T.count_big == p && (T.rows_big & (T.rows_big - 1)) == 0) {
-      int lg = 0;
-      while ((1 << lg) < T.rows_big) lg++;
-      D.rows_lg = lg;
-    }
-  }
-  D.nstage = (int)T.stages.size();
-  D.cyclic = d->cyclic;
-  for (int s = 0; s < D.nstage; s++) D.stage_has_c[s] = T.stage_has_c[s];
-  const size_t ncoef = T.coef.size(), nsrc = T.src.size();
-  const size_t bytes = ncoef * sizeof(double) + ncoef * sizeof(float) + nsrc * sizeof(int) + 256;
-  std::vector<float> coefF(T.coef.begin(), T.coef.end());
-  cudaError_t e = cudaMalloc(&P->dbuf, bytes);
-  if (e != cudaSuccess) {
+  st = fill_dev_tables(P->dev, T, A, d, 0, &P->dbuf);
+  if (st) {
     delete P;
-    return cuda_fail(e, "cudaMalloc(plan tables)");
+    return st;
   }
-  char* base = (char*)P->dbuf;
-  e = cudaMemcpy(base, T.coef.data(), ncoef * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(base + ncoef * sizeof(double), coefF.data(), ncoef * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(base + ncoef * (sizeof(double) + sizeof(float)), T.src.data(), nsrc * sizeof(int),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&P->dstatus, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
-  if (e != cudaSuccess) {
+  if (cudaMalloc(&P->dstatus, sizeof(int)) != cudaSuccess || cudaMemset(P->dstatus, 0, sizeof(int)) != cudaSuccess) {
     cudaFree(P->dbuf);
     if (P->dstatus) cudaFree(P->dstatus);
     delete P;
-    return cuda_fail(e, "uploading plan tables");
+    return fail(CBS_ERR_CUDA, "status word allocation");
   }
-  D.coef = (const double*)base;
-  D.coefF = (const float*)(base + ncoef * sizeof(double));
-  D.src = (const int*)(base + ncoef * (sizeof(double) + sizeof(float)));
 
   // ---- kernel arguments that do not change between solves ----
   LineArgs& a = P->args;
@@ -432,6 +557,8 @@ cbs_status cbs_plan_destroy(cbs_plan* P) {
   if (!P) return fail(CBS_ERR_INVALID_ARG, "null plan");
   cudaDeviceSynchronize();
   if (P->dbuf) cudaFree(P->dbuf);
+  if (P->lbuf) cudaFree(P->lbuf);
+  if (P->sbuf) cudaFree(P->sbuf);
   if (P->dstatus) cudaFree(P->dstatus);
   delete P;
   return CBS_OK;
@@ -451,7 +578,7 @@ cbs_status cbs_plan_info_get(const cbs_plan* P, cbs_plan_info* info) {
   info->detached_rows = P->host.detached_rows;
   info->stage_count = (int32_t)P->host.stages.size();
   info->kernel = P->kind;
-  info->threads_per_line = P->dev.pw;
+  info->threads_per_line = P->kind == 1 ? P->inner_threads : P->dev.pw;
   info->lines = P->nlines;
   return CBS_OK;
 }
@@ -471,10 +598,21 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     g_launches = 1;
     return CBS_OK;
   }
+  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  if (P->kind == 1) {
+    LongArgs la = P->largs;
+    la.in = in;
+    la.out = out;
+    int launches = 0;
+    cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->dev,
+                                P->dev_inner, (cudaStream_t)stream, &launches);
+    if (e != cudaSuccess) return cuda_fail(e, "long-line kernel launch");
+    g_launches = launches;
+    return CBS_OK;
+  }
   LineArgs a = P->args;
   a.in = in;
   a.out = out;
-  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaErrorInvalidValue;
   const int R = P->r;
@@ -483,6 +621,7 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
   else if (mode == kModeF32) e = (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
   else e = (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
 #undef CBS_L
+  if (e == cudaErrorNotSupported) return fail(CBS_ERR_UNSUPPORTED, "no kernel variant for these element types");
   if (e != cudaSuccess) return cuda_fail(e, "line kernel launch");
   g_launches = 1;
   return CBS_OK;
@@ -508,6 +647,7 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
     g_launches = 1;
     return CBS_OK;
   }
+  if (P->kind != 0) return fail(CBS_ERR_UNSUPPORTED, "transpose solve of long-line plans");
   // Toeplitz: A is symmetric, and on a periodic grid A^{-1} and the central
   // stencil S are both circulant, so S^T A^{-T} g = A^{-1} (S^T g) = A^{-1} (-S g):
   // the same line kernel with negated stencil weights.
@@ -599,6 +739,10 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       return fail(st, msg);
     }
     B->plans.push_back(P);
+    if (P->kind != 0) {
+      cbs_batch_destroy(B);
+      return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": lines too long for one warp");
+    }
     const int mode = d.precision == CBS_FP64 ? kModeF64 : kModeRefine;
     const int variant = batch_variant_host(P->r, P->ks, P->M, mode);
     if (variant < 0) {

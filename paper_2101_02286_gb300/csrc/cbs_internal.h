@@ -42,9 +42,11 @@ struct LineTables {
   // fac[j*(2r+1) + q-1] = l_q (q=1..r), fac[j*(2r+1) + r] = 1/pivot,
   // fac[j*(2r+1) + r + q] = u_q / pivot (q=1..r).
   std::vector<double> fac;
-  // S_i = D_i^{-1} L_i and R_i = D_i^{-1} U_i, per partition, layout
-  // sr[(j * 2r + c) * P + i], c < r: S column c, c >= r: R column c - r.
-  std::vector<double> sr;
+  // S_i = D_i^{-1} L_i and R_i = D_i^{-1} U_i for a partition of rows_big
+  // (srB) and of rows_small (srS) rows, layout [j * 2r + c], c < r: S column
+  // c, c >= r: R column c - r (cyclic; an acyclic system's last partition has
+  // R = 0, which the kernels apply themselves).
+  std::vector<double> srB, srS;
   // b-hat assembly blocks (Eq. 21): Lt[q][e] multiplies y_{i-1}[N_{i-1}-r+e],
   // Ut[q][e] multiplies y_i[e]; identical for all partitions (Toeplitz).
   double Lt[kMaxR][kMaxR] = {}, Ut[kMaxR][kMaxR] = {};
@@ -66,6 +68,10 @@ struct LineTables {
 // set when a pivot or interface block is zero / non-finite.
 std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool cyclic,
                               bool* singular, int max_lanes);
+
+// Rows q < nrows of D^{-1} for the bulk block of N rows of plan tables T
+// (forward/backward elimination with T.fac), row-major nrows x N.
+std::vector<double> bulk_inverse_rows(const LineTables& T, int N, int nrows);
 
 // Tables passed by value to the on-chip kernel (they live in the constant
 // bank, so uniform reads cost no load instruction).

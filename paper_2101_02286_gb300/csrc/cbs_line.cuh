@@ -225,6 +225,14 @@ __device__ __forceinline__ float sel(bool c, float a, float b) {
   return r;
 }
 
+// sel with a compile-time switch: PLAIN (partition sizes known at compile
+// time, so conditions fold away) uses the C++ conditional.
+template <bool PLAIN, typename T>
+__device__ __forceinline__ T sel2(bool c, T a, T b) {
+  if constexpr (PLAIN) return c ? a : b;
+  else return sel(c, a, b);
+}
+
 // Partition of lane i (first count_big partitions have rows_big rows).
 __device__ __forceinline__ void partition_of(const DevLineTables& t, int i, int& start, int& size) {
   if (i < t.count_big) {
@@ -236,13 +244,46 @@ __device__ __forceinline__ void partition_of(const DevLineTables& t, int i, int&
   }
 }
 
+// ------------------------------------------------- interface messages
+// The paper's sendToPartition / getFromPartition (Algorithms 1-4): value of
+// `v` held by partition `src`.  Within a line group of a warp the message is
+// a shuffle; when the partitions of one system span a whole CTA it goes
+// through a double-buffered shared-memory slot (one barrier per message; all
+// threads of the CTA must exchange in lock step).
+struct WarpXchg {
+  int pw;
+  template <typename V>
+  __device__ __forceinline__ V get(V v, int src) {
+    return __shfl_sync(kFull, v, src, pw);
+  }
+};
+struct CtaXchg {
+  unsigned long long* buf;  // 2 * blockDim.x slots
+  int flip;
+  template <typename V>
+  __device__ __forceinline__ V get(V v, int src) {
+    unsigned long long* b = buf + flip * blockDim.x;
+    flip ^= 1;
+    if constexpr (sizeof(V) == 8) {
+      b[threadIdx.x] = (unsigned long long)__double_as_longlong((double)v);
+      __syncthreads();
+      return (V)__longlong_as_double((long long)b[src]);
+    } else {
+      b[threadIdx.x] = (unsigned long long)__float_as_uint((float)v);
+      __syncthreads();
+      return (V)__uint_as_float((unsigned)b[src]);
+    }
+  }
+};
+
 // ------------------------------------------------- per-partition solve (a2-a4)
 // v[0..size) holds b of this partition on entry and x on exit.  Must be
 // called by all 32 lanes of the warp (it shuffles).  `lane_ok` marks lanes
 // that own a partition (i < p).
-template <typename T, int R, int M, typename TI>
-__device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const int i,
-                                                const bool lane_ok, const DevLineTables& t) {
+template <typename T, int R, int M, typename TI, bool FULL = false, typename X = WarpXchg>
+__device__ __forceinline__ void solve_partition(T (&v)[M], const int size_rt, const int i,
+                                                const bool lane_ok, const DevLineTables& t, X& xch) {
+  const int size = FULL ? M : size_rt;
   constexpr int F = 2 * R + 1;
   constexpr int NB = M - R;  // max bulk rows
   const int N = size - R;
@@ -280,7 +321,7 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const
   for (int e = 0; e < R; e++) {
     T val = T(0);
 #pragma unroll
-    for (int u = R; u < M; u++) val = sel(u == N + e, v[u], val);
+    for (int u = R; u < M; u++) val = sel2<FULL>(u == N + e, v[u], val);
     ylast[e] = val;
   }
   const int prev = (i == 0) ? p - 1 : i - 1;
@@ -290,7 +331,7 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const
   TI xt[R];
 #pragma unroll
   for (int e = 0; e < R; e++) {
-    const T yp = __shfl_sync(kFull, ylast[e], prev, pw);
+    const T yp = xch.get(ylast[e], prev);
     ylast[e] = yp;  // now y_{i-1}[N_{i-1} - r + e]
   }
 #pragma unroll
@@ -336,8 +377,8 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const
     TI xm[R], xp[R];
 #pragma unroll
     for (int q = 0; q < R; q++) {
-      xm[q] = __shfl_sync(kFull, xt[q], sm, pw);
-      xp[q] = __shfl_sync(kFull, xt[q], sp, pw);
+      xm[q] = xch.get(xt[q], sm);
+      xp[q] = xch.get(xt[q], sp);
     }
     TI nxt[R];
     const bool hc = t.stage_has_c[st] != 0;
@@ -363,7 +404,7 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const
   T xa[R], xb[R];
 #pragma unroll
   for (int q = 0; q < R; q++) {
-    const TI xn = __shfl_sync(kFull, xt[q], next, pw);
+    const TI xn = xch.get(xt[q], next);
     xa[q] = (T)xt[q];
     xb[q] = has_next ? (T)xn : T(0);
   }
@@ -386,11 +427,12 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size, const
 // Residual r = b - A x for this partition's rows, to FP64 accuracy, with x
 // given as an unevaluated sum xh + xl of floats and b as bh + bl.  Neighbour
 // rows of x come from the adjacent lanes.  Result rounded to FP32.
-template <int R, int M, bool XLO>
+template <int R, int M, bool XLO, bool FULL = false, typename X = WarpXchg>
 __device__ __forceinline__ void residual_df(const float (&bh)[M], const float (&bl)[M],
                                             const float (&xh)[M], const float (&xl)[M],
-                                            float (&res)[M], const int size, const int i,
-                                            const DevLineTables& t) {
+                                            float (&res)[M], const int size_rt, const int i,
+                                            const DevLineTables& t, X& xch) {
+  const int size = FULL ? M : size_rt;
   const int p = t.p, pw = t.pw;
   const int prev = (i == 0) ? p - 1 : i - 1;
   const int next = (i + 1 >= p) ? 0 : i + 1;
@@ -401,17 +443,21 @@ __device__ __forceinline__ void residual_df(const float (&bh)[M], const float (&
     float lh = 0.f, ll = 0.f;
 #pragma unroll
     for (int u = 0; u < M; u++) {
-      lh = sel(u == size - R + e, xh[u], lh);
-      ll = sel(u == size - R + e, xl[u], ll);
+      lh = sel2<FULL>(u == size - R + e, xh[u], lh);
+      ll = sel2<FULL>(u == size - R + e, xl[u], ll);
     }
-    hh_prev[e] = __shfl_sync(kFull, lh, prev, pw);
-    hh_next[e] = __shfl_sync(kFull, xh[e], next, pw);
+    hh_prev[e] = xch.get(lh, prev);
+    hh_next[e] = xch.get(xh[e], next);
     if (XLO) {
-      hl_prev[e] = __shfl_sync(kFull, ll, prev, pw);
-      hl_next[e] = __shfl_sync(kFull, xl[e], next, pw);
+      hl_prev[e] = xch.get(ll, prev);
+      hl_next[e] = xch.get(xl[e], next);
     } else {
       hl_prev[e] = 0.f;
       hl_next[e] = 0.f;
+    }
+    if (!t.cyclic) {  // acyclic system: nothing beyond its first and last rows
+      if (i == 0) hh_prev[e] = hl_prev[e] = 0.f;
+      if (i + 1 >= p) hh_next[e] = hl_next[e] = 0.f;
     }
   }
 #pragma unroll
@@ -433,8 +479,8 @@ __device__ __forceinline__ void residual_df(const float (&bh)[M], const float (&
           // rows past the end of this partition belong to the next one
 #pragma unroll
           for (int e = 0; e < R; e++) {
-            vh = sel(kk == size + e, hh_next[e], vh);
-            vl = sel(kk == size + e, hl_next[e], vl);
+            vh = sel2<FULL>(kk == size + e, hh_next[e], vh);
+            vl = sel2<FULL>(kk == size + e, hl_next[e], vl);
           }
         }
         const float bH = t.bandHi[tt + R], bL = t.bandLo[tt + R];
@@ -583,24 +629,46 @@ __device__ __forceinline__ void tile_copy(const TileRef& tr, const DevLineTables
 
 // h[idx] for a small register array and a runtime idx in [0, K), written as a
 // select chain so the array stays in registers.
-template <typename T, int K>
+template <typename T, int K, bool PLAIN = false>
 __device__ __forceinline__ T pick(const T (&h)[K], int idx) {
   T r = h[0];
 #pragma unroll
-  for (int e = 1; e < K; e++) r = sel(idx == e, h[e], r);
+  for (int e = 1; e < K; e++) r = sel2<PLAIN>(idx == e, h[e], r);
   return r;
 }
 
 // ---------------------------------------------------------------- kernel
+// Window value at row offset k + q of a lane's partition: its own rows, or
+// the upper halo once k + q runs past the partition (k, q compile-time).
+template <typename TW, int M, int KS, int KA, bool FULL>
+__device__ __forceinline__ TW window_up(const TW (&w)[M + KS], const TW (&hh)[KA], int k, int q, int size) {
+  const int kq = (k + q < M) ? k + q : M - 1;  // compile-time clamp
+  if (k + q < M) return sel2<FULL>(k + q < size, w[KS + kq], pick<TW, KA, FULL>(hh, k + q - size));
+  return pick<TW, KA, FULL>(hh, k + q - size);
+}
+
+// Split of an input element into an unevaluated FP32 pair.
+template <typename X>
+__device__ __forceinline__ f2 split_in(X x) {
+  if constexpr (sizeof(X) == 8) return split_f64((double)x);
+  else return f2{(float)x, 0.f};
+}
+
 // One tile = blockDim / pw consecutive lines starting at line L0, processed by
-// the whole CTA: copy-in, per-lane stencil + solve, copy-out.  KS: stencil
-// terms compiled in (0 = the input already is b).  Used by the per-plan
-// kernel (one tile per CTA) and by the persistent batch kernel (many tiles).
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut>
+// the whole CTA: gather the rows (+ stencil halo) of every lane's partition,
+// stencil + solve per lane, write back.  KS: stencil terms compiled in (0 =
+// the input already is b).  FULL: every partition has exactly M rows (sizes
+// known at compile time).  DIRECT: x-lines, each lane reads and writes its
+// own contiguous rows with 16-byte vector accesses (no shared memory);
+// otherwise the tile is staged through shared memory (y and z lines, and
+// x-lines with ragged partitions).  Used by the per-plan kernel (one tile per
+// CTA) and by the persistent batch kernel (many tiles per CTA).
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, bool DIRECT = false>
 __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables& t, const void* in_ptr,
                                           void* out_ptr, const int tx, const int to, unsigned char* smem_raw) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
+  using TW = typename std::conditional<DIRECT, TIn, TT>::type;  // element type of the gathered window
   constexpr int KA = KS > 0 ? KS : 1;  // halo array size (KS = 0 compiles no stencil)
   TT* S = reinterpret_cast<TT*>(smem_raw);
   const int pw = t.pw;
@@ -611,92 +679,105 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   const bool lane_ok = i < t.p;
   const bool ok = lane_ok && g < nl;
   int start = 0, size = R * 2;
-  if (lane_ok) partition_of(t, i, start, size);
+  if (FULL) {
+    start = i * M;
+    size = M;
+  } else if (lane_ok) {
+    partition_of(t, i, start, size);
+  }
   const int n = t.n;
   TT* SL = S + g * t.lsz;
+  const TIn* gin = (const TIn*)in_ptr + tr.base + (int64_t)g * n;  // DIRECT: this lane's line
+  TOut* gout = (TOut*)out_ptr + tr.base + (int64_t)g * n;
 
-  tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
-  __syncthreads();
-
-  if (MODE != kModeRefine) {
-    T v[M];
-    if (KS == 0) {
+  // ---- gather: w[KS + k] = row start + k, w[q] = row start - KS + q, hh[q] = row start + size + q
+  TW w[M + KS], hh[KA];
+  if constexpr (DIRECT) {
+    constexpr int V = 16 / sizeof(TIn);
+    if (FULL && (M % V) == 0) {
 #pragma unroll
-      for (int k = 0; k < M; k++) v[k] = (ok && k < size) ? conv<T>(SL[k * t.sp + i]) : T(0);
-    } else {
-      // a1: stencil from rows start-KS .. start+size-1+KS (halo rows of the
-      // neighbouring partitions, periodic in the line)
-      T fw[M + KS], hh[KA];
+      for (int k = 0; k < M; k += V) {
+        TIn tmp[V];
+        if (ok) V16<TIn, V>::ld(gin + start + k, tmp);
+        else {
 #pragma unroll
-      for (int q = 0; q < KS; q++) {
-        int rlo = start - KS + q;
-        rlo += (rlo < 0) ? n : 0;
-        fw[q] = ok ? conv<T>(SL[slot_of(t, rlo)]) : T(0);
-        int rhi = start + size + q;
-        rhi -= (rhi >= n) ? n : 0;
-        hh[q] = ok ? conv<T>(SL[slot_of(t, rhi)]) : T(0);
+          for (int u = 0; u < V; u++) tmp[u] = TIn(0);
+        }
+#pragma unroll
+        for (int u = 0; u < V; u++) w[KS + k + u] = tmp[u];
       }
+    } else {
 #pragma unroll
-      for (int k = 0; k < M; k++) fw[KS + k] = (ok && k < size) ? conv<T>(SL[k * t.sp + i]) : T(0);
+      for (int k = 0; k < M; k++) w[KS + k] = (ok && k < size) ? __ldg(gin + start + k) : TIn(0);
+    }
 #pragma unroll
-      for (int k = 0; k < M; k++) {
+    for (int q = 0; q < KS; q++) {
+      int rlo = start - KS + q;
+      rlo += (rlo < 0) ? n : 0;
+      w[q] = ok ? __ldg(gin + rlo) : TIn(0);
+      int rhi = start + size + q;
+      rhi -= (rhi >= n) ? n : 0;
+      hh[q] = ok ? __ldg(gin + rhi) : TIn(0);
+    }
+  } else {
+    tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < M; k++) w[KS + k] = (ok && (FULL || k < size)) ? SL[k * t.sp + i] : TT(0);
+#pragma unroll
+    for (int q = 0; q < KS; q++) {
+      int rlo = start - KS + q;
+      rlo += (rlo < 0) ? n : 0;
+      w[q] = ok ? SL[slot_of(t, rlo)] : TT(0);
+      int rhi = start + size + q;
+      rhi -= (rhi >= n) ? n : 0;
+      hh[q] = ok ? SL[slot_of(t, rhi)] : TT(0);
+    }
+  }
+
+  TOut xo[M];
+  WarpXchg wx{pw};
+  if constexpr (MODE != kModeRefine) {
+    T v[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      if (KS == 0) {
+        v[k] = conv<T>(w[KS + k]);
+      } else {
+        // a1: b_k = sum_q w_q (f_{k+q} - f_{k-q})
         T s = T(0);
 #pragma unroll
-        for (int q = 1; q <= KS; q++) {
-          T up;
-          const int kq = (k + q < M) ? k + q : M - 1;  // compile-time clamp
-          if (k + q < M) up = (k + q < size) ? fw[KS + kq] : pick<T, KA>(hh, k + q - size);
-          else up = pick<T, KA>(hh, k + q - size);
-          s += (T)a.w[q - 1] * (up - fw[KS + k - q]);
-        }
+        for (int q = 1; q <= KS; q++)
+          s += (T)a.w[q - 1] * (conv<T>(window_up<TW, M, KS, KA, FULL>(w, hh, k, q, size)) - conv<T>(w[KS + k - q]));
         v[k] = s;
       }
     }
-    solve_partition<T, R, M, T>(v, size, i, lane_ok, t);
-    __syncwarp();
-    if (ok) {
+    solve_partition<T, R, M, T, FULL>(v, size, i, lane_ok, t, wx);
 #pragma unroll
-      for (int k = 0; k < M; k++)
-        if (k < size) SL[k * t.sp + i] = conv<TT>(v[k]);
-    }
+    for (int k = 0; k < M; k++) xo[k] = conv<TOut>(v[k]);
   } else {
     // FP32 bulk + FP64-accurate residual refinement.
     float bh[M], bl[M];
     if (KS == 0) {
 #pragma unroll
       for (int k = 0; k < M; k++) {
-        f2 sv = {0.f, 0.f};
-        if (ok && k < size) {
-          const TT x = SL[k * t.sp + i];
-          if (sizeof(TT) == 8) sv = split_f64((double)x);
-          else sv = {(float)x, 0.f};
-        }
+        const f2 sv = split_in(w[KS + k]);
         bh[k] = sv.hi;
         bl[k] = sv.lo;
       }
     } else {
-      float fh[M + KS], fl[M + KS], hh[KA], hl[KA];
+      float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
 #pragma unroll
-      for (int q = 0; q < KS; q++) {
-        int rlo = start - KS + q;
-        rlo += (rlo < 0) ? n : 0;
-        const TT x = ok ? SL[slot_of(t, rlo)] : TT(0);
-        const f2 sv = (sizeof(TT) == 8) ? split_f64((double)x) : f2{(float)x, 0.f};
-        fh[q] = sv.hi;
-        fl[q] = sv.lo;
-        int rhi = start + size + q;
-        rhi -= (rhi >= n) ? n : 0;
-        const TT y = ok ? SL[slot_of(t, rhi)] : TT(0);
-        const f2 sy = (sizeof(TT) == 8) ? split_f64((double)y) : f2{(float)y, 0.f};
-        hh[q] = sy.hi;
-        hl[q] = sy.lo;
+      for (int u = 0; u < M + KS; u++) {
+        const f2 sv = split_in(w[u]);
+        fh[u] = sv.hi;
+        fl[u] = sv.lo;
       }
 #pragma unroll
-      for (int k = 0; k < M; k++) {
-        const TT x = (ok && k < size) ? SL[k * t.sp + i] : TT(0);
-        const f2 sv = (sizeof(TT) == 8) ? split_f64((double)x) : f2{(float)x, 0.f};
-        fh[KS + k] = sv.hi;
-        fl[KS + k] = sv.lo;
+      for (int q = 0; q < KS; q++) {
+        const f2 sv = split_in(hh[q]);
+        hhh[q] = sv.hi;
+        hhl[q] = sv.lo;
       }
       // a1 in double-float: b = sum_q w_q (f_{k+q} - f_{k-q})
 #pragma unroll
@@ -704,33 +785,37 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         float dh = 0.f, dl = 0.f;
 #pragma unroll
         for (int q = 1; q <= KS; q++) {
+          const int kq = (k + q < M) ? k + q : M - 1;
           float uh, ul;
-          const int kq = (k + q < M) ? k + q : M - 1;  // compile-time clamp
-          if (k + q < M && k + q < size) {
-            uh = fh[KS + kq];
-            ul = fl[KS + kq];
+          if (k + q < M) {
+            uh = sel2<FULL>(k + q < size, fh[KS + kq], pick<float, KA, FULL>(hhh, k + q - size));
+            ul = sel2<FULL>(k + q < size, fl[KS + kq], pick<float, KA, FULL>(hhl, k + q - size));
           } else {
-            uh = pick<float, KA>(hh, k + q - size);
-            ul = pick<float, KA>(hl, k + q - size);
+            uh = pick<float, KA, FULL>(hhh, k + q - size);
+            ul = pick<float, KA, FULL>(hhl, k + q - size);
           }
           const f2 df = two_sum(uh, -fh[KS + k - q]);
           const float dlo = df.lo + (ul - fl[KS + k - q]);
           const f2 pr = two_prod(a.wHi[q - 1], df.hi);
           const float plo = pr.lo + __fmaf_rn(a.wHi[q - 1], dlo, a.wLo[q - 1] * df.hi);
-          const f2 sm = two_sum(dh, pr.hi);
-          dh = sm.hi;
-          dl += sm.lo + plo;
+          if (q == 1) {
+            dh = pr.hi;
+            dl = plo;
+          } else {
+            const f2 sm = two_sum(dh, pr.hi);
+            dh = sm.hi;
+            dl += sm.lo + plo;
+          }
         }
-        const f2 nrm = two_sum(dh, dl);
-        bh[k] = nrm.hi;
-        bl[k] = nrm.lo;
+        bh[k] = dh;  // unnormalised pair: bh carries the leading bits, bl the rest
+        bl[k] = dl;
       }
     }
-    // sweep 0: x0 = A^{-1} round(b)
+    // sweep 0: x0 = A^{-1} bh
     float xh[M], xl[M], v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) v[k] = bh[k];
-    solve_partition<float, R, M, float>(v, size, i, lane_ok, t);
+    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
 #pragma unroll
     for (int k = 0; k < M; k++) {
       xh[k] = v[k];
@@ -738,34 +823,67 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     }
     // refinement sweeps: x <- x + A^{-1}(b - A x), residual to FP64 accuracy
     for (int sw = 0; sw < a.sweeps; sw++) {
-      if (sw == 0) residual_df<R, M, false>(bh, bl, xh, xl, v, size, i, t);
-      else residual_df<R, M, true>(bh, bl, xh, xl, v, size, i, t);
-      solve_partition<float, R, M, float>(v, size, i, lane_ok, t);
+      if (sw == 0) residual_df<R, M, false, FULL>(bh, bl, xh, xl, v, size, i, t, wx);
+      else residual_df<R, M, true, FULL>(bh, bl, xh, xl, v, size, i, t, wx);
+      solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
+      if (sw + 1 < a.sweeps) {
 #pragma unroll
-      for (int k = 0; k < M; k++) {
-        const f2 sm = two_sum(xh[k], v[k]);
-        xh[k] = sm.hi;
-        xl[k] = xl[k] + sm.lo;
+        for (int k = 0; k < M; k++) {
+          const f2 sm = two_sum(xh[k], v[k]);
+          xh[k] = sm.hi;
+          xl[k] = xl[k] + sm.lo;
+        }
+      } else {
+        // x = xh + (xl + delta): one FP64 add per unknown (the FP32 path
+        // leaves the FP64 pipe idle otherwise); exact integer conversions
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+          const double xd = f32_to_f64(xh[k]) + f32_to_f64(xl[k] + v[k]);
+          if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
+          else xo[k] = (TOut)xh[k];
+        }
       }
     }
+    if (a.sweeps == 0) {
+#pragma unroll
+      for (int k = 0; k < M; k++) xo[k] = conv<TOut>(xh[k]);
+    }
+  }
+
+  // ---- write back
+  if constexpr (DIRECT) {
+    constexpr int V = 16 / sizeof(TOut);
+    if (ok) {
+      if (FULL && (M % V) == 0) {
+#pragma unroll
+        for (int k = 0; k < M; k += V) {
+          TOut tmp[V];
+#pragma unroll
+          for (int u = 0; u < V; u++) tmp[u] = xo[k + u];
+          V16<TOut, V>::st(gout + start + k, tmp);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < M; k++)
+          if (k < size) gout[start + k] = xo[k];
+      }
+    }
+  } else {
     __syncwarp();
     if (ok) {
 #pragma unroll
       for (int k = 0; k < M; k++)
-        if (k < size) {
-          const f2 nrm = fast_two_sum(xh[k], xl[k]);
-          SL[k * t.sp + i] = (sizeof(TT) == 8) ? (TT)df_to_double(nrm.hi, nrm.lo) : (TT)nrm.hi;
-        }
+        if (FULL || k < size) SL[k * t.sp + i] = conv<TT>(xo[k]);
     }
+    __syncthreads();
+    tile_copy<false, TOut, TT>(tr, t, S, (TOut*)out_ptr);
   }
-  __syncthreads();
-  tile_copy<false, TOut, TT>(tr, t, S, (TOut*)out_ptr);
 }
 
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut>
-__global__ void __launch_bounds__(256, (MODE == kModeRefine) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL, bool DIRECT>
+__global__ void __launch_bounds__(256, (MODE == kModeRefine || M == 32) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  line_tile<R, M, MODE, KS, TIn, TOut>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
+  line_tile<R, M, MODE, KS, TIn, TOut, FULL, DIRECT>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace cbs

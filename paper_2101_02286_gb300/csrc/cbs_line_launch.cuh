@@ -13,7 +13,7 @@ inline dim3 tile_grid(int64_t nx, int64_t ny, int64_t nz, int64_t nlines, int di
   return dim3((unsigned)((nx + lines_per_cta - 1) / lines_per_cta), (unsigned)(dir == 1 ? nz : ny), 1);
 }
 
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, bool DIRECT = false>
 cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
   const int threads = kLineThreads;
@@ -23,55 +23,73 @@ cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s
   const size_t smem = (size_t)lines_per_cta * t.lsz * sizeof(TT);
   static size_t configured = 0;  // per instantiation
   if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut>,
+    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, DIRECT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  line_kernel<R, M, MODE, KS, TIn, TOut><<<grid, threads, smem, s>>>(a, t);
+  line_kernel<R, M, MODE, KS, TIn, TOut, FULL, DIRECT><<<grid, threads, DIRECT ? 0 : smem, s>>>(a, t);
   return cudaGetLastError();
+}
+
+// Whole-size partitions (n = p M): sizes are compile-time constants; x-lines
+// then skip shared memory.  Compiled for FP64 input and output only.
+inline bool tile_full(const DevLineTables& t, int M) { return t.count_big == t.p && t.rows_big == M; }
+
+template <int R, int M, int MODE, int KSV, typename TIn, typename TOut>
+cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
+  if constexpr (sizeof(TIn) == 8 && sizeof(TOut) == 8) {
+    if (tile_full(t, M)) {
+      if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, true>(a, t, s);
+      return launch_one<R, M, MODE, KSV, TIn, TOut, true, false>(a, t, s);
+    }
+  }
+  return launch_one<R, M, MODE, KSV, TIn, TOut, false, false>(a, t, s);
 }
 
 template <int R, int M, int MODE, typename TIn, typename TOut>
 cudaError_t launch_ks(int KS, const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   switch (KS) {
-    case 0: return launch_one<R, M, MODE, 0, TIn, TOut>(a, t, s);
-    case 2: return launch_one<R, M, MODE, 2, TIn, TOut>(a, t, s);
-    case 3: return launch_one<R, M, MODE, 3, TIn, TOut>(a, t, s);
+    case 0: return launch_variant<R, M, MODE, 0, TIn, TOut>(a, t, s);
+    case 2: return launch_variant<R, M, MODE, 2, TIn, TOut>(a, t, s);
+    case 3: return launch_variant<R, M, MODE, 3, TIn, TOut>(a, t, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int R, int MODE, typename TIn, typename TOut>
-cudaError_t launch_m(int M, int KS, const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
+// Defined once per (MODE, R, M) in its own translation unit (parallel build).
+template <int MODE, int R, int M>
+cudaError_t launch_line_mrm(int KS, int tin, int tout, const LineArgs& a, const DevLineTables& t, cudaStream_t s);
+
+// Supported element types: FP64 -> FP64 for every mode; FP32 -> FP32 for the
+// FP32 mode; FP32 input -> FP64 output without a stencil for the FP64 and
+// refinement modes.
+#define CBS_DEFINE_LINE_LAUNCH(MODE, R, M)                                                        \
+  template <>                                                                                     \
+  cudaError_t launch_line_mrm<MODE, R, M>(int KS, int tin, int tout, const LineArgs& a,           \
+                                          const DevLineTables& t, cudaStream_t s) {               \
+    const bool i64 = tin == CBS_DTYPE_F64, o64 = tout == CBS_DTYPE_F64;                          \
+    if (i64 && o64) return launch_ks<R, M, MODE, double, double>(KS, a, t, s);                    \
+    if constexpr (MODE == kModeF32) {                                                             \
+      if (!i64 && !o64) return launch_ks<R, M, MODE, float, float>(KS, a, t, s);                  \
+    } else {                                                                                      \
+      if (!i64 && o64 && KS == 0) return launch_one<R, M, MODE, 0, float, double>(a, t, s);       \
+    }                                                                                             \
+    return cudaErrorNotSupported;                                                                 \
+  }
+
+// Dispatch over M (declared specialisations live in the per-M units).
+template <int MODE, int R>
+inline cudaError_t launch_line_mode_r(int M, int KS, int tin, int tout, const LineArgs& a, const DevLineTables& t,
+                                      cudaStream_t s) {
   switch (M) {
-    case 8: return launch_ks<R, 8, MODE, TIn, TOut>(KS, a, t, s);
-    case 16: return launch_ks<R, 16, MODE, TIn, TOut>(KS, a, t, s);
+    case 8: return launch_line_mrm<MODE, R, 8>(KS, tin, tout, a, t, s);
+    case 16: return launch_line_mrm<MODE, R, 16>(KS, tin, tout, a, t, s);
     case 32:
-      if (MODE != kModeRefine) return launch_ks<R, (MODE != kModeRefine ? 32 : 16), MODE, TIn, TOut>(KS, a, t, s);
+      if constexpr (MODE != kModeRefine) return launch_line_mrm<MODE, R, 32>(KS, tin, tout, a, t, s);
       break;
   }
-  return cudaErrorInvalidValue;
+  return cudaErrorNotSupported;
 }
-
-// Defined once per (MODE, R) in its own translation unit.
-template <int MODE, int R>
-cudaError_t launch_line_mode_r(int M, int KS, int tin, int tout, const LineArgs& a,
-                               const DevLineTables& t, cudaStream_t s);
-
-#define CBS_DEFINE_LINE_LAUNCH(MODE, R)                                                      \
-  template <>                                                                                \
-  cudaError_t launch_line_mode_r<MODE, R>(int M, int KS, int tin, int tout, const LineArgs& a, \
-                                          const DevLineTables& t, cudaStream_t s) {          \
-    const bool i64 = tin == CBS_DTYPE_F64, o64 = tout == CBS_DTYPE_F64;                     \
-    if (MODE != kModeF32 && !o64) return cudaErrorInvalidValue;                              \
-    if (i64 && o64) return launch_m<R, MODE, double, double>(M, KS, a, t, s);                \
-    if (!i64 && o64) return launch_m<R, MODE, float, double>(M, KS, a, t, s);                \
-    if (MODE == kModeF32) {                                                                  \
-      if (i64) return launch_m<R, MODE, double, float>(M, KS, a, t, s);                      \
-      return launch_m<R, MODE, float, float>(M, KS, a, t, s);                                \
-    }                                                                                        \
-    return cudaErrorInvalidValue;                                                            \
-  }
 
 }  // namespace cbs

@@ -1,0 +1,267 @@
+// cbs_long.cu -- lines too long for one warp: p segments per line, one CTA
+// per segment (the paper's distributed level across thread blocks).
+//
+// A solve is three launches on one stream:
+//   1. ends:  for every segment only the first r and last r rows of
+//             y_i = D_i^{-1} b_i are needed (Sec. 4: only those rows cross
+//             partitions).  They are dot products of the segment's right-hand
+//             side with rows of D_i^{-1} (Toeplitz, symmetric and
+//             persymmetric, so one table of r rows serves both ends).  The
+//             rows decay geometrically away from the diagonal; the plan keeps
+//             the K leading entries whose tail is below 2^-60 of the row's
+//             l1 norm, so only the segment ends are read.  FP64.
+//   2. iface: per line, b-hat (Eq. 21) and the cyclic interface system by
+//             the pre-factorised block PCR with detach/reattach
+//             (Algorithms 1-4), messages through shared memory.  FP64.
+//   3. seg:   per segment, D_i x_i = b_i - L_i x~_i - U_i x~_{i+1} (Eq. 9),
+//             solved by the same partition method one level down: the
+//             CTA's threads are acyclic sub-partitions exchanging through
+//             shared memory; FP64, FP32, or FP32 + refinement with an
+//             FP64-accurate residual.  Writes every row of x, interface rows
+//             included.
+// Scratch: yb and cc (2r doubles per segment) and xt (r doubles per segment).
+#include "cbs_line.cuh"
+#include "cbs_long.cuh"
+
+namespace cbs {
+
+
+
+// ---------------------------------------------------------------- 1. ends
+template <typename TIn>
+__global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a) {
+  const int seg = blockIdx.x;
+  const int64_t line = blockIdx.y;
+  const int r = a.r, N = a.m - r;
+  const TIn* b = (const TIn*)a.in + line * a.n + (int64_t)seg * a.m + r;  // first bulk row
+  double accF[kMaxR], accL[kMaxR];
+#pragma unroll
+  for (int q = 0; q < kMaxR; q++) accF[q] = accL[q] = 0.0;
+  for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
+    const double bf = (double)__ldg(b + j), bl = (double)__ldg(b + N - 1 - j);
+#pragma unroll
+    for (int q = 0; q < kMaxR; q++)
+      if (q < r) {
+        accF[q] += __ldg(a.G + q * a.K + j) * bf;
+        accL[q] += __ldg(a.G + (r - 1 - q) * a.K + j) * bl;  // persymmetry of D^{-1}
+      }
+  }
+  __shared__ double red[2 * kMaxR][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 2 * kMaxR; q++) {
+    double v = (q < kMaxR) ? accF[q] : accL[q - kMaxR];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * r) {
+    const int q = threadIdx.x;  // 0..r-1 first rows, r..2r-1 last rows
+    const int slot = (q < r) ? q : kMaxR + (q - r);
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[slot][w];
+    a.yb[(line * a.p + seg) * 2 * r + q] = v;
+  }
+}
+
+// ---------------------------------------------------------------- 2. interface
+template <typename TIn>
+__global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, const DevLineTables t) {
+  extern __shared__ __align__(16) double xs[];  // 2 buffers of p*r
+  const int64_t line = blockIdx.x;
+  const int p = a.p, r = a.r, rr = r * r;
+  const double* yb = a.yb + line * p * 2 * r;
+  const TIn* bl = (const TIn*)a.in + line * a.n;
+  double* X0 = xs;
+  double* X1 = xs + p * r;
+  // b-hat_i = b~_i - L~ y_{i-1}[last] - U~ y_i[first]   (Eq. 21)
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const int im = (i == 0) ? p - 1 : i - 1;
+    for (int q = 0; q < r; q++) {
+      double v = (double)__ldg(bl + (int64_t)i * a.m + q);
+      for (int e = 0; e < r; e++) {
+        v -= t.Lt[q][e] * yb[im * 2 * r + r + e];
+        v -= t.Ut[q][e] * yb[i * 2 * r + e];
+      }
+      X0[i * r + q] = v;
+    }
+  }
+  __syncthreads();
+  for (int st = 0; st < t.nstage; st++) {
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+      const int sm = __ldg(t.src + (st * 2 + 0) * p + i), sp = __ldg(t.src + (st * 2 + 1) * p + i);
+      for (int q = 0; q < r; q++) {
+        double acc = 0.0;
+        for (int e = 0; e < r; e++) {
+          acc += __ldg(t.coef + ((st * 3 + 0) * rr + q * r + e) * p + i) * X0[i * r + e];
+          acc -= __ldg(t.coef + ((st * 3 + 1) * rr + q * r + e) * p + i) * X0[sm * r + e];
+          acc -= __ldg(t.coef + ((st * 3 + 2) * rr + q * r + e) * p + i) * X0[sp * r + e];
+        }
+        X1[i * r + q] = acc;
+      }
+    }
+    __syncthreads();
+    double* tmp = X0;
+    X0 = X1;
+    X1 = tmp;
+  }
+  for (int k = threadIdx.x; k < p * r; k += blockDim.x) a.xt[line * p * r + k] = X0[k];
+  // Eq. 9 right-hand-side terms for every segment: bulk row j < r couples to
+  // x~_i[q] at offset q - r - j; bulk row N - r + e couples to x~_{i+1}[q]
+  // at offset q + r - e.
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const int ip = (i + 1 == p) ? 0 : i + 1;
+    for (int j = 0; j < r; j++) {
+      double c = 0.0, d = 0.0;
+      for (int q = 0; q < r; q++) {
+        const int o1 = q - r - j, o2 = q + r - j;
+        if (o1 >= -r) c += a.band[o1 + r] * X0[i * r + q];
+        if (o2 <= r) d += a.band[o2 + r] * X0[ip * r + q];
+      }
+      a.cc[(line * p + i) * 2 * r + j] = c;
+      a.cc[(line * p + i) * 2 * r + r + j] = d;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- 3. segments
+// One CTA per (segment, line); thread i = inner partition i of the segment's
+// bulk rows (acyclic, tables `tin`).
+template <int R, int M, int MODE, typename TIn, typename TOut>
+__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin) {
+  extern __shared__ __align__(16) unsigned long long xbuf[];  // 2 * blockDim slots
+  using T = typename std::conditional<MODE == kModeF64, double, float>::type;
+  const int seg = blockIdx.x;
+  const int64_t line = blockIdx.y;
+  const int i = threadIdx.x, P = tin.p;
+  const bool lane_ok = i < P;
+  int start = 0, size = 2 * R;
+  if (lane_ok) partition_of(tin, i, start, size);
+  const int N = a.m - R;
+  const int64_t row0 = line * a.n + (int64_t)seg * a.m;  // segment's first row
+  const TIn* b = (const TIn*)a.in + row0 + R + start;   // this partition's bulk rows
+  TOut* x = (TOut*)a.out + row0 + R + start;
+  const double* xt_here = a.xt + (line * a.p + seg) * R;
+  const double* cc = a.cc + (line * a.p + seg) * 2 * R;  // [first R rows | last R rows]
+  CtaXchg xch{xbuf, 0};
+  // Eq. 9 couplings to the known interface values, moved to the RHS; only the
+  // first partition (bulk rows 0..R-1) and the last (rows size-R..size-1)
+  double cF[R], cL[R];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    cF[e] = (lane_ok && i == 0) ? cc[e] : 0.0;
+    cL[e] = (lane_ok && i == P - 1) ? cc[R + e] : 0.0;
+  }
+  if constexpr (MODE != kModeRefine) {
+    T v[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      T val = (lane_ok && k < size) ? conv<T>(__ldg(b + k)) : T(0);
+      if (k < R) val -= conv<T>(cF[k]);
+#pragma unroll
+      for (int e = 0; e < R; e++) val -= sel(k == size - R + e, conv<T>(cL[e]), T(0));
+      v[k] = val;
+    }
+    solve_partition<T, R, M, T, false>(v, size, i, lane_ok, tin, xch);
+    if (lane_ok) {
+#pragma unroll
+      for (int k = 0; k < M; k++)
+        if (k < size) x[k] = conv<TOut>(v[k]);
+    }
+  } else {
+    float bh[M], bl[M], xh[M], xl[M], v[M];
+    f2 sF[R], sL[R];
+#pragma unroll
+    for (int e = 0; e < R; e++) {
+      sF[e] = split_f64(cF[e]);
+      sL[e] = split_f64(cL[e]);
+    }
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      f2 s = {0.f, 0.f};
+      if (lane_ok && k < size) s = split_in(__ldg(b + k));
+      // subtract the correction (zero on all but the edge rows) exactly
+      f2 c = {0.f, 0.f};
+      if (k < R) c = sF[k];
+#pragma unroll
+      for (int e = 0; e < R; e++) {
+        c.hi = sel(k == size - R + e, sL[e].hi, c.hi);
+        c.lo = sel(k == size - R + e, sL[e].lo, c.lo);
+      }
+      const f2 d = two_sum(s.hi, -c.hi);
+      bh[k] = d.hi;
+      bl[k] = d.lo + (s.lo - c.lo);
+      v[k] = d.hi;
+    }
+    solve_partition<float, R, M, float, false>(v, size, i, lane_ok, tin, xch);
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      xh[k] = v[k];
+      xl[k] = 0.f;
+    }
+    for (int sw = 0; sw < a.sweeps; sw++) {
+      if (sw == 0) residual_df<R, M, false, false>(bh, bl, xh, xl, v, size, i, tin, xch);
+      else residual_df<R, M, true, false>(bh, bl, xh, xl, v, size, i, tin, xch);
+      solve_partition<float, R, M, float, false>(v, size, i, lane_ok, tin, xch);
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const f2 s = two_sum(xh[k], v[k]);
+        xh[k] = s.hi;
+        xl[k] = xl[k] + s.lo;
+      }
+    }
+    if (lane_ok) {
+#pragma unroll
+      for (int k = 0; k < M; k++)
+        if (k < size) x[k] = (TOut)(f32_to_f64(xh[k]) + f32_to_f64(xl[k]));
+    }
+  }
+  // the segment's interface rows
+  if (threadIdx.x < R) ((TOut*)a.out)[row0 + threadIdx.x] = (TOut)xt_here[threadIdx.x];
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
+                        const DevLineTables& inner, cudaStream_t s, int* launches) {
+  *launches = 0;
+  const dim3 gs((unsigned)a.p, (unsigned)a.lines);
+  if (in64) long_ends_kernel<double><<<gs, 128, 0, s>>>(a);
+  else long_ends_kernel<float><<<gs, 128, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ithreads = a.p < 1024 ? ((a.p + 31) / 32) * 32 : 1024;
+  const size_t ismem = 2 * (size_t)a.p * a.r * sizeof(double);
+  static size_t iconf = 0;
+  if (ismem > 48 * 1024 && ismem > iconf) {
+    e = cudaFuncSetAttribute(long_iface_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(long_iface_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    if (e != cudaSuccess) return e;
+    iconf = ismem;
+  }
+  if (in64) long_iface_kernel<double><<<(unsigned)a.lines, ithreads, ismem, s>>>(a, outer);
+  else long_iface_kernel<float><<<(unsigned)a.lines, ithreads, ismem, s>>>(a, outer);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int threads = ((inner.p + 31) / 32) * 32;
+  const size_t smem = 2 * (size_t)threads * sizeof(unsigned long long);
+#define CBS_SEG(MO, RR, TI, TO) long_seg_kernel<RR, 16, MO, TI, TO><<<gs, threads, smem, s>>>(a, inner)
+  if (mode == kModeRefine) {
+    if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }
+    else { if (in64) CBS_SEG(kModeRefine, 2, double, double); else CBS_SEG(kModeRefine, 2, float, double); }
+  } else if (mode == kModeF64) {
+    if (R == 1) { if (in64) CBS_SEG(kModeF64, 1, double, double); else CBS_SEG(kModeF64, 1, float, double); }
+    else { if (in64) CBS_SEG(kModeF64, 2, double, double); else CBS_SEG(kModeF64, 2, float, double); }
+  } else {
+    if (R == 1) { if (in64) CBS_SEG(kModeF32, 1, double, float); else CBS_SEG(kModeF32, 1, float, float); }
+    else { if (in64) CBS_SEG(kModeF32, 2, double, float); else CBS_SEG(kModeF32, 2, float, float); }
+  }
+#undef CBS_SEG
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  *launches = 3;
+  return cudaSuccess;
+}
+
+}  // namespace cbs

@@ -202,31 +202,42 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
     }
   };
 
-  // ---- S_i, R_i (Eq. 15-16) per partition ----
-  T.sr.assign((size_t)nmax * 2 * r * p, 0.0);
-  std::vector<std::vector<double>> S(p), R(p);  // [j*r + q]
+  // ---- S_i, R_i (Eq. 15-16): they depend only on the partition size ----
+  // class 0 = rows_big, class 1 = rows_small; [j*r + q]
+  std::vector<double> Scl[2], Rcl[2];
   std::vector<double> col(nmax), sol(nmax);
-  for (int i = 0; i < p; i++) {
-    const int m = T.size[i], N = m - r;
-    S[i].assign((size_t)N * r, 0.0);
-    R[i].assign((size_t)N * r, 0.0);
+  for (int c = 0; c < 2; c++) {
+    const int m = c == 0 ? T.rows_big : T.rows_small, N = m - r;
+    Scl[c].assign((size_t)N * r, 0.0);
+    Rcl[c].assign((size_t)N * r, 0.0);
     for (int q = 0; q < r; q++) {
       // L_i[:, q]: bulk row j couples to own interface column q at offset q - r - j
       for (int j = 0; j < N; j++) col[j] = A.at(q - r - j);
       solveD(N, col.data(), sol.data());
-      for (int j = 0; j < N; j++) S[i][(size_t)j * r + q] = sol[j];
+      for (int j = 0; j < N; j++) Scl[c][(size_t)j * r + q] = sol[j];
       // U_i[:, q]: bulk row j couples to next interface column q at offset m + q - r - j
-      bool has_next = cyclic || i + 1 < p;
-      for (int j = 0; j < N; j++) col[j] = has_next ? A.at(m + q - r - j) : 0.0;
+      for (int j = 0; j < N; j++) col[j] = A.at(m + q - r - j);
       solveD(N, col.data(), sol.data());
-      for (int j = 0; j < N; j++) R[i][(size_t)j * r + q] = sol[j];
+      for (int j = 0; j < N; j++) Rcl[c][(size_t)j * r + q] = sol[j];
     }
+  }
+  T.srB.assign((size_t)(T.rows_big - r) * 2 * r, 0.0);
+  T.srS.assign((size_t)(T.rows_small - r) * 2 * r, 0.0);
+  for (int c = 0; c < 2; c++) {
+    std::vector<double>& dst = c == 0 ? T.srB : T.srS;
+    const int N = (c == 0 ? T.rows_big : T.rows_small) - r;
     for (int j = 0; j < N; j++)
       for (int q = 0; q < r; q++) {
-        T.sr[((size_t)j * 2 * r + q) * p + i] = S[i][(size_t)j * r + q];
-        T.sr[((size_t)j * 2 * r + r + q) * p + i] = R[i][(size_t)j * r + q];
+        dst[(size_t)j * 2 * r + q] = Scl[c][(size_t)j * r + q];
+        dst[(size_t)j * 2 * r + r + q] = Rcl[c][(size_t)j * r + q];
       }
   }
+  auto cls = [&](int i) { return i < T.count_big ? 0 : 1; };
+  // acyclic: the last partition has no next interface, so its R is zero
+  auto S_at = [&](int i, int j, int q) { return Scl[cls(i)][(size_t)j * r + q]; };
+  auto R_at = [&](int i, int j, int q) {
+    return (!cyclic && i == p - 1) ? 0.0 : Rcl[cls(i)][(size_t)j * r + q];
+  };
 
   // ---- b-hat assembly blocks (Eq. 21) ----
   for (int q = 0; q < r; q++)
@@ -249,11 +260,11 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
         double a1 = 0, a2 = 0, a3 = 0, a4 = 0;
         for (int e = 0; e < r; e++) {
           if (has_prev) {
-            a1 += T.Lt[q][e] * R[im][(size_t)(Nm - r + e) * r + qq];
-            a3 += T.Lt[q][e] * S[im][(size_t)(Nm - r + e) * r + qq];
+            a1 += T.Lt[q][e] * R_at(im, Nm - r + e, qq);
+            a3 += T.Lt[q][e] * S_at(im, Nm - r + e, qq);
           }
-          a2 += T.Ut[q][e] * S[i][(size_t)e * r + qq];
-          a4 += T.Ut[q][e] * R[i][(size_t)e * r + qq];
+          a2 += T.Ut[q][e] * S_at(i, e, qq);
+          a4 += T.Ut[q][e] * R_at(i, e, qq);
         }
         (void)N;
         LRm(q, qq) = a1;
@@ -391,12 +402,33 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
       *singular = true;
       return "non-finite interface coefficient";
     }
-  for (double v : T.sr)
+  for (double v : T.srB)
     if (!std::isfinite(v)) {
       *singular = true;
       return "non-finite S/R entry";
     }
   return "";
+}
+
+std::vector<double> bulk_inverse_rows(const LineTables& T, int N, int nrows) {
+  const int r = T.r, F = 2 * r + 1;
+  std::vector<double> out((size_t)nrows * N), y(N);
+  for (int q = 0; q < nrows; q++) {
+    for (int j = 0; j < N; j++) y[j] = (j == q) ? 1.0 : 0.0;
+    for (int j = 0; j < N; j++) {
+      double s = y[j];
+      for (int k = 1; k <= r && j - k >= 0; k++) s -= T.fac[(size_t)j * F + k - 1] * y[j - k];
+      y[j] = s;
+    }
+    for (int j = N - 1; j >= 0; j--) {
+      double s = T.fac[(size_t)j * F + r] * y[j];
+      for (int k = 1; k <= r && j + k < N; k++) s -= T.fac[(size_t)j * F + r + k] * y[j + k];
+      y[j] = s;
+    }
+    // D is symmetric, so column q of D^{-1} is row q
+    for (int j = 0; j < N; j++) out[(size_t)q * N + j] = y[j];
+  }
+  return out;
 }
 
 }  // namespace cbs

@@ -1,0 +1,68 @@
+"""GPU parity of the long-line path (segments across CTAs): the
+pentadiagonal precision workload and its smaller relatives, against the
+FP64 oracle (banded LU + Woodbury)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2101_02286_gb300 import workloads as W
+from paper_2101_02286_gb300.solver import Plan
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(d32, lhs, segments, precision="fp32_refine", sweeps=2, in_dtype=torch.float32):
+    lines, n = d32.shape
+    plan = Plan((1, lines, n), 0, lhs=lhs, rhs=None, segments=segments, precision=precision, sweeps=sweeps,
+                in_dtype=in_dtype)
+    x = plan.solve(torch.from_numpy(d32.reshape(1, lines, n)).to("cuda", in_dtype))
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    return x.double().cpu().numpy().reshape(lines, n), info
+
+
+@pytest.mark.parametrize("lhs", [W.PENTA10["lhs"], W.LELE6_TRI["lhs"]])
+@pytest.mark.parametrize("n,p", [(4096, 8), (8192, 16), (3072, 3), (5632, 11), (2048, 1), (16384, 64), (6144, 2)])
+def test_long_refine(cuda, lhs, n, p):
+    d = np.random.default_rng(n + p).standard_normal((3, n)).astype(np.float32)
+    x, info = _solve(d, lhs, p)
+    assert info["kernel"] == 1 and info["segments"] == p
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, lhs), d.astype(np.float64))
+    assert oracle.rel_err(x, ref) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol,sweeps", [("fp64", 1e-12, 1), ("fp32", 2e-5, 1), ("fp32_refine", 1e-12, 1)])
+def test_long_precisions(cuda, precision, tol, sweeps):
+    n, p = 8192, 8
+    d = np.random.default_rng(7).standard_normal((2, n))
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    x, _ = _solve(d, W.LELE6_TRI["lhs"], p, precision=precision, sweeps=sweeps, in_dtype=dt)
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.LELE6_TRI["lhs"]),
+                              d.astype(np.float32).astype(np.float64) if dt == torch.float32 else d)
+    assert oracle.rel_err(x, ref) < tol
+
+
+def test_long_unrefined_fp32_error_scale(cuda):
+    # one FP32 solve of the pentadiagonal system stays within 2e-5
+    n = 8192
+    d = np.random.default_rng(3).standard_normal((2, n)).astype(np.float32)
+    x, _ = _solve(d, W.PENTA10["lhs"], 8, precision="fp32", sweeps=1)
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d.astype(np.float64))
+    assert oracle.rel_err(x, ref) < 2e-5
+
+
+@pytest.mark.slow
+def test_long_full_workload_sampled(cuda):
+    # 32 lines of 2^22, pentadiagonal, FP32 right-hand side, 1024 segments
+    d = W.long_lines()
+    lines, n = d.shape
+    plan = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=1024, precision="fp32_refine",
+                sweeps=2, in_dtype=torch.float32)
+    x = plan.solve(torch.from_numpy(d.reshape(1, lines, n)).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    for l in (0, 17, 31):
+        ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d[l:l + 1].astype(np.float64))
+        assert oracle.rel_err(x[0, l].cpu().numpy(), ref[0]) < 1e-12
