@@ -48,6 +48,26 @@ def parse():
     return ap.parse_args()
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank scalar over the process group (identity when not
+    initialised).  Used for the step time: the job is as slow as its slowest
+    rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput (units/s x 1e-9) when every rank processes
+    units_per_rank in ms_max milliseconds (weak scaling)."""
+    return world * units_per_rank / (ms_max * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
@@ -186,34 +206,35 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(ps, steps, warmup, sampler=None):
+    def timed(ps, steps, warmup):
         for _ in range(warmup):
             step(ps)
         barrier()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev_dir = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-        ctx = sampler if sampler is not None else _Null()
-        with ctx:
-            ev[0].record(stream)
-            for s in range(steps):
-                ev_dir[s][0].record(stream)
-                for d in range(3):
-                    ps[d].solve(f, outs[d], stream)
-                    ev_dir[s][d + 1].record(stream)
-            ev[1].record(stream)
-            barrier()
+        ev[0].record(stream)
+        for s in range(steps):
+            ev_dir[s][0].record(stream)
+            for d in range(3):
+                ps[d].solve(f, outs[d], stream)
+                ev_dir[s][d + 1].record(stream)
+        ev[1].record(stream)
+        barrier()
         ms = ev[0].elapsed_time(ev[1]) / steps
         per_dir = [sum(ev_dir[s][d].elapsed_time(ev_dir[s][d + 1]) for s in range(steps)) / steps
                    for d in range(3)]
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         return ms, per_dir
 
+    # clocks are sampled (every 100 ms) across all the device-timed work
     sampler = ClockSampler(local)
-    ms_ref, dir_ref = timed(plans["fp32_refine"], args.steps, max(args.warmup, 3), sampler)
-    ms_64, dir_64 = timed(plans["fp64"], max(3, args.steps // 2), 3)
+    with sampler:
+        time.sleep(0.3)
+        ms_ref, dir_ref = timed(plans["fp32_refine"], args.steps, max(args.warmup, 3))
+        ms_64, dir_64 = timed(plans["fp64"], max(3, args.steps // 2), 3)
+        for _ in range(max(1, int(0.3 / max(ms_ref * 1e-3, 1e-4)))):  # keep the GPU busy while sampling
+            step(plans["fp32_refine"])
+        barrier()
 
     # accuracy of both paths against the FP64 oracle on sampled lines
     err = {}
@@ -253,10 +274,7 @@ def main():
         e2e_step(plans["fp32_refine"])
     barrier()
     e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
 
     if rank == 0:
         peaks = {}
@@ -274,7 +292,7 @@ def main():
         fp64_flops = 15.0 * N ** 3
         fp64_ach = fp64_flops / (sum(dir_64) / 3 * 1e-3) / 1e12
         clocks = sampler.summary()
-        value = world * UNKNOWNS_PER_STEP / (ms_ref * 1e-3) / 1e9
+        value = job_throughput(UNKNOWNS_PER_STEP, world, ms_ref)
         cpu_v, cores, sample = oracle_sample(args.cpu_seconds)
         rec = {
             "metric": METRIC, "value": value, "unit": "Gunknowns/s", "n_gpus": world, "steps": args.steps,
