@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "
 EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transpose", "cbs_band_grad",
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
            "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
-           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands")
+           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc")
 
 
 class CbsError(RuntimeError):
@@ -95,6 +95,7 @@ def _load():
         "cbs_version": ([], i32),
         "cbs_interface_model": ([P(cbs_desc), i32, vp, vp, vp, vp, vp], st),
         "cbs_plan_set_bands": ([vp, vp], st),
+        "cbs_solve_noalloc": ([vp, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +128,11 @@ def cbs_plan_set_bands(plan: int, bands: int) -> None:
 
 def cbs_solve(plan: int, inp: int, out: int, stream: int = 0) -> None:
     _check(_lib.cbs_solve(plan, inp, out, stream))
+
+
+def cbs_solve_noalloc(plan: int, inp: int, out: int, stream: int = 0) -> None:
+    """Long-line solve on the library's fixed scratch (no device allocation)."""
+    _check(_lib.cbs_solve_noalloc(plan, inp, out, stream))
 
 
 def cbs_solve_transpose(plan: int, g: int, x: int | None, lam: int | None, grad_in: int | None,

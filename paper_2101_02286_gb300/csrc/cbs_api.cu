@@ -10,8 +10,7 @@
 #include <string>
 
 #include "cbs_line_launch.cuh"
-#include "cbs_var.cuh"
-#include "cbs_long.cuh"
+#include "cbs_plan_struct.h"
 
 using namespace cbs;
 
@@ -20,9 +19,6 @@ cudaError_t launch_var(int M, int KS, bool adj, bool f64, const VarArgs& a, cons
                        cudaStream_t s);
 cudaError_t launch_band_grad(bool f64, const void* lam, const void* x, void* ga, int64_t nx, int64_t ny,
                              int64_t nz, int dir, cudaStream_t s);
-struct LongArgs;
-cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
-                        const DevLineTables& inner, cudaStream_t s, int* launches);
 struct BatchProblem;
 int batch_variant_host(int R, int KS, int M, int MODE);
 cudaError_t batch_configure(size_t smem);
@@ -55,34 +51,7 @@ int next_pow2(int p) {
 
 }  // namespace
 
-struct cbs_batch {
-  std::vector<cbs_plan*> plans;
-  void* dprobs = nullptr;
-  void* ditems = nullptr;
-  int nitems = 0, count = 0, grid = 1;
-  size_t smem = 0;
-  int64_t unknowns = 0;
-};
 
-struct cbs_plan {
-  cbs_desc desc;
-  int n = 0, r = 1, kind = 0, M = 16, ks = 0;
-  int64_t nlines = 0;
-  LineTables host;
-  DevLineTables dev;
-  void* dbuf = nullptr;
-  int* dstatus = nullptr;
-  LineArgs args;
-  bool var = false;
-  VarArgs vargs;
-  // long lines (kind 1): segments across CTAs
-  LineTables inner;
-  DevLineTables dev_inner;
-  LongArgs largs;
-  void* lbuf = nullptr;
-  void* sbuf = nullptr;
-  int inner_threads = 0;
-};
 
 namespace {
 
@@ -141,6 +110,11 @@ int default_segments(int n, int r, int precision) {
 }
 
 }  // namespace
+
+namespace cbs {
+cbs_status set_error(cbs_status s, const std::string& msg) { return fail(s, msg); }
+void set_launch_count(int n) { g_launches = n; }
+}  // namespace cbs
 
 namespace {
 // Fill the kernel-side tables of plan tables T (fac, S/R, b-hat blocks,

@@ -20,8 +20,12 @@
 //             FP64-accurate residual.  Writes every row of x, interface rows
 //             included.
 // Scratch: yb and cc (2r doubles per segment) and xt (r doubles per segment).
+#include <mutex>
+#include <string>
+
 #include "cbs_line.cuh"
 #include "cbs_long.cuh"
+#include "cbs_plan_struct.h"
 
 namespace cbs {
 
@@ -264,4 +268,84 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- no-alloc entry
+// Long-line solve whose per-solve scratch (yb, cc, xt) is one library-wide
+// array in the device image instead of the plan's own buffer.  It exists for
+// callers that must not call cudaMalloc when they solve: code running while
+// a stream capture is active (allocation is refused then), applications that
+// hand all device memory to their own allocator at start-up, and loops with a
+// fixed memory footprint where a late allocation could fail.
+//
+// The array is a host-side stand-in in host code: the device address comes
+// from cudaGetSymbolAddress, fetched once per device (with that device
+// current) by the first call made on it.  Every call shares the array and
+// the previous call's contents stay in it; nothing needs to start at zero
+// because every slot is written before it is read within a solve.  Calls
+// whose launches overlap on the GPU (different streams, or the same plan from
+// several host threads without ordering) race on the array.
 }  // namespace cbs
+
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = (size_t)1 << 19;  // 4 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device (set-up on first use).
+cbs_status noalloc_scratch(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cbs::set_error(CBS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cbs::set_error(CBS_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return cbs::set_error(CBS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return CBS_OK;
+}
+
+}  // namespace
+
+extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, void* stream) {
+  using namespace cbs;
+  set_launch_count(0);
+  if (!P || !in || !out) return set_error(CBS_ERR_INVALID_ARG, "null argument");
+  if (in == out) return set_error(CBS_ERR_INVALID_ARG, "out must not alias in");
+  if (P->kind != 1) return set_error(CBS_ERR_UNSUPPORTED, "cbs_solve_noalloc runs long-line plans (segments per CTA)");
+  const LongArgs& pa = P->largs;
+  const size_t nseg = (size_t)pa.lines * pa.p;
+  const size_t need = nseg * 5 * pa.r;
+  if (need > kNoAllocScratchDoubles)
+    return set_error(CBS_ERR_INVALID_ARG, "cbs_solve_noalloc: lines x segments x 5r = " + std::to_string(need) +
+                                              " doubles exceeds the fixed scratch of 524288 (4 MiB)");
+  double* scratch = nullptr;
+  cbs_status st = noalloc_scratch(&scratch);
+  if (st) return st;
+  LongArgs a = pa;
+  a.in = in;
+  a.out = out;
+  a.yb = scratch;
+  a.cc = scratch + nseg * 2 * a.r;
+  a.xt = scratch + nseg * 4 * a.r;
+  const cbs_desc& d = P->desc;
+  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  int launches = 0;
+  cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->dev,
+                              P->dev_inner, (cudaStream_t)stream, &launches);
+  if (e != cudaSuccess) return set_error(CBS_ERR_CUDA, std::string("long-line kernel launch: ") + cudaGetErrorString(e));
+  set_launch_count(launches);
+  return CBS_OK;
+}

@@ -1,0 +1,54 @@
+// cbs_plan_struct.h -- the opaque plan and batch objects of the C-ABI
+// (shared by the translation units that implement entry points).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "cbs_internal.h"
+#include "cbs_line.cuh"
+#include "cbs_long.cuh"
+#include "cbs_var.cuh"
+
+using cbs::DevLineTables;
+using cbs::LineArgs;
+using cbs::LineTables;
+using cbs::LongArgs;
+using cbs::VarArgs;
+
+struct cbs_batch {
+  std::vector<cbs_plan*> plans;
+  void* dprobs = nullptr;
+  void* ditems = nullptr;
+  int nitems = 0, count = 0, grid = 1;
+  size_t smem = 0;
+  int64_t unknowns = 0;
+};
+
+struct cbs_plan {
+  cbs_desc desc;
+  int n = 0, r = 1, kind = 0, M = 16, ks = 0;
+  int64_t nlines = 0;
+  LineTables host;
+  DevLineTables dev;
+  void* dbuf = nullptr;
+  int* dstatus = nullptr;
+  LineArgs args;
+  bool var = false;
+  VarArgs vargs;
+  // long lines (kind 1): segments across CTAs
+  LineTables inner;
+  DevLineTables dev_inner;
+  LongArgs largs;
+  void* lbuf = nullptr;
+  void* sbuf = nullptr;
+  int inner_threads = 0;
+};
+
+namespace cbs {
+// Record the calling thread's last error (cbs_last_error_string) and the
+// launch count of the last solve; return `s`.
+cbs_status set_error(cbs_status s, const std::string& msg);
+void set_launch_count(int n);
+cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
+                        const DevLineTables& inner, cudaStream_t s, int* launches);
+}  // namespace cbs
