@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--size", type=int, default=N,
+                    help="grid points per axis (512 = the benchmark workload; smaller for profiling)")
     return ap.parse_args()
 
 
@@ -184,10 +186,11 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    f_host, modes = W.noisy_cube(N)  # seeded: U(-1,1) + one plane wave
+    n = args.size
+    f_host, modes = W.noisy_cube(n)  # seeded: U(-1,1) + one plane wave
     f_pin = torch.from_numpy(f_host).pin_memory()
     f = f_pin.to(dev)
-    h = W.grid_spacing(N)
+    h = W.grid_spacing(n)
     sch = W.LELE6_TRI
 
     def make(prec):
@@ -247,7 +250,7 @@ def main():
             e = 0.0
             for d in range(3):
                 ax = 2 - d
-                idx = rng.integers(0, N, size=(64, 2))
+                idx = rng.integers(0, n, size=(64, 2))
                 fl = np.moveaxis(f_host, ax, -1)[idx[:, 0], idx[:, 1]]
                 ref = oracle.derivative(fl, sch["lhs"], sch["rhs"], h)
                 got = np.moveaxis(outs[d].cpu().numpy(), ax, -1)[idx[:, 0], idx[:, 1]]
@@ -284,38 +287,40 @@ def main():
             pass
         hbm = peaks.get("hbm_gbs", 6800.0)
         hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-        bytes_per_launch = 16.0 * N ** 3  # read f (FP64), write f' (FP64)
+        bytes_per_launch = 16.0 * n ** 3  # read f (FP64), write f' (FP64)
         kdir = max(range(3), key=lambda d: dir_ref[d])
         achieved = bytes_per_launch / (sum(dir_ref) / 3 * 1e-3) / 1e9
         # FP64 path: bound by the FP64 pipe; 15 algorithmic FP64 flops per unknown
         fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
-        fp64_flops = 15.0 * N ** 3
+        fp64_flops = 15.0 * n ** 3
         fp64_ach = fp64_flops / (sum(dir_64) / 3 * 1e-3) / 1e12
         clocks = sampler.summary()
-        value = job_throughput(UNKNOWNS_PER_STEP, world, ms_ref)
-        cpu_v, cores, sample = oracle_sample(args.cpu_seconds)
+        units = 3 * n ** 3
+        value = job_throughput(units, world, ms_ref)
+        cpu_v, cores, sample = oracle_sample(args.cpu_seconds) if args.cpu_seconds > 0 else (None, None, "skipped")
         rec = {
             "metric": METRIC, "value": value, "unit": "Gunknowns/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_ref, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64-accurate residual via FP32 error-free transforms)",
             "data": "synthetic (seeded U(-1,1) + one plane wave, numpy PCG64 seed 1)",
-            "config": dict(CONFIG, parallelism="replicas" if world > 1 else "single GPU", precision="fp32_refine",
+            "config": dict(CONFIG, grid=[n, n, n], parallelism="replicas" if world > 1 else "single GPU",
+                           precision="fp32_refine",
                            sweeps=1, segments=plans["fp32_refine"][0].info()["segments"]),
             "max_rel_err": err.get("fp32_refine"),
             "ms_per_direction": dir_ref,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "peak_source": hbm_src,
                          "kernel": "line_kernel<R=1,M=16,refine,K=2>", "slowest_direction": "xyz"[kdir]},
-            "fp64_path": {"value": world * UNKNOWNS_PER_STEP / (ms_64 * 1e-3) / 1e9, "unit": "Gunknowns/s",
+            "fp64_path": {"value": job_throughput(units, world, ms_64), "unit": "Gunknowns/s",
                           "ms_per_step": ms_64, "ms_per_direction": dir_64, "max_rel_err": err.get("fp64"),
                           "segments": plans["fp64"][0].info()["segments"],
                           "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak_tflops,
                                        "unit": "TFLOP/s (FP64)", "frac": fp64_ach / fp64_peak_tflops,
                                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
-                          "hbm_frac": 16.0 * N ** 3 / (sum(dir_64) / 3 * 1e-3) / 1e9 / hbm},
+                          "hbm_frac": 16.0 * n ** 3 / (sum(dir_64) / 3 * 1e-3) / 1e9 / hbm},
             "speedup_refine_vs_fp64": ms_64 / ms_ref,
-            "e2e": {"value": world * UNKNOWNS_PER_STEP / (e2e_ms * 1e-3) / 1e9, "unit": "Gunknowns/s",
-                    "h2d_bytes_per_step": 8 * N ** 3, "d2h_bytes_per_step": 3 * 8 * N ** 3,
+            "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": "Gunknowns/s",
+                    "h2d_bytes_per_step": 8 * n ** 3, "d2h_bytes_per_step": 3 * 8 * n ** 3,
                     "ms_per_step": e2e_ms},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,

@@ -135,6 +135,18 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* desc);
  * plans or NULL. */
 cbs_status cbs_plan_set_bands(cbs_plan* plan, const void* bands);
 
+/* Autotuner: times every admissible partition count for `desc` (p = 1..32
+ * lanes for lines that fit one warp, divisors giving 64..8192-row segments
+ * for long lines) on scratch buffers it allocates and frees on the current
+ * device (inputs filled with a fixed pattern), with `reps` timed solves each
+ * after two warm-ups, and records the fastest in a per-process cache keyed by
+ * (dims, direction, bandwidth, precision, dtypes, stencil, bands kind).
+ * Later cbs_plan_create calls with segments == 0 use the cached choice.
+ * Writes the choice to *best_segments and its time per solve to *best_ms
+ * (either may be NULL).  Synchronises the device.  Errors: as
+ * cbs_plan_create, CUDA, NO_MEMORY. */
+cbs_status cbs_autotune(const cbs_desc* desc, int32_t reps, int32_t* best_segments, double* best_ms);
+
 /* Destroy a plan and free its device memory (synchronises the device). */
 cbs_status cbs_plan_destroy(cbs_plan* plan);
 

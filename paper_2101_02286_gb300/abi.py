@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "
 EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transpose", "cbs_band_grad",
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
            "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
-           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc")
+           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune")
 
 
 class CbsError(RuntimeError):
@@ -96,6 +96,7 @@ def _load():
         "cbs_interface_model": ([P(cbs_desc), i32, vp, vp, vp, vp, vp], st),
         "cbs_plan_set_bands": ([vp, vp], st),
         "cbs_solve_noalloc": ([vp, vp, vp, vp], st),
+        "cbs_autotune": ([P(cbs_desc), i32, P(i32), P(ctypes.c_double)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -116,6 +117,15 @@ def cbs_plan_create(desc: cbs_desc) -> int:
     h = ctypes.c_void_p()
     _check(_lib.cbs_plan_create(ctypes.byref(h), ctypes.byref(desc)))
     return h.value
+
+
+def cbs_autotune(desc: cbs_desc, reps: int = 5) -> tuple[int, float]:
+    """Time every admissible partition count; returns (segments, ms per solve)
+    and caches the choice for plans created with segments == 0."""
+    p = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(_lib.cbs_autotune(ctypes.byref(desc), reps, ctypes.byref(p), ctypes.byref(ms)))
+    return p.value, ms.value
 
 
 def cbs_plan_destroy(plan: int) -> None:

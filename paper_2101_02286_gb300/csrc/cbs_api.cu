@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +33,20 @@ constexpr int kBatchMax = 256;
 }  // namespace cbs
 
 namespace {
+
+// autotuner cache: descriptor key -> partitions per line
+using TuneKey = std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+TuneKey tune_key(const cbs_desc* d) {
+  return TuneKey(d->dims[0], d->dims[1], d->dims[2], d->direction, d->bandwidth, d->precision, d->in_dtype,
+                 d->out_dtype, d->rhs_kind, d->rhs_terms, d->lhs_kind);
+}
+int tuned_segments(const cbs_desc* d) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune_cache.find(tune_key(d));
+  return it == g_tune_cache.end() ? 0 : it->second;
+}
 
 thread_local std::string g_err;
 thread_local int g_launches = 0;
@@ -401,7 +418,13 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   }
   P->nlines = d->dims[0] * d->dims[1] * d->dims[2] / P->n;
   P->var = d->lhs_kind == CBS_LHS_VARIABLE;
-  int p = d->segments;
+  int p = d->segments ? d->segments : tuned_segments(d);
+  if (p) {
+    cbs_desc dd = *d;
+    dd.segments = p;
+    P->desc = dd;
+    d = &P->desc;
+  }
   if (!p) {
     if (P->var) {
       // registers hold ~5 arrays of rows per lane: keep partitions <= 8 rows
@@ -786,6 +809,74 @@ cbs_status cbs_batch_status_poll(cbs_batch* B, int32_t* st) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "batch status");
   *st = CBS_OK;
+  return CBS_OK;
+}
+
+cbs_status cbs_autotune(const cbs_desc* d, int32_t reps, int32_t* best_segments, double* best_ms) {
+  cbs_status st = validate(d);
+  if (st) return st;
+  if (reps < 1) reps = 1;
+  const int n = (int)d->dims[d->direction], r = (d->bandwidth - 1) / 2;
+  // candidates
+  std::vector<int> cand;
+  for (int p = 1; p <= kMaxLanes; p++)
+    if (n >= 2 * r * p) cand.push_back(p);
+  for (int p = kMaxLanes + 1; p <= n / 64 && (int)cand.size() < 256; p++)
+    if (n % p == 0 && n / p <= 8192 + r) cand.push_back(p);
+  const int64_t elems = d->dims[0] * d->dims[1] * d->dims[2];
+  const size_t isz = d->in_dtype == CBS_DTYPE_F64 ? 8 : 4, osz = d->out_dtype == CBS_DTYPE_F64 ? 8 : 4;
+  void *in = nullptr, *out = nullptr, *bands = nullptr;
+  cudaError_t e = cudaMalloc(&in, elems * isz);
+  if (e == cudaSuccess) e = cudaMalloc(&out, elems * osz);
+  if (e == cudaSuccess && d->lhs_kind == CBS_LHS_VARIABLE) e = cudaMalloc(&bands, elems * isz);
+  // fixed byte patterns: 0x3F.. is a normal finite value in FP64 (4.8e-4)
+  // and FP32 (0.75); 0x3E.. keeps variable bands diagonally dominant (FP64
+  // 7.1e-9, FP32 0.19).  Solve times do not depend on the values.
+  if (e == cudaSuccess) e = cudaMemset(in, 0x3F, elems * isz);
+  if (e == cudaSuccess && bands) e = cudaMemset(bands, 0x3E, elems * isz);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaFree(in); cudaFree(out); cudaFree(bands);
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "autotune buffers");
+  }
+  int best = 0;
+  double bms = 1e300;
+  for (int p : cand) {
+    cbs_desc dd = *d;
+    dd.segments = p;
+    if (bands) dd.bands = bands;
+    cbs_plan* P = nullptr;
+    if (cbs_plan_create(&P, &dd) != CBS_OK) continue;  // not admissible for this kernel
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; w++) ok = cbs_solve(P, in, out, nullptr) == CBS_OK;
+    float ms = 0.f;
+    if (ok) {
+      cudaEventRecord(e0, nullptr);
+      for (int k = 0; k < reps && ok; k++) ok = cbs_solve(P, in, out, nullptr) == CBS_OK;
+      cudaEventRecord(e1, nullptr);
+      ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    }
+    cbs_plan_destroy(P);
+    if (ok && ms / reps < bms) {
+      bms = ms / reps;
+      best = p;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(in);
+  cudaFree(out);
+  if (bands) cudaFree(bands);
+  if (!best) return fail(CBS_ERR_UNSUPPORTED, "no admissible partition count for this descriptor");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[tune_key(d)] = best;
+  }
+  if (best_segments) *best_segments = best;
+  if (best_ms) *best_ms = bms;
   return CBS_OK;
 }
 

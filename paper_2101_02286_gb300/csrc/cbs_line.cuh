@@ -169,6 +169,21 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   }
   return __hiloint2double((int)hw, (int)lw);
 }
+// FP32 -> FP64 for normal numbers and zero only (5 integer operations plus
+// a zero test); subnormal FP32 inputs become zero, inf/nan are not handled.
+// Used for the refinement's output, whose values are normal or zero.
+__device__ __forceinline__ double f32_to_f64_normal(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned mag = u & 0x7fffffffu;
+  unsigned hw = ((mag >> 3) + 0x38000000u) | (u & 0x80000000u);
+  unsigned lw = u << 29;
+  if (mag < 0x00800000u) {  // zero (or subnormal): signed zero
+    hw = u & 0x80000000u;
+    lw = 0u;
+  }
+  return __hiloint2double((int)hw, (int)lw);
+}
+
 // The double at or toward zero from hi + lo (exact when the pair spans <= 53
 // bits) for |lo| <= ulp(hi) as produced by two_sum; integer arithmetic on the
 // 53-bit significand.  Outside the normal FP32 range the result is hi alone.
@@ -244,6 +259,57 @@ __device__ __forceinline__ void partition_of(const DevLineTables& t, int i, int&
   }
 }
 
+// Residual r = b - A x for whole-size partitions of a symmetric band with
+// unit diagonal (the Toeplitz plans): r_k = b_k - x_k - sum_q a_q (x_{k-q} +
+// x_{k+q}); each x-pair sum and band product is formed exactly (two-sum,
+// two-product), the unit diagonal needs no product.  Same accuracy as
+// residual_df with fewer operations.
+template <int R, int M, bool XLO, typename X>
+__device__ __forceinline__ void residual_sym(const float (&bh)[M], const float (&bl)[M], const float (&xh)[M],
+                                             const float (&xl)[M], float (&res)[M], const int i,
+                                             const DevLineTables& t, X& xch) {
+  const int p = t.p;
+  const int prev = (i == 0) ? p - 1 : i - 1;
+  const int next = (i + 1 >= p) ? 0 : i + 1;
+  float ph[R], pl[R], nh[R], nl[R];  // last R rows of the previous partition, first R of the next
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    ph[e] = xch.get(xh[M - R + e], prev);
+    nh[e] = xch.get(xh[e], next);
+    pl[e] = XLO ? xch.get(xl[M - R + e], prev) : 0.f;
+    nl[e] = XLO ? xch.get(xl[e], next) : 0.f;
+    if (!t.cyclic) {
+      if (i == 0) ph[e] = pl[e] = 0.f;
+      if (i + 1 >= p) nh[e] = nl[e] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < M; k++) {
+    const f2 s0 = two_sum(bh[k], -xh[k]);
+    float ah = s0.hi;
+    float al = bl[k] + s0.lo;
+    if (XLO) al -= xl[k];
+#pragma unroll
+    for (int q = 1; q <= R; q++) {
+      const float mh = (k - q >= 0) ? xh[(k - q >= 0) ? k - q : 0] : ph[(k - q >= 0) ? 0 : R + k - q];
+      const float uh = (k + q < M) ? xh[(k + q < M) ? k + q : 0] : nh[(k + q < M) ? 0 : k + q - M];
+      const f2 sx = two_sum(mh, uh);
+      const float aH = t.bandHi[R + q], aL = t.bandLo[R + q];
+      const f2 pr = two_prod(aH, sx.hi);
+      const f2 s1 = two_sum(ah, -pr.hi);
+      ah = s1.hi;
+      float lo = s1.lo - pr.lo - __fmaf_rn(aH, sx.lo, aL * sx.hi);
+      if (XLO) {
+        const float ml = (k - q >= 0) ? xl[(k - q >= 0) ? k - q : 0] : pl[(k - q >= 0) ? 0 : R + k - q];
+        const float ul = (k + q < M) ? xl[(k + q < M) ? k + q : 0] : nl[(k + q < M) ? 0 : k + q - M];
+        lo -= aH * (ml + ul);
+      }
+      al += lo;
+    }
+    res[k] = ah + al;
+  }
+}
+
 // ------------------------------------------------- interface messages
 // The paper's sendToPartition / getFromPartition (Algorithms 1-4): value of
 // `v` held by partition `src`.  Within a line group of a warp the message is
@@ -287,7 +353,7 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size_rt, co
   constexpr int F = 2 * R + 1;
   constexpr int NB = M - R;  // max bulk rows
   const int N = size - R;
-  const bool big = i < t.count_big;
+  const bool big = FULL || i < t.count_big;  // whole-size partitions are all "big"
   const int pw = t.pw, p = t.p;
 
   // a2: forward elimination of the bulk block
@@ -691,8 +757,14 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   TOut* gout = (TOut*)out_ptr + tr.base + (int64_t)g * n;
 
   // ---- gather: w[KS + k] = row start + k, w[q] = row start - KS + q, hh[q] = row start + size + q
+  // (the refinement mode gathers straight into FP32 pairs below)
   TW w[M + KS], hh[KA];
-  if constexpr (DIRECT) {
+  if constexpr (MODE == kModeRefine) {
+    if constexpr (!DIRECT) {
+      tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
+      __syncthreads();
+    }
+  } else if constexpr (DIRECT) {
     constexpr int V = 16 / sizeof(TIn);
     if (FULL && (M % V) == 0) {
 #pragma unroll
@@ -756,29 +828,77 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
 #pragma unroll
     for (int k = 0; k < M; k++) xo[k] = conv<TOut>(v[k]);
   } else {
-    // FP32 bulk + FP64-accurate residual refinement.
+    // FP32 bulk + FP64-accurate residual refinement.  Every element is split
+    // into an FP32 pair as soon as it is loaded.
     float bh[M], bl[M];
-    if (KS == 0) {
+    float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
+    if constexpr (DIRECT) {
+      constexpr int V = 16 / sizeof(TIn);
+      if (FULL && (M % V) == 0) {
 #pragma unroll
-      for (int k = 0; k < M; k++) {
-        const f2 sv = split_in(w[KS + k]);
-        bh[k] = sv.hi;
-        bl[k] = sv.lo;
-      }
-    } else {
-      float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
+        for (int k = 0; k < M; k += V) {
+          TIn tmp[V];
+          if (ok) V16<TIn, V>::ld(gin + start + k, tmp);
+          else {
 #pragma unroll
-      for (int u = 0; u < M + KS; u++) {
-        const f2 sv = split_in(w[u]);
-        fh[u] = sv.hi;
-        fl[u] = sv.lo;
+            for (int u = 0; u < V; u++) tmp[u] = TIn(0);
+          }
+#pragma unroll
+          for (int u = 0; u < V; u++) {
+            const f2 sv = split_in(tmp[u]);
+            fh[KS + k + u] = sv.hi;
+            fl[KS + k + u] = sv.lo;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+          const f2 sv = split_in((ok && k < size) ? __ldg(gin + start + k) : TIn(0));
+          fh[KS + k] = sv.hi;
+          fl[KS + k] = sv.lo;
+        }
       }
 #pragma unroll
       for (int q = 0; q < KS; q++) {
-        const f2 sv = split_in(hh[q]);
-        hhh[q] = sv.hi;
-        hhl[q] = sv.lo;
+        int rlo = start - KS + q;
+        rlo += (rlo < 0) ? n : 0;
+        const f2 a0 = split_in(ok ? __ldg(gin + rlo) : TIn(0));
+        fh[q] = a0.hi;
+        fl[q] = a0.lo;
+        int rhi = start + size + q;
+        rhi -= (rhi >= n) ? n : 0;
+        const f2 a1 = split_in(ok ? __ldg(gin + rhi) : TIn(0));
+        hhh[q] = a1.hi;
+        hhl[q] = a1.lo;
       }
+    } else {
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const f2 sv = split_in((ok && (FULL || k < size)) ? SL[k * t.sp + i] : TT(0));
+        fh[KS + k] = sv.hi;
+        fl[KS + k] = sv.lo;
+      }
+#pragma unroll
+      for (int q = 0; q < KS; q++) {
+        int rlo = start - KS + q;
+        rlo += (rlo < 0) ? n : 0;
+        const f2 a0 = split_in(ok ? SL[slot_of(t, rlo)] : TT(0));
+        fh[q] = a0.hi;
+        fl[q] = a0.lo;
+        int rhi = start + size + q;
+        rhi -= (rhi >= n) ? n : 0;
+        const f2 a1 = split_in(ok ? SL[slot_of(t, rhi)] : TT(0));
+        hhh[q] = a1.hi;
+        hhl[q] = a1.lo;
+      }
+    }
+    if (KS == 0) {
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        bh[k] = fh[KS + k];
+        bl[k] = fl[KS + k];
+      }
+    } else {
       // a1 in double-float: b = sum_q w_q (f_{k+q} - f_{k-q})
 #pragma unroll
       for (int k = 0; k < M; k++) {
@@ -812,41 +932,43 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       }
     }
     // sweep 0: x0 = A^{-1} bh
-    float xh[M], xl[M], v[M];
+    float xh[M], v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) v[k] = bh[k];
     solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
 #pragma unroll
-    for (int k = 0; k < M; k++) {
-      xh[k] = v[k];
-      xl[k] = 0.f;
-    }
-    // refinement sweeps: x <- x + A^{-1}(b - A x), residual to FP64 accuracy
-    for (int sw = 0; sw < a.sweeps; sw++) {
-      if (sw == 0) residual_df<R, M, false, FULL>(bh, bl, xh, xl, v, size, i, t, wx);
+    for (int k = 0; k < M; k++) xh[k] = v[k];
+    // refinement sweep 1: x <- x0 + A^{-1}(b - A x0), residual to FP64 accuracy
+    if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, wx);
+    else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, wx);
+    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
+    if (a.sweeps < 2) {
+      // x = x0 + delta: one FP64 add per unknown (the FP32 path leaves the
+      // FP64 pipe idle otherwise); exact integer conversions
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const double xd = f32_to_f64_normal(xh[k]) + f32_to_f64_normal(v[k]);
+        if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
+        else xo[k] = (TOut)(xh[k] + v[k]);
+      }
+    } else {
+      // sweep 2 on the unevaluated pair x = xh + xl
+      float xl[M];
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const f2 sm = two_sum(xh[k], v[k]);
+        xh[k] = sm.hi;
+        xl[k] = sm.lo;
+      }
+      if constexpr (FULL) residual_sym<R, M, true>(bh, bl, xh, xl, v, i, t, wx);
       else residual_df<R, M, true, FULL>(bh, bl, xh, xl, v, size, i, t, wx);
       solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
-      if (sw + 1 < a.sweeps) {
 #pragma unroll
-        for (int k = 0; k < M; k++) {
-          const f2 sm = two_sum(xh[k], v[k]);
-          xh[k] = sm.hi;
-          xl[k] = xl[k] + sm.lo;
-        }
-      } else {
-        // x = xh + (xl + delta): one FP64 add per unknown (the FP32 path
-        // leaves the FP64 pipe idle otherwise); exact integer conversions
-#pragma unroll
-        for (int k = 0; k < M; k++) {
-          const double xd = f32_to_f64(xh[k]) + f32_to_f64(xl[k] + v[k]);
-          if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
-          else xo[k] = (TOut)xh[k];
-        }
+      for (int k = 0; k < M; k++) {
+        const double xd = f32_to_f64_normal(xh[k]) + f32_to_f64_normal(xl[k] + v[k]);
+        if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
+        else xo[k] = (TOut)(xh[k] + (xl[k] + v[k]));
       }
-    }
-    if (a.sweeps == 0) {
-#pragma unroll
-      for (int k = 0; k < M; k++) xo[k] = conv<TOut>(xh[k]);
     }
   }
 

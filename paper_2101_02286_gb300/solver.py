@@ -61,12 +61,19 @@ class Plan:
     """A pre-factorised solver for one (shape, direction, operator, precision)."""
 
     def __init__(self, shape_zyx, direction: int, **kw):
+        """kw as for make_desc; segments="tune" times every admissible
+        partition count first (cbs_autotune) and uses the fastest."""
         self.shape = tuple(int(s) for s in shape_zyx)
         self.direction = int(direction)
         self.in_dtype = kw.get("in_dtype", torch.float64)
         prec = kw.get("precision", "fp64")
         self.out_dtype = kw.get("out_dtype") or (torch.float64 if prec != "fp32" else self.in_dtype)
+        tune = kw.get("segments") == "tune"
+        if tune:
+            kw = dict(kw, segments=0)
         self.desc = make_desc(self.shape, direction, **kw)
+        if tune:
+            self.desc.segments, self.tuned_ms = abi.cbs_autotune(self.desc)
         self.handle = abi.cbs_plan_create(self.desc)
 
     def info(self) -> dict:

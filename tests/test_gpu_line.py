@@ -134,3 +134,21 @@ def test_invalid_arguments(cuda):
     with pytest.raises(abi.CbsError):
         abi.cbs_solve(plan.handle, 0, x.data_ptr(), 0)
     plan.close()
+
+
+def test_autotune_picks_admissible_and_caches(cuda):
+    from paper_2101_02286_gb300.solver import make_desc
+    shape = (4, 16, 384)
+    d = make_desc(shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=W.LELE6_TRI["rhs"], h=W.grid_spacing(384))
+    p, ms = abi.cbs_autotune(d, 3)
+    assert 1 <= p <= 32 and ms > 0
+    # a plan with segments = 0 now uses the cached choice
+    plan = Plan(shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=W.LELE6_TRI["rhs"], h=W.grid_spacing(384))
+    assert plan.info()["segments"] == p
+    f = np.random.default_rng(1).uniform(-1, 1, size=shape)
+    y = plan.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert oracle.rel_err(y, oracle_derivative(f, 0, "tri6")) < 1e-12
+    plan.close()
+    tuned = Plan(shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=W.LELE6_TRI["rhs"], h=W.grid_spacing(384), segments="tune")
+    assert tuned.info()["segments"] >= 1
+    tuned.close()
