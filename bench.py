@@ -2,15 +2,21 @@
 
 One step = the whole hot path over one field: the cyclic tridiagonal
 derivative (Lele 6th order, alpha = 1/3) along x (contiguous), y and z
-(strided), each = stencil + per-partition solve + FP64 interface PCR +
-back-substitution (+ refinement), i.e. 3 x 512^3 unknowns.
+(strided), each = stencil + per-partition solve + interface block PCR +
+back-substitution (+ refinement), i.e. 3 x 512^3 unknowns.  The partition
+count of each direction is picked by the library's autotuner.
 
 The headline path is FP32 bulk + FP64-accurate refinement (one sweep), whose
 error against the FP64 oracle is <= 1e-12; the plain FP64 path is timed on
 the same field and reported beside it.  Inputs (1 GiB) exceed the 129 MB L2,
-so no flush is needed between steps.
+so no flush is needed between steps.  The other workloads of the method
+(64^3 Fourier field, 32 long pentadiagonal lines, a ragged batch of 48 grids
+under a CUDA graph, the 256^3 variable-alpha forward and adjoint) are timed
+after it and reported under "other_workloads", each with its error against
+the FP64 oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--size N] [--profile] [--no-configs] [--cpu-seconds S]
 
 Under torchrun each rank solves its own 512^3 field (independent lines, no
 data exchange: weak scaling); rank 0 prints one JSON line.
@@ -34,7 +40,7 @@ UNKNOWNS_PER_STEP = 3 * N ** 3
 METRIC = "Gunknowns/s (3 x 512^3 cyclic tridiagonal 6th-order derivatives, x/y/z, <=1e-12 rel err)"
 CONFIG = {"workload": "512^3 periodic FP64 field, Lele 6th-order cyclic tridiagonal first derivative "
                       "along x, y and z (3 x 262144 systems of n=512)",
-          "grid": [N, N, N], "scheme": "alpha=1/3, a=14/9, b=1/9", "segments": "auto",
+          "grid": [N, N, N], "scheme": "alpha=1/3, a=14/9, b=1/9", "segments": "autotuned",
           "l2": "inputs (1 GiB FP64) larger than L2; no flush"}
 
 
@@ -47,6 +53,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--size", type=int, default=N,
                     help="grid points per axis (512 = the benchmark workload; smaller for profiling)")
+    ap.add_argument("--profile", action="store_true",
+                    help="headline solves only (W + K steps of x, y, z), for profiler captures")
+    ap.add_argument("--segments", default="tune",
+                    help="partitions per line: 'tune' (autotuner) or a fixed count")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (64^3 Fourier, long lines, ragged batch, variable alpha)")
     return ap.parse_args()
 
 
@@ -165,6 +177,192 @@ def run_reference(args):
         "e2e": {"value": val, "unit": "Gunknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+
+def nvtx(torch, label):
+    """Push (label) or pop (None) an NVTX range; a no-op where NVTX is absent."""
+    try:
+        torch.cuda.nvtx.range_push(label) if label else torch.cuda.nvtx.range_pop()
+    except (RuntimeError, AttributeError):
+        pass
+
+
+# ---------------------------------------------------------------- traffic record
+KERNEL_SOURCES = ("paper_2101_02286_gb300/csrc/cbs_line.cuh", "paper_2101_02286_gb300/csrc/cbs_line_launch.cuh",
+                  "paper_2101_02286_gb300/csrc/cbs_internal.h")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel: str, size: int):
+    """DRAM bytes per launch of `kernel` from an ncu capture summarised under
+    profiles/ (a line 'traffic-record: kernel=K size=S source=H bytes=B'), or
+    None when no record exists or the kernel sources changed since."""
+    d = os.path.join(ROOT, "profiles")
+    want = kernel_source_hash()
+    try:
+        names = sorted(os.listdir(d))
+    except OSError:
+        return None
+    for name in names:
+        if not name.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(d, name)):
+            if not line.startswith("traffic-record:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("kernel") == kernel and kv.get("size") == str(size) and kv.get("source") == want:
+                return float(kv["bytes"])
+    return None
+
+
+# ---------------------------------------------------------------- other workloads
+def time_ms(fn, stream, steps: int, warmup: int = 3) -> float:
+    """Average device time of fn() (CUDA events on `stream`, warm-ups first)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _entry(workload, unknowns, ms, bytes_per_unknown, hbm, err, **extra):
+    gbs = bytes_per_unknown * unknowns / (ms * 1e-3) / 1e9
+    return dict({"workload": workload, "value": unknowns / (ms * 1e-3) / 1e9, "unit": "Gunknowns/s", "ms": ms,
+                 "algorithmic_bytes_per_unknown": bytes_per_unknown, "achieved_gbs": gbs, "hbm_frac": gbs / hbm,
+                 "max_rel_err": err}, **extra)
+
+
+def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
+    """The four other workloads of the method, each timed on `stream` and
+    checked against the FP64 oracle (whole output or sampled lines)."""
+    import numpy as np
+    import torch
+    from paper_2101_02286_gb300 import abi
+    from paper_2101_02286_gb300 import workloads as W
+    from paper_2101_02286_gb300.autograd import variable_plan
+    from paper_2101_02286_gb300.solver import Batch, Plan
+    if check:
+        import oracle
+    res = []
+    rng = np.random.default_rng(17)
+
+    # 64^3 Fourier field, x-derivative, 4 partitions per line, FP64 (fits in L2)
+    f64, _ = W.fourier_cube(64, 8)
+    sch = W.LELE6_TRI
+    h = W.grid_spacing(64)
+    pl = Plan(f64.shape, 0, lhs=sch["lhs"], rhs=sch["rhs"], h=h, segments=4, precision="fp64")
+    fi = torch.from_numpy(f64).to(dev)
+    fo = torch.empty_like(fi)
+    ms = time_ms(lambda: pl.solve(fi, fo, stream), stream, max(steps, 20))
+    err = oracle.rel_err(fo.cpu().numpy(), oracle.derivative(f64, sch["lhs"], sch["rhs"], h)) if check else None
+    res.append(_entry("64^3 sum of 8 plane waves, x-derivative, tri 6th order, p=4, fp64 (L2-resident)",
+                      64 ** 3, ms, 16, hbm, err, segments=4))
+    pl.close()
+    del fi, fo
+
+    # long lines: 32 x 2^22 cyclic pentadiagonal, FP32 right-hand side, FP64 solution
+    d = W.long_lines()
+    lines, n = d.shape
+    di = torch.from_numpy(d.reshape(1, lines, n)).to(dev)
+    do = torch.empty((1, lines, n), dtype=torch.float64, device=dev)
+    for prec, sweeps in (("fp32_refine", 2), ("fp64", 1)):
+        pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=1024, precision=prec,
+                  sweeps=sweeps, in_dtype=torch.float32)
+        ms = time_ms(lambda: pl.solve(di, do, stream), stream, steps)
+        err = None
+        if check:
+            k = int(rng.integers(0, lines))
+            ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d[k:k + 1].astype(np.float64))
+            err = oracle.rel_err(do[0, k:k + 1].cpu().numpy(), ref)
+        res.append(_entry("32 x 2^22 cyclic penta (1/20,1/2,1,1/2,1/20), N(0,1) rhs stored FP32, FP64 out, "
+                          "p=1024 segments across CTAs, %s sweeps=%d" % (prec, sweeps),
+                          lines * n, ms, 12, hbm, err, segments=1024, precision=prec, sampled_lines=1))
+        pl.close()
+    del di, do, d
+
+    # ragged batch: 48 grids, one persistent launch replayed from a CUDA graph
+    items = W.ragged_batch()
+    specs = []
+    for it in items:
+        nn = it.shape_zyx[2 - it.direction]
+        sc = W.LELE6_TRI if it.scheme == "tri6" else W.PENTA10
+        specs.append((it.shape_zyx, it.direction,
+                      dict(lhs=sc["lhs"], rhs=sc["rhs"], h=W.grid_spacing(nn), precision=it.precision,
+                           sweeps=2 if (it.scheme == "penta10" and it.precision == "fp32_refine") else 1)))
+    b = Batch(specs)
+    ins = [torch.from_numpy(it.f).to(dev) for it in items]
+    outs = [torch.empty_like(x) for x in ins]
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    b.solve(ins, outs, side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        b.solve(ins, outs, side)
+    unk = sum(int(np.prod(it.shape_zyx)) for it in items)
+    ms = time_ms(g.replay, stream, steps)
+    err = None
+    if check:
+        err = 0.0
+        for it, y in zip(items, outs):
+            ax = 2 - it.direction
+            sc = W.LELE6_TRI if it.scheme == "tri6" else W.PENTA10
+            nn = it.shape_zyx[ax]
+            fl = np.moveaxis(it.f, ax, -1)
+            other = fl.shape[:2]
+            idx = [(int(rng.integers(0, other[0])), int(rng.integers(0, other[1]))) for _ in range(4)]
+            sel = np.stack([fl[i, j] for i, j in idx])
+            ref = oracle.derivative(sel, sc["lhs"], sc["rhs"], W.grid_spacing(nn))
+            yl = np.moveaxis(y.cpu().numpy(), ax, -1)
+            err = max(err, oracle.rel_err(np.stack([yl[i, j] for i, j in idx]), ref))
+    res.append(_entry("ragged batch of 48 grids (sizes from {32..384} per axis, seed 3), mixed tri/penta, "
+                      "fp64/fp32_refine, one persistent launch under a CUDA graph", unk, ms, 16, hbm, err,
+                      problems=len(items), launches_per_step=abi.cbs_last_launch_count(), sampled_lines=4 * len(items)))
+    b.close()
+    del ins, outs, items, g
+
+    # variable alpha: 256^3, forward and adjoint, FP64 and FP32 (x lines)
+    f, al = W.variable_alpha_cube(256)
+    c4 = W.CENTRAL4["rhs"]
+    hv = W.grid_spacing(256)
+    gseed = np.random.default_rng(18).standard_normal(f.shape)
+    for prec, dt, bpu_f, bpu_b in (("fp64", torch.float64, 24, 40), ("fp32", torch.float32, 12, 20)):
+        fa, aa, ga = (torch.from_numpy(a).to(dev, dt) for a in (f, al, gseed))
+        pl = variable_plan(f.shape, 0, aa, c4, hv, prec)
+        x = torch.empty_like(fa)
+        gf, gal = torch.empty_like(fa), torch.empty_like(fa)
+        ms_f = time_ms(lambda: pl.solve(fa, x, stream), stream, steps)
+        ms_b = time_ms(lambda: abi.cbs_solve_transpose(pl.handle, ga.data_ptr(), x.data_ptr(), None, gf.data_ptr(),
+                                                       gal.data_ptr(), stream.cuda_stream), stream, steps)
+        ef = eb = None
+        if check:
+            ii = rng.integers(0, 256, size=(32, 2))
+            pick = lambda a: np.stack([a[i, j] for i, j in ii])
+            src = [pick(a.double().cpu().numpy()) for a in (fa, aa, ga)]
+            gfr, gar, _, xr = oracle.adjoint_variable_tri(src[0], src[1], src[2], c4, hv, axis=-1)
+            ef = oracle.rel_err(pick(x.double().cpu().numpy()), xr)
+            eb = max(oracle.rel_err(pick(gf.double().cpu().numpy()), gfr),
+                     oracle.rel_err(pick(gal.double().cpu().numpy()), gar))
+        w = "256^3 variable alpha ~ U(0.2,0.4), 4th-order central rhs, x lines, %s" % prec
+        res.append(_entry(w + ", forward", 256 ** 3, ms_f, bpu_f, hbm, ef, sampled_lines=32))
+        res.append(_entry(w + ", adjoint (grad f and grad alpha)", 256 ** 3, ms_b, bpu_b, hbm, eb, sampled_lines=32))
+        pl.close()
+    return res
+
 # ---------------------------------------------------------------- GPU
 def main():
     args = parse()
@@ -194,14 +392,31 @@ def main():
     sch = W.LELE6_TRI
 
     def make(prec):
-        return [Plan(f.shape, d, lhs=sch["lhs"], rhs=sch["rhs"], h=h, precision=prec, sweeps=1) for d in range(3)]
+        # partition count per direction picked by the library's autotuner
+        seg = "tune" if args.segments == "tune" else int(args.segments)
+        return [Plan(f.shape, d, lhs=sch["lhs"], rhs=sch["rhs"], h=h, precision=prec, sweeps=1, segments=seg)
+                for d in range(3)]
 
-    plans = {"fp32_refine": make("fp32_refine"), "fp64": make("fp64")}
-    outs = [torch.empty_like(f) for _ in range(3)]
+    plans = {"fp32_refine": make("fp32_refine")}
+    if args.profile:
+        outs = [torch.empty_like(f)] * 3  # one output buffer keeps captures small
+    else:
+        outs = [torch.empty_like(f) for _ in range(3)]
 
     def step(ps):
         for d in range(3):
             ps[d].solve(f, outs[d], stream)
+
+    if args.profile:
+        # headline solves only: W warm-up steps, then K steps (x, y, z each)
+        for _ in range(args.warmup + args.steps):
+            step(plans["fp32_refine"])
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"profile": True, "size": n, "steps": args.steps, "warmup": args.warmup,
+                              "segments": [p.info()["segments"] for p in plans["fp32_refine"]]}))
+        return
+    plans["fp64"] = make("fp64")
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -209,12 +424,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(ps, steps, warmup):
+    def timed(ps, steps, warmup, label):
         for _ in range(warmup):
             step(ps)
         barrier()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev_dir = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        nvtx(torch, label)  # lets a profiler select the timed launches
         ev[0].record(stream)
         for s in range(steps):
             ev_dir[s][0].record(stream)
@@ -222,6 +438,7 @@ def main():
                 ps[d].solve(f, outs[d], stream)
                 ev_dir[s][d + 1].record(stream)
         ev[1].record(stream)
+        nvtx(torch, None)
         barrier()
         ms = ev[0].elapsed_time(ev[1]) / steps
         per_dir = [sum(ev_dir[s][d].elapsed_time(ev_dir[s][d + 1]) for s in range(steps)) / steps
@@ -233,8 +450,8 @@ def main():
     sampler = ClockSampler(local)
     with sampler:
         time.sleep(0.3)
-        ms_ref, dir_ref = timed(plans["fp32_refine"], args.steps, max(args.warmup, 3))
-        ms_64, dir_64 = timed(plans["fp64"], max(3, args.steps // 2), 3)
+        ms_ref, dir_ref = timed(plans["fp32_refine"], args.steps, max(args.warmup, 3), "headline")
+        ms_64, dir_64 = timed(plans["fp64"], max(3, args.steps // 2), 3, "fp64_path")
         for _ in range(max(1, int(0.3 / max(ms_ref * 1e-3, 1e-4)))):  # keep the GPU busy while sampling
             step(plans["fp32_refine"])
         barrier()
@@ -289,7 +506,12 @@ def main():
         hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
         bytes_per_launch = 16.0 * n ** 3  # read f (FP64), write f' (FP64)
         kdir = max(range(3), key=lambda d: dir_ref[d])
-        achieved = bytes_per_launch / (sum(dir_ref) / 3 * 1e-3) / 1e9
+        # dominant kernel: the shared-memory-staged variant that runs the y and
+        # z lines (two of the three launches of a step, the longer ones)
+        ms_yz = (dir_ref[1] + dir_ref[2]) / 2
+        achieved = bytes_per_launch / (ms_yz * 1e-3) / 1e9
+        achieved_x = bytes_per_launch / (dir_ref[0] * 1e-3) / 1e9
+        traffic = traffic_record("line_kernel_refine_yz", n)
         # FP64 path: bound by the FP64 pipe; 15 algorithmic FP64 flops per unknown
         fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
         fp64_flops = 15.0 * n ** 3
@@ -297,6 +519,7 @@ def main():
         clocks = sampler.summary()
         units = 3 * n ** 3
         value = job_throughput(units, world, ms_ref)
+        others = [] if args.no_configs else other_configs(dev, stream, max(5, args.steps // 2), hbm, check=True)
         cpu_v, cores, sample = oracle_sample(args.cpu_seconds) if args.cpu_seconds > 0 else (None, None, "skipped")
         rec = {
             "metric": METRIC, "value": value, "unit": "Gunknowns/s", "n_gpus": world, "steps": args.steps,
@@ -304,16 +527,21 @@ def main():
             "vs_baseline": None, "dtype": "f32 (FP64-accurate residual via FP32 error-free transforms)",
             "data": "synthetic (seeded U(-1,1) + one plane wave, numpy PCG64 seed 1)",
             "config": dict(CONFIG, grid=[n, n, n], parallelism="replicas" if world > 1 else "single GPU",
-                           precision="fp32_refine",
-                           sweeps=1, segments=plans["fp32_refine"][0].info()["segments"]),
+                           precision="fp32_refine", sweeps=1,
+                           segments=[p.info()["segments"] for p in plans["fp32_refine"]]),
             "max_rel_err": err.get("fp32_refine"),
             "ms_per_direction": dir_ref,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_source": hbm_src,
-                         "kernel": "line_kernel<R=1,M=16,refine,K=2>", "slowest_direction": "xyz"[kdir]},
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": hbm_src,
+                         "kernel": "line_kernel refine, shared-memory staged (y and z lines)",
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_yz,
+                         "slowest_direction": "xyz"[kdir]},
+            "roofline_x": {"bound": "hbm", "achieved": achieved_x, "peak": hbm, "unit": "GB/s",
+                           "frac": achieved_x / hbm, "kernel": "line_kernel refine, direct 16-byte loads (x lines)",
+                           "ms_per_launch": dir_ref[0]},
             "fp64_path": {"value": job_throughput(units, world, ms_64), "unit": "Gunknowns/s",
                           "ms_per_step": ms_64, "ms_per_direction": dir_64, "max_rel_err": err.get("fp64"),
-                          "segments": plans["fp64"][0].info()["segments"],
+                          "segments": [p.info()["segments"] for p in plans["fp64"]],
                           "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak_tflops,
                                        "unit": "TFLOP/s (FP64)", "frac": fp64_ach / fp64_peak_tflops,
                                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
@@ -326,6 +554,7 @@ def main():
             "clocks": clocks,
             "cpu_baseline": {"value": cpu_v, "unit": "Gunknowns/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
+            "other_workloads": others,
         }
         print(json.dumps(rec))
     for ps in plans.values():

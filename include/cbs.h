@@ -120,6 +120,13 @@ typedef struct cbs_plan_info {
     int32_t kernel;           /* implementation id (0 = on-chip lines, 1 = long lines) */
     int32_t threads_per_line;
     int64_t lines;            /* independent systems in one solve                   */
+    /* Stages of the interface solve that exchange values between partitions:
+     * a stage whose coupling blocks are below 2^-60 (FP64) or 2^-30 (FP32) of
+     * its diagonal blocks reduces to a local product (the blocks shrink
+     * geometrically with the partition size and square at every PCR step).
+     * inner_*: the segment-level system of a long-line plan (kernel 1). */
+    int32_t message_stages, message_stages_f32;
+    int32_t inner_message_stages, inner_message_stages_f32;
 } cbs_plan_info;
 
 /* Create a plan: validates the descriptor, chooses p when segments == 0,

@@ -67,6 +67,8 @@ class cbs_plan_info(ctypes.Structure):
         ("pcr_steps", ctypes.c_int32), ("detach_steps", ctypes.c_int32), ("detached_rows", ctypes.c_int32),
         ("stage_count", ctypes.c_int32), ("kernel", ctypes.c_int32), ("threads_per_line", ctypes.c_int32),
         ("lines", ctypes.c_int64),
+        ("message_stages", ctypes.c_int32), ("message_stages_f32", ctypes.c_int32),
+        ("inner_message_stages", ctypes.c_int32), ("inner_message_stages_f32", ctypes.c_int32),
     ]
 
 

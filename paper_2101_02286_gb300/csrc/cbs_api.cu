@@ -207,7 +207,10 @@ cbs_status fill_dev_tables(DevLineTables& D, const LineTables& T, const Bands& A
   D.count_big = T.count_big;
   D.nstage = ns;
   D.cyclic = T.cyclic ? 1 : 0;
-  for (int st = 0; st < ns && st < kMaxStages; st++) D.stage_has_c[st] = T.stage_has_c[st];
+  for (int st = 0; st < ns && st < kMaxStages; st++) {
+    D.stage_has_c[st] = T.stage_has_c[st];
+    D.stage_msg[st] = T.stage_msg[st];
+  }
   // shared-memory tile geometry (see tile_copy): sp odd, lsz chosen so the
   // lanes of different lines in one wavefront hit different banks
   {
@@ -382,6 +385,7 @@ cbs_status cbs_interface_model(const cbs_desc* d, int32_t p, double* dhat, doubl
     std::vector<double> x(bhat, bhat + (size_t)p * r), y((size_t)p * r);
     const int rr = r * r;
     for (int s = 0; s < (int)T.stages.size(); s++) {
+      const bool msg = (T.stage_msg[s] & 1) != 0;  // FP64 kernels skip the rest
       for (int i = 0; i < p; i++) {
         const int sm = T.src[(size_t)(s * 2 + 0) * p + i], sp = T.src[(size_t)(s * 2 + 1) * p + i];
         for (int q = 0; q < r; q++) {
@@ -390,7 +394,8 @@ cbs_status cbs_interface_model(const cbs_desc* d, int32_t p, double* dhat, doubl
             const double C = T.coef[((size_t)(s * 3 + 0) * rr + q * r + e) * p + i];
             const double KM = T.coef[((size_t)(s * 3 + 1) * rr + q * r + e) * p + i];
             const double KP = T.coef[((size_t)(s * 3 + 2) * rr + q * r + e) * p + i];
-            acc += C * x[(size_t)i * r + e] - KM * x[(size_t)sm * r + e] - KP * x[(size_t)sp * r + e];
+            acc += C * x[(size_t)i * r + e];
+            if (msg) acc -= KM * x[(size_t)sm * r + e] + KP * x[(size_t)sp * r + e];
           }
           y[(size_t)i * r + q] = acc;
         }
@@ -577,6 +582,17 @@ cbs_status cbs_plan_info_get(const cbs_plan* P, cbs_plan_info* info) {
   info->kernel = P->kind;
   info->threads_per_line = P->kind == 1 ? P->inner_threads : P->dev.pw;
   info->lines = P->nlines;
+  auto count = [](const LineTables& T, int bit) {
+    int c = 0;
+    for (int m : T.stage_msg) c += (m & bit) ? 1 : 0;
+    return c;
+  };
+  info->message_stages = count(P->host, 1);
+  info->message_stages_f32 = count(P->host, 2);
+  if (P->kind == 1) {
+    info->inner_message_stages = count(P->inner, 1);
+    info->inner_message_stages_f32 = count(P->inner, 2);
+  }
   return CBS_OK;
 }
 

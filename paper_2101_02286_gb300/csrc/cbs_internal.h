@@ -57,6 +57,10 @@ struct LineTables {
   std::vector<double> coef;
   std::vector<int> src;
   std::vector<int> stage_has_c;  // 1 when C != I for some lane
+  // bit 0 (FP64) / bit 1 (FP32): the stage's coupling blocks KM, KP exceed
+  // rounding in that precision, so the stage needs the neighbours' values;
+  // otherwise it reduces to x~ <- C x~ (or nothing when C = I).
+  std::vector<int> stage_msg;
   // schedule counts (Sec. 4)
   int pcr_steps = 0, detach_steps = 0, detached_rows = 0;
   // Reduced system blocks before PCR (for introspection/tests): W = D-hat,
@@ -101,6 +105,7 @@ struct DevLineTables {
   int rows_big, rows_small, count_big;
   int nstage, cyclic;
   int stage_has_c[kMaxStages];
+  int stage_msg[kMaxStages];   // see LineTables::stage_msg
   // shared-memory tile: line slot S[l*lsz + k*sp + i] holds row k of partition i
   int lsz, sp, bound;          // bound = count_big * rows_big
   unsigned mag_b, mag_s;       // ceil(2^32 / rows_big), ceil(2^32 / rows_small)

@@ -274,10 +274,9 @@ __device__ __forceinline__ void residual_sym(const float (&bh)[M], const float (
   float ph[R], pl[R], nh[R], nl[R];  // last R rows of the previous partition, first R of the next
 #pragma unroll
   for (int e = 0; e < R; e++) {
-    ph[e] = xch.get(xh[M - R + e], prev);
-    nh[e] = xch.get(xh[e], next);
-    pl[e] = XLO ? xch.get(xl[M - R + e], prev) : 0.f;
-    nl[e] = XLO ? xch.get(xl[e], next) : 0.f;
+    xch.get_two(xh[M - R + e], prev, xh[e], next, ph[e], nh[e]);
+    pl[e] = nl[e] = 0.f;
+    if (XLO) xch.get_two(xl[M - R + e], prev, xl[e], next, pl[e], nl[e]);
     if (!t.cyclic) {
       if (i == 0) ph[e] = pl[e] = 0.f;
       if (i + 1 >= p) nh[e] = nl[e] = 0.f;
@@ -316,29 +315,70 @@ __device__ __forceinline__ void residual_sym(const float (&bh)[M], const float (
 // a shuffle; when the partitions of one system span a whole CTA it goes
 // through a double-buffered shared-memory slot (one barrier per message; all
 // threads of the CTA must exchange in lock step).
+// get2: the value v of partitions a and b (one message round);
+// get_two: va of partition a and vb of partition b (one message round).
 struct WarpXchg {
   int pw;
   template <typename V>
   __device__ __forceinline__ V get(V v, int src) {
     return __shfl_sync(kFull, v, src, pw);
   }
+  template <typename V>
+  __device__ __forceinline__ void get2(V v, int a, int b, V& ra, V& rb) {
+    ra = __shfl_sync(kFull, v, a, pw);
+    rb = __shfl_sync(kFull, v, b, pw);
+  }
+  template <typename V>
+  __device__ __forceinline__ void get_two(V va, int a, V vb, int b, V& ra, V& rb) {
+    ra = __shfl_sync(kFull, va, a, pw);
+    rb = __shfl_sync(kFull, vb, b, pw);
+  }
 };
+constexpr int kCtaXchgSlots = 4;  // 64-bit slots per thread: 2 buffers x 2 values
 struct CtaXchg {
-  unsigned long long* buf;  // 2 * blockDim.x slots
+  unsigned long long* buf;  // kCtaXchgSlots * blockDim.x slots
   int flip;
+  int stride = 1, offset = 0;  // partition src lives in thread src * stride + offset
+  template <typename V>
+  static __device__ __forceinline__ unsigned long long bits(V v) {
+    if constexpr (sizeof(V) == 8) return (unsigned long long)__double_as_longlong((double)v);
+    else return (unsigned long long)__float_as_uint((float)v);
+  }
+  template <typename V>
+  static __device__ __forceinline__ V value(unsigned long long u) {
+    if constexpr (sizeof(V) == 8) return (V)__longlong_as_double((long long)u);
+    else return (V)__uint_as_float((unsigned)u);
+  }
+  // the buffer of this round (alternating, so one barrier per round suffices)
+  __device__ __forceinline__ unsigned long long* round() {
+    unsigned long long* b = buf + flip * 2 * blockDim.x;
+    flip ^= 1;
+    return b;
+  }
   template <typename V>
   __device__ __forceinline__ V get(V v, int src) {
-    unsigned long long* b = buf + flip * blockDim.x;
-    flip ^= 1;
-    if constexpr (sizeof(V) == 8) {
-      b[threadIdx.x] = (unsigned long long)__double_as_longlong((double)v);
-      __syncthreads();
-      return (V)__longlong_as_double((long long)b[src]);
-    } else {
-      b[threadIdx.x] = (unsigned long long)__float_as_uint((float)v);
-      __syncthreads();
-      return (V)__uint_as_float((unsigned)b[src]);
-    }
+    unsigned long long* b = round();
+    b[threadIdx.x] = bits(v);
+    __syncthreads();
+    return value<V>(b[src * stride + offset]);
+  }
+  template <typename V>
+  __device__ __forceinline__ void get2(V v, int a, int b_, V& ra, V& rb) {
+    unsigned long long* b = round();
+    b[threadIdx.x] = bits(v);
+    __syncthreads();
+    ra = value<V>(b[a * stride + offset]);
+    rb = value<V>(b[b_ * stride + offset]);
+  }
+  template <typename V>
+  __device__ __forceinline__ void get_two(V va, int a, V vb, int b_, V& ra, V& rb) {
+    unsigned long long* b = round();
+    const unsigned n = blockDim.x;
+    b[threadIdx.x] = bits(va);
+    b[n + threadIdx.x] = bits(vb);
+    __syncthreads();
+    ra = value<V>(b[a * stride + offset]);
+    rb = value<V>(b[n + b_ * stride + offset]);
   }
 };
 
@@ -415,6 +455,9 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size_rt, co
   // with the W^{-1} products of every stage precomputed in the plan
   constexpr int rr = R * R;
   for (int st = 0; st < t.nstage; st++) {
+    const bool hc = t.stage_has_c[st] != 0;
+    const bool msg = (t.stage_msg[st] & (sizeof(TI) == 8 ? 1 : 2)) != 0;  // uniform over the CTA
+    if (!msg && !hc) continue;  // coupling below rounding and C = I: nothing to do
     int sm = i, sp = i;
     TI C[rr], KM[rr], KP[rr];
     if (t.uniform) {
@@ -441,13 +484,11 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size_rt, co
       for (int e = 0; e < rr; e++) C[e] = KM[e] = KP[e] = TI(0);
     }
     TI xm[R], xp[R];
+    if (msg) {
 #pragma unroll
-    for (int q = 0; q < R; q++) {
-      xm[q] = xch.get(xt[q], sm);
-      xp[q] = xch.get(xt[q], sp);
+      for (int q = 0; q < R; q++) xch.get2(xt[q], sm, sp, xm[q], xp[q]);
     }
     TI nxt[R];
-    const bool hc = t.stage_has_c[st] != 0;
 #pragma unroll
     for (int q = 0; q < R; q++) {
       TI acc;
@@ -458,8 +499,10 @@ __device__ __forceinline__ void solve_partition(T (&v)[M], const int size_rt, co
       } else {
         acc = xt[q];
       }
+      if (msg) {
 #pragma unroll
-      for (int e = 0; e < R; e++) acc -= KM[q * R + e] * xm[e] + KP[q * R + e] * xp[e];
+        for (int e = 0; e < R; e++) acc -= KM[q * R + e] * xm[e] + KP[q * R + e] * xp[e];
+      }
       nxt[q] = acc;
     }
 #pragma unroll
@@ -512,11 +555,9 @@ __device__ __forceinline__ void residual_df(const float (&bh)[M], const float (&
       lh = sel2<FULL>(u == size - R + e, xh[u], lh);
       ll = sel2<FULL>(u == size - R + e, xl[u], ll);
     }
-    hh_prev[e] = xch.get(lh, prev);
-    hh_next[e] = xch.get(xh[e], next);
+    xch.get_two(lh, prev, xh[e], next, hh_prev[e], hh_next[e]);
     if (XLO) {
-      hl_prev[e] = xch.get(ll, prev);
-      hl_next[e] = xch.get(xl[e], next);
+      xch.get_two(ll, prev, xl[e], next, hl_prev[e], hl_next[e]);
     } else {
       hl_prev[e] = 0.f;
       hl_next[e] = 0.f;
@@ -720,28 +761,47 @@ __device__ __forceinline__ f2 split_in(X x) {
   else return f2{(float)x, 0.f};
 }
 
-// One tile = blockDim / pw consecutive lines starting at line L0, processed by
-// the whole CTA: gather the rows (+ stencil halo) of every lane's partition,
-// stencil + solve per lane, write back.  KS: stencil terms compiled in (0 =
-// the input already is b).  FULL: every partition has exactly M rows (sizes
-// known at compile time).  DIRECT: x-lines, each lane reads and writes its
-// own contiguous rows with 16-byte vector accesses (no shared memory);
-// otherwise the tile is staged through shared memory (y and z lines, and
-// x-lines with ragged partitions).  Used by the per-plan kernel (one tile per
-// CTA) and by the persistent batch kernel (many tiles per CTA).
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, bool DIRECT = false>
+// How a tile reaches its threads.
+//  kStaged: a warp holds one line (lane = partition); the tile is staged
+//    through shared memory with 16-byte coalesced global accesses.
+//  kDirectX: x-lines, a warp holds one line and each lane reads and writes
+//    its own contiguous rows with 16-byte vector accesses (no staging).
+//  kDirectStrided: y/z lines, thread = (partition i, line g) with g fastest,
+//    so one warp-wide access of a row covers TL consecutive x positions of
+//    32 / TL partitions (full 32-byte sectors, no staging); the interface
+//    messages between partitions then cross warps through shared memory.
+constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2;
+
+// Exchanger of the interface messages for a layout: warp shuffles when a
+// warp holds a whole line, shared memory otherwise.
+template <bool CTA>
+__device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int stride, int offset) {
+  if constexpr (CTA) return CtaXchg{reinterpret_cast<unsigned long long*>(smem), 0, stride, offset};
+  else return WarpXchg{pw};
+}
+
+// One tile = blockDim / pw consecutive lines, processed by the whole CTA:
+// gather the rows (+ stencil halo) of every partition, stencil + solve per
+// thread, write back.  KS: stencil terms compiled in (0 = the input already
+// is b).  FULL: every partition has exactly M rows (sizes known at compile
+// time).  LAYOUT: see kStaged / kDirectX / kDirectStrided.  Used by the
+// per-plan kernel (one tile per CTA) and by the persistent batch kernel (many
+// tiles per CTA).
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged>
 __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables& t, const void* in_ptr,
                                           void* out_ptr, const int tx, const int to, unsigned char* smem_raw) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
-  using TW = typename std::conditional<DIRECT, TIn, TT>::type;  // element type of the gathered window
+  constexpr bool DIRECT = LAYOUT == kDirectX, DSTR = LAYOUT == kDirectStrided;
+  using TW = typename std::conditional<DIRECT || DSTR, TIn, TT>::type;  // element type of the gathered window
   constexpr int KA = KS > 0 ? KS : 1;  // halo array size (KS = 0 compiles no stencil)
   TT* S = reinterpret_cast<TT*>(smem_raw);
   const int pw = t.pw;
   const int TL = blockDim.x / pw;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
   const int nl = tr.nl;
-  const int g = threadIdx.x / pw, i = threadIdx.x % pw;
+  const int g = DSTR ? threadIdx.x % TL : threadIdx.x / pw;
+  const int i = DSTR ? threadIdx.x / TL : threadIdx.x % pw;
   const bool lane_ok = i < t.p;
   const bool ok = lane_ok && g < nl;
   int start = 0, size = R * 2;
@@ -753,16 +813,30 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   }
   const int n = t.n;
   TT* SL = S + g * t.lsz;
-  const TIn* gin = (const TIn*)in_ptr + tr.base + (int64_t)g * n;  // DIRECT: this lane's line
-  TOut* gout = (TOut*)out_ptr + tr.base + (int64_t)g * n;
+  // direct layouts: row 0 of this thread's line; row r at gin[r * es]
+  const int64_t es = DSTR ? tr.es : 1;
+  const TIn* gin = (const TIn*)in_ptr + tr.base + (DSTR ? (int64_t)g : (int64_t)g * n);
+  TOut* gout = (TOut*)out_ptr + tr.base + (DSTR ? (int64_t)g : (int64_t)g * n);
 
   // ---- gather: w[KS + k] = row start + k, w[q] = row start - KS + q, hh[q] = row start + size + q
   // (the refinement mode gathers straight into FP32 pairs below)
   TW w[M + KS], hh[KA];
   if constexpr (MODE == kModeRefine) {
-    if constexpr (!DIRECT) {
+    if constexpr (LAYOUT == kStaged) {
       tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
       __syncthreads();
+    }
+  } else if constexpr (DSTR) {
+#pragma unroll
+    for (int k = 0; k < M; k++) w[KS + k] = (ok && (FULL || k < size)) ? __ldg(gin + (start + k) * es) : TIn(0);
+#pragma unroll
+    for (int q = 0; q < KS; q++) {
+      int rlo = start - KS + q;
+      rlo += (rlo < 0) ? n : 0;
+      w[q] = ok ? __ldg(gin + rlo * es) : TIn(0);
+      int rhi = start + size + q;
+      rhi -= (rhi >= n) ? n : 0;
+      hh[q] = ok ? __ldg(gin + rhi * es) : TIn(0);
     }
   } else if constexpr (DIRECT) {
     constexpr int V = 16 / sizeof(TIn);
@@ -808,7 +882,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   }
 
   TOut xo[M];
-  WarpXchg wx{pw};
+  auto xch = make_xchg<DSTR>(pw, smem_raw, TL, g);
   if constexpr (MODE != kModeRefine) {
     T v[M];
 #pragma unroll
@@ -824,7 +898,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         v[k] = s;
       }
     }
-    solve_partition<T, R, M, T, FULL>(v, size, i, lane_ok, t, wx);
+    solve_partition<T, R, M, T, FULL>(v, size, i, lane_ok, t, xch);
 #pragma unroll
     for (int k = 0; k < M; k++) xo[k] = conv<TOut>(v[k]);
   } else {
@@ -832,7 +906,27 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     // into an FP32 pair as soon as it is loaded.
     float bh[M], bl[M];
     float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
-    if constexpr (DIRECT) {
+    if constexpr (DSTR) {
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const f2 sv = split_in((ok && (FULL || k < size)) ? __ldg(gin + (start + k) * es) : TIn(0));
+        fh[KS + k] = sv.hi;
+        fl[KS + k] = sv.lo;
+      }
+#pragma unroll
+      for (int q = 0; q < KS; q++) {
+        int rlo = start - KS + q;
+        rlo += (rlo < 0) ? n : 0;
+        const f2 a0 = split_in(ok ? __ldg(gin + rlo * es) : TIn(0));
+        fh[q] = a0.hi;
+        fl[q] = a0.lo;
+        int rhi = start + size + q;
+        rhi -= (rhi >= n) ? n : 0;
+        const f2 a1 = split_in(ok ? __ldg(gin + rhi * es) : TIn(0));
+        hhh[q] = a1.hi;
+        hhl[q] = a1.lo;
+      }
+    } else if constexpr (DIRECT) {
       constexpr int V = 16 / sizeof(TIn);
       if (FULL && (M % V) == 0) {
 #pragma unroll
@@ -935,13 +1029,13 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     float xh[M], v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) v[k] = bh[k];
-    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
+    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
 #pragma unroll
     for (int k = 0; k < M; k++) xh[k] = v[k];
     // refinement sweep 1: x <- x0 + A^{-1}(b - A x0), residual to FP64 accuracy
-    if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, wx);
-    else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, wx);
-    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
+    if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
+    else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, xch);
+    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
     if (a.sweeps < 2) {
       // x = x0 + delta: one FP64 add per unknown (the FP32 path leaves the
       // FP64 pipe idle otherwise); exact integer conversions
@@ -960,9 +1054,9 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         xh[k] = sm.hi;
         xl[k] = sm.lo;
       }
-      if constexpr (FULL) residual_sym<R, M, true>(bh, bl, xh, xl, v, i, t, wx);
-      else residual_df<R, M, true, FULL>(bh, bl, xh, xl, v, size, i, t, wx);
-      solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, wx);
+      if constexpr (FULL) residual_sym<R, M, true>(bh, bl, xh, xl, v, i, t, xch);
+      else residual_df<R, M, true, FULL>(bh, bl, xh, xl, v, size, i, t, xch);
+      solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
 #pragma unroll
       for (int k = 0; k < M; k++) {
         const double xd = f32_to_f64_normal(xh[k]) + f32_to_f64_normal(xl[k] + v[k]);
@@ -973,7 +1067,13 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   }
 
   // ---- write back
-  if constexpr (DIRECT) {
+  if constexpr (DSTR) {
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < M; k++)
+        if (FULL || k < size) gout[(start + k) * es] = xo[k];
+    }
+  } else if constexpr (DIRECT) {
     constexpr int V = 16 / sizeof(TOut);
     if (ok) {
       if (FULL && (M % V) == 0) {
@@ -1002,10 +1102,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   }
 }
 
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL, bool DIRECT>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL, int LAYOUT>
 __global__ void __launch_bounds__(256, (MODE == kModeRefine || M == 32) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  line_tile<R, M, MODE, KS, TIn, TOut, FULL, DIRECT>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
+  line_tile<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace cbs

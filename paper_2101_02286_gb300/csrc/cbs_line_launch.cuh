@@ -6,6 +6,19 @@ namespace cbs {
 
 constexpr int kLineThreads = 256;
 
+// Streaming multiprocessors of the current device (cached per process).
+inline int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      n = v;
+    else
+      return 152;
+  }
+  return n;
+}
+
 // Launch grid of the tile kernels: x-lines are tiled along the line index;
 // y/z lines along x (grid.x) and the remaining coordinate (grid.y).
 inline dim3 tile_grid(int64_t nx, int64_t ny, int64_t nz, int64_t nlines, int dir, int lines_per_cta) {
@@ -13,38 +26,48 @@ inline dim3 tile_grid(int64_t nx, int64_t ny, int64_t nz, int64_t nlines, int di
   return dim3((unsigned)((nx + lines_per_cta - 1) / lines_per_cta), (unsigned)(dir == 1 ? nz : ny), 1);
 }
 
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, bool DIRECT = false>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged>
 cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
-  const int threads = kLineThreads;
-  const int lines_per_cta = threads / t.pw;
   if (a.nlines <= 0) return cudaSuccess;
-  const dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, lines_per_cta);
-  const size_t smem = (size_t)lines_per_cta * t.lsz * sizeof(TT);
+  // 256 threads per CTA; small problems shrink the CTA (down to 64 threads)
+  // until the grid covers every SM at least twice
+  int threads = kLineThreads;
+  dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
+  const int64_t want = 2 * (int64_t)sm_count();
+  while (threads > 64 && threads > t.pw && (int64_t)grid.x * grid.y < want) {
+    threads /= 2;
+    grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
+  }
+  const int lines_per_cta = threads / t.pw;
+  // staged: the tile; direct strided: the message buffer
+  const size_t smem = LAYOUT == kStaged ? (size_t)lines_per_cta * t.lsz * sizeof(TT)
+                      : LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0;
   static size_t configured = 0;  // per instantiation
   if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, DIRECT>,
+    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  line_kernel<R, M, MODE, KS, TIn, TOut, FULL, DIRECT><<<grid, threads, DIRECT ? 0 : smem, s>>>(a, t);
+  line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT><<<grid, threads, smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
-// Whole-size partitions (n = p M): sizes are compile-time constants; x-lines
-// then skip shared memory.  Compiled for FP64 input and output only.
+// Whole-size partitions (n = p M): sizes are compile-time constants and
+// neither x-lines nor y/z lines are staged through shared memory.  Compiled
+// for FP64 input and output only.
 inline bool tile_full(const DevLineTables& t, int M) { return t.count_big == t.p && t.rows_big == M; }
 
 template <int R, int M, int MODE, int KSV, typename TIn, typename TOut>
 cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if constexpr (sizeof(TIn) == 8 && sizeof(TOut) == 8) {
     if (tile_full(t, M)) {
-      if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, true>(a, t, s);
-      return launch_one<R, M, MODE, KSV, TIn, TOut, true, false>(a, t, s);
+      if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectX>(a, t, s);
+      return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectStrided>(a, t, s);
     }
   }
-  return launch_one<R, M, MODE, KSV, TIn, TOut, false, false>(a, t, s);
+  return launch_one<R, M, MODE, KSV, TIn, TOut, false, kStaged>(a, t, s);
 }
 
 template <int R, int M, int MODE, typename TIn, typename TOut>

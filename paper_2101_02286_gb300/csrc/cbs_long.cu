@@ -93,14 +93,20 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
   }
   __syncthreads();
   for (int st = 0; st < t.nstage; st++) {
+    // flags exist for the first kMaxStages stages; later ones run in full
+    const bool known = st < kMaxStages;
+    const bool msg = !known || (t.stage_msg[st] & 1) != 0;  // couplings above FP64 rounding
+    if (!msg && known && !t.stage_has_c[st]) continue;
     for (int i = threadIdx.x; i < p; i += blockDim.x) {
       const int sm = __ldg(t.src + (st * 2 + 0) * p + i), sp = __ldg(t.src + (st * 2 + 1) * p + i);
       for (int q = 0; q < r; q++) {
         double acc = 0.0;
         for (int e = 0; e < r; e++) {
           acc += __ldg(t.coef + ((st * 3 + 0) * rr + q * r + e) * p + i) * X0[i * r + e];
-          acc -= __ldg(t.coef + ((st * 3 + 1) * rr + q * r + e) * p + i) * X0[sm * r + e];
-          acc -= __ldg(t.coef + ((st * 3 + 2) * rr + q * r + e) * p + i) * X0[sp * r + e];
+          if (msg) {
+            acc -= __ldg(t.coef + ((st * 3 + 1) * rr + q * r + e) * p + i) * X0[sm * r + e];
+            acc -= __ldg(t.coef + ((st * 3 + 2) * rr + q * r + e) * p + i) * X0[sp * r + e];
+          }
         }
         X1[i * r + q] = acc;
       }
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 // bulk rows (acyclic, tables `tin`).
 template <int R, int M, int MODE, typename TIn, typename TOut>
 __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin) {
-  extern __shared__ __align__(16) unsigned long long xbuf[];  // 2 * blockDim slots
+  extern __shared__ __align__(16) unsigned long long xbuf[];  // kCtaXchgSlots * blockDim slots
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   const int seg = blockIdx.x;
   const int64_t line = blockIdx.y;
@@ -249,7 +255,7 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int threads = ((inner.p + 31) / 32) * 32;
-  const size_t smem = 2 * (size_t)threads * sizeof(unsigned long long);
+  const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
 #define CBS_SEG(MO, RR, TI, TO) long_seg_kernel<RR, 16, MO, TI, TO><<<gs, threads, smem, s>>>(a, inner)
   if (mode == kModeRefine) {
     if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }

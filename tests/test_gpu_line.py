@@ -152,3 +152,19 @@ def test_autotune_picks_admissible_and_caches(cuda):
     tuned = Plan(shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=W.LELE6_TRI["rhs"], h=W.grid_spacing(384), segments="tune")
     assert tuned.info()["segments"] >= 1
     tuned.close()
+
+
+def test_interface_stages_below_rounding_skip_messages(cuda):
+    # 32 partitions of 16 rows: the interface couplings are ~1e-7 of the
+    # diagonal blocks and square at every PCR step, so only the first steps
+    # exchange values; the rest reduce to local products
+    plan = Plan((1, 1, 512), 0, lhs=W.LELE6_TRI["lhs"], segments=32)
+    info = plan.info()
+    assert info["pcr_steps"] == 5
+    assert 1 <= info["message_stages_f32"] <= info["message_stages"] < info["pcr_steps"]
+    plan.close()
+    # 4096-row segments of a long line decouple completely at the outer level
+    long_plan = Plan((1, 2, 1 << 16), 0, lhs=W.PENTA10["lhs"], segments=16)
+    li = long_plan.info()
+    assert li["kernel"] == 1 and li["message_stages"] == 0 and li["inner_message_stages"] >= 1
+    long_plan.close()
