@@ -506,8 +506,8 @@ def main():
         hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
         bytes_per_launch = 16.0 * n ** 3  # read f (FP64), write f' (FP64)
         kdir = max(range(3), key=lambda d: dir_ref[d])
-        # dominant kernel: the shared-memory-staged variant that runs the y and
-        # z lines (two of the three launches of a step, the longer ones)
+        # dominant kernel: the pipelined refinement kernel in its strided layout,
+        # which runs the y and z lines (two of the three launches of a step)
         ms_yz = (dir_ref[1] + dir_ref[2]) / 2
         achieved = bytes_per_launch / (ms_yz * 1e-3) / 1e9
         achieved_x = bytes_per_launch / (dir_ref[0] * 1e-3) / 1e9
@@ -533,11 +533,11 @@ def main():
             "ms_per_direction": dir_ref,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": hbm_src,
-                         "kernel": "line_kernel refine, shared-memory staged (y and z lines)",
+                         "kernel": "line_kernel_pipe refine, strided direct layout (y and z lines)",
                          "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_yz,
                          "slowest_direction": "xyz"[kdir]},
             "roofline_x": {"bound": "hbm", "achieved": achieved_x, "peak": hbm, "unit": "GB/s",
-                           "frac": achieved_x / hbm, "kernel": "line_kernel refine, direct 16-byte loads (x lines)",
+                           "frac": achieved_x / hbm, "kernel": "line_kernel_pipe refine, 16-byte prefetch (x lines)",
                            "ms_per_launch": dir_ref[0]},
             "fp64_path": {"value": job_throughput(units, world, ms_64), "unit": "Gunknowns/s",
                           "ms_per_step": ms_64, "ms_per_direction": dir_64, "max_rel_err": err.get("fp64"),

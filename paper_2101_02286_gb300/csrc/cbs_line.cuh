@@ -9,8 +9,9 @@
 //       plan's pre-factorised LU of D_i (Eq. 17), in registers;
 //   a3  b-hat_i = b~_i - L~_i y_{i-1} - U~_i y_i (Eq. 21) and the cyclic
 //       block-PCR with detach/reattach on the interface system
-//       (Algorithms 1-4) using warp shuffles, always in FP64, with the W^{-1}
-//       products precomputed per stage (Sec. 4);
+//       (Algorithms 1-4) using warp shuffles (or shared memory when the
+//       partitions of a line span several warps), with the W^{-1} products
+//       precomputed per stage (Sec. 4), in the precision of the solve;
 //   a4  x_i = y_i - S_i x~_i - R_i x~_{i+1} (Eq. 22).
 // The FP32 + refinement mode runs a2-a4 in FP32 twice (or three times) and
 // evaluates the residual b - A x to FP64 accuracy with error-free FP32
@@ -761,6 +762,20 @@ __device__ __forceinline__ f2 split_in(X x) {
   else return f2{(float)x, 0.f};
 }
 
+// ---------------------------------------------------------------- async copies
+// Global -> shared copies that hold no registers while in flight (the
+// pipelined kernel prefetches the next tile's rows while it computes).
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // How a tile reaches its threads.
 //  kStaged: a warp holds one line (lane = partition); the tile is staged
 //    through shared memory with 16-byte coalesced global accesses.
@@ -780,6 +795,80 @@ __device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int strid
   else return WarpXchg{pw};
 }
 
+// This thread's own rows from the prefetch slots (layout of prefetch_rows;
+// VEC: 16-byte units read back with 16-byte shared loads).
+template <int M, typename TIn, bool VEC>
+__device__ __forceinline__ void pipe_rows(const TIn* slots, TIn (&v)[M]) {
+  const int bd = blockDim.x;
+  if constexpr (VEC && (M % (16 / sizeof(TIn))) == 0) {
+    constexpr int V = 16 / sizeof(TIn);
+#pragma unroll
+    for (int u = 0; u < M / V; u++) {
+      const float4 q = *reinterpret_cast<const float4*>(slots + ((size_t)u * bd + threadIdx.x) * V);
+      const TIn* e = reinterpret_cast<const TIn*>(&q);
+#pragma unroll
+      for (int j = 0; j < V; j++) v[u * V + j] = e[j];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < M; k++) v[k] = slots[(size_t)k * bd + threadIdx.x];
+  }
+}
+
+// Partition and line of this thread within a tile (see the layouts above).
+struct ThreadPart {
+  int g, i, start, size;
+  bool lane_ok;
+};
+template <int M, bool FULL, int LAYOUT>
+__device__ __forceinline__ ThreadPart thread_part(const DevLineTables& t) {
+  ThreadPart r;
+  const int pw = t.pw, TL = blockDim.x / pw;
+  r.g = LAYOUT == kDirectStrided ? threadIdx.x % TL : threadIdx.x / pw;
+  r.i = LAYOUT == kDirectStrided ? threadIdx.x / TL : threadIdx.x % pw;
+  r.lane_ok = r.i < t.p;
+  r.start = 0;
+  r.size = 2 * t.r;
+  if (FULL) {
+    r.start = r.i * M;
+    r.size = M;
+  } else if (r.lane_ok) {
+    partition_of(t, r.i, r.start, r.size);
+  }
+  return r;
+}
+
+// Prefetch slots of the pipelined kernel: thread-private, slot j of thread
+// tid at slots[j * blockDim + tid] (conflict-free); j < M: own row j,
+// M + q: row start - KS + q, M + KS + q: row start + size + q (periodic).
+// VEC (contiguous rows, M a multiple of the 16-byte vector width V): own
+// rows are copied in 16-byte units, unit u of thread tid at element offset
+// (u * bd + tid) * V, conflict-free for 16-byte shared loads.
+template <int M, int KS, bool FULL, typename TIn, bool VEC = false>
+__device__ __forceinline__ void prefetch_rows(TIn* slot0, const TIn* gline, int64_t es, int start, int size,
+                                              int n) {
+  const int bd = blockDim.x;
+  if constexpr (VEC) {
+    constexpr int V = 16 / sizeof(TIn);
+    TIn* base = slot0 - threadIdx.x;  // thread 0's slot 0
+#pragma unroll
+    for (int u = 0; u < M / V; u++) cp_async<16>(base + ((size_t)u * bd + threadIdx.x) * V, gline + start + u * V);
+  } else {
+#pragma unroll
+    for (int k = 0; k < M; k++)
+      if (FULL || k < size) cp_async<sizeof(TIn)>(slot0 + k * bd, gline + (start + k) * es);
+  }
+#pragma unroll
+  for (int q = 0; q < KS; q++) {
+    int rlo = start - KS + q;
+    rlo += (rlo < 0) ? n : 0;
+    cp_async<sizeof(TIn)>(slot0 + (M + q) * bd, gline + rlo * es);
+    int rhi = start + size + q;
+    rhi -= (rhi >= n) ? n : 0;
+    cp_async<sizeof(TIn)>(slot0 + (M + KS + q) * bd, gline + rhi * es);
+  }
+}
+
 // One tile = blockDim / pw consecutive lines, processed by the whole CTA:
 // gather the rows (+ stencil halo) of every partition, stencil + solve per
 // thread, write back.  KS: stencil terms compiled in (0 = the input already
@@ -787,9 +876,11 @@ __device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int strid
 // time).  LAYOUT: see kStaged / kDirectX / kDirectStrided.  Used by the
 // per-plan kernel (one tile per CTA) and by the persistent batch kernel (many
 // tiles per CTA).
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged,
+          bool PIPE = false>
 __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables& t, const void* in_ptr,
-                                          void* out_ptr, const int tx, const int to, unsigned char* smem_raw) {
+                                          void* out_ptr, const int tx, const int to, unsigned char* smem_raw,
+                                          const TIn* pslots = nullptr) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
   constexpr bool DIRECT = LAYOUT == kDirectX, DSTR = LAYOUT == kDirectStrided;
@@ -800,17 +891,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   const int TL = blockDim.x / pw;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
   const int nl = tr.nl;
-  const int g = DSTR ? threadIdx.x % TL : threadIdx.x / pw;
-  const int i = DSTR ? threadIdx.x / TL : threadIdx.x % pw;
-  const bool lane_ok = i < t.p;
+  const ThreadPart tp = thread_part<M, FULL, LAYOUT>(t);
+  const int g = tp.g, i = tp.i, start = tp.start, size = tp.size;
+  const bool lane_ok = tp.lane_ok;
   const bool ok = lane_ok && g < nl;
-  int start = 0, size = R * 2;
-  if (FULL) {
-    start = i * M;
-    size = M;
-  } else if (lane_ok) {
-    partition_of(t, i, start, size);
-  }
   const int n = t.n;
   TT* SL = S + g * t.lsz;
   // direct layouts: row 0 of this thread's line; row r at gin[r * es]
@@ -825,6 +909,18 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     if constexpr (LAYOUT == kStaged) {
       tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
       __syncthreads();
+    }
+  } else if constexpr (PIPE) {
+    const TIn* s0 = pslots + threadIdx.x;
+    const int bd = blockDim.x;
+    TIn own[M];
+    pipe_rows<M, TIn, DIRECT>(pslots, own);
+#pragma unroll
+    for (int k = 0; k < M; k++) w[KS + k] = (ok && (FULL || k < size)) ? own[k] : TIn(0);
+#pragma unroll
+    for (int q = 0; q < KS; q++) {
+      w[q] = ok ? s0[(M + q) * bd] : TIn(0);
+      hh[q] = ok ? s0[(M + KS + q) * bd] : TIn(0);
     }
   } else if constexpr (DSTR) {
 #pragma unroll
@@ -906,7 +1002,27 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     // into an FP32 pair as soon as it is loaded.
     float bh[M], bl[M];
     float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
-    if constexpr (DSTR) {
+    if constexpr (PIPE) {
+      const TIn* s0 = pslots + threadIdx.x;
+      const int bd = blockDim.x;
+      TIn own[M];
+      pipe_rows<M, TIn, DIRECT>(pslots, own);
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        const f2 sv = split_in((ok && (FULL || k < size)) ? own[k] : TIn(0));
+        fh[KS + k] = sv.hi;
+        fl[KS + k] = sv.lo;
+      }
+#pragma unroll
+      for (int q = 0; q < KS; q++) {
+        const f2 a0 = split_in(ok ? s0[(M + q) * bd] : TIn(0));
+        fh[q] = a0.hi;
+        fl[q] = a0.lo;
+        const f2 a1 = split_in(ok ? s0[(M + KS + q) * bd] : TIn(0));
+        hhh[q] = a1.hi;
+        hhl[q] = a1.lo;
+      }
+    } else if constexpr (DSTR) {
 #pragma unroll
       for (int k = 0; k < M; k++) {
         const f2 sv = split_in((ok && (FULL || k < size)) ? __ldg(gin + (start + k) * es) : TIn(0));
@@ -1106,6 +1222,57 @@ template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL
 __global__ void __launch_bounds__(256, (MODE == kModeRefine || M == 32) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   line_tile<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Issue (and commit) the copies of this thread's rows of tile `tile` into
+// half `buf` of the double buffer (whole-size partitions).
+template <int M, int KS, typename TIn, int LAYOUT>
+__device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTables& t, const ThreadPart& tp,
+                                              const int gx, const int tile, TIn* slots, const int buf) {
+  constexpr int NS = M + 2 * KS;
+  const int bd = blockDim.x, TL = bd / t.pw;
+  const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
+  const TileRef tr = tile_of(a, t.n, TL, tx, to);
+  if (tp.lane_ok && tp.g < tr.nl) {
+    const TIn* gline = (const TIn*)a.in + tr.base + (LAYOUT == kDirectStrided ? (int64_t)tp.g : (int64_t)tp.g * t.n);
+    constexpr bool VEC = LAYOUT == kDirectX && (M % (16 / sizeof(TIn))) == 0;
+    prefetch_rows<M, KS, true, TIn, VEC>(slots + (size_t)buf * NS * bd + threadIdx.x, gline,
+                                         LAYOUT == kDirectStrided ? tr.es : 1, tp.start, tp.size, t.n);
+  }
+  cp_async_commit();
+}
+
+// Persistent, software-pipelined variant of the direct layouts: each CTA
+// walks the tiles tile = blockIdx.x, + gridDim.x, ... (tile -> (tx, to) with
+// gx tiles along the first grid axis) and, before computing a tile, issues
+// the asynchronous copies of the next tile's rows into the other half of a
+// double buffer of thread-private shared-memory slots, so HBM traffic
+// overlaps the arithmetic.  Shared memory: the message buffer (strided
+// layout only, kCtaXchgSlots 64-bit slots per thread) followed by 2 x
+// (M + 2 KS) slots of TIn per thread.
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT>
+__global__ void __launch_bounds__(256, (MODE == kModeRefine || M == 32) ? 2 : 3)
+    line_kernel_pipe(const LineArgs a, const DevLineTables t, const int gx, const int ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NS = M + 2 * KS;
+  const int bd = blockDim.x;
+  const size_t xbytes = LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * bd * sizeof(unsigned long long) : 0;
+  TIn* slots = reinterpret_cast<TIn*>(smem_raw + xbytes);
+  const ThreadPart tp = thread_part<M, true, LAYOUT>(t);
+  int tile = blockIdx.x, buf = 0;
+  if (tile < ntiles) prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, tile, slots, 0);
+  for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, next, slots, buf ^ 1);
+      cp_async_wait<1>();  // this tile's copies are done, the next tile's stay in flight
+    } else {
+      cp_async_wait<0>();
+    }
+    const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
+    line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true>(a, t, a.in, a.out, tx, to, smem_raw,
+                                                           slots + (size_t)buf * NS * bd);
+  }
 }
 
 }  // namespace cbs

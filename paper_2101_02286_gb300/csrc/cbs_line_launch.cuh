@@ -54,6 +54,34 @@ cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Persistent pipelined launch (whole-size partitions, direct layouts): one
+// CTA per resident slot (occupancy x SMs), each walking tiles with the next
+// tile's rows in flight while it computes the current one.
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT>
+cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
+  if (a.nlines <= 0) return cudaSuccess;
+  constexpr int NS = M + 2 * KS;
+  const int threads = kLineThreads;
+  const dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
+  const int64_t ntiles = (int64_t)grid.x * grid.y;
+  if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
+  const size_t smem = (LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0) +
+                      2 * (size_t)NS * threads * sizeof(TIn);
+  auto kern = line_kernel_pipe<R, M, MODE, KS, TIn, TOut, LAYOUT>;
+  static int per_sm = 0;  // per instantiation (the shared-memory size only depends on it)
+  if (per_sm == 0) {
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int64_t want = (int64_t)per_sm * sm_count();
+  const unsigned blocks = (unsigned)(ntiles < want ? ntiles : want);
+  kern<<<blocks, threads, smem, s>>>(a, t, (int)grid.x, (int)ntiles);
+  return cudaGetLastError();
+}
+
 // Whole-size partitions (n = p M): sizes are compile-time constants and
 // neither x-lines nor y/z lines are staged through shared memory.  Compiled
 // for FP64 input and output only.
@@ -63,8 +91,16 @@ template <int R, int M, int MODE, int KSV, typename TIn, typename TOut>
 cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if constexpr (sizeof(TIn) == 8 && sizeof(TOut) == 8) {
     if (tile_full(t, M)) {
-      if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectX>(a, t, s);
-      return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectStrided>(a, t, s);
+      // the refinement kernel holds 2 CTAs per SM (registers), too few to
+      // hide HBM latency without the pipelined prefetch; the FP64 / FP32
+      // kernels keep 3 CTAs per SM and load directly
+      if constexpr (MODE == kModeRefine) {
+        if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectX>(a, t, s);
+        return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectStrided>(a, t, s);
+      } else {
+        if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectX>(a, t, s);
+        return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectStrided>(a, t, s);
+      }
     }
   }
   return launch_one<R, M, MODE, KSV, TIn, TOut, false, kStaged>(a, t, s);
