@@ -524,6 +524,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
     a.wHi[q] = (float)w;
     a.wLo[q] = (float)(w - (double)a.wHi[q]);
   }
+  pack_weights(a);
   a.status = P->dstatus;
   P->kind = 0;
   if (P->var) {
@@ -695,6 +696,7 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
       a.wHi[q] = -a.wHi[q];
       a.wLo[q] = -a.wLo[q];
     }
+    pack_weights(a);
     cudaError_t e = run(a, P->ks);
     if (e != cudaSuccess) return cuda_fail(e, "transpose solve launch");
     launches++;

@@ -41,8 +41,24 @@ struct LineArgs {
   int sweeps;            // refinement sweeps (kModeRefine)
   double w[kMaxRhsTerms];              // c_q / (2 q h)
   float wHi[kMaxRhsTerms], wLo[kMaxRhsTerms];
+  // the same split weights as pairs for the two-rows-per-instruction
+  // arithmetic: [q][0] = (wHi, wHi), [q][1] = (-wHi, -wHi), [q][2] = (wLo, wLo)
+  unsigned long long wP[kMaxRhsTerms][3];
   int* status;
 };
+
+// Host: refresh the paired weights after wHi / wLo changed.
+inline void pack_weights(LineArgs& a) {
+  for (int q = 0; q < kMaxRhsTerms; q++) {
+    const float v[3] = {a.wHi[q], -a.wHi[q], a.wLo[q]};
+    for (int m = 0; m < 3; m++) {
+      unsigned u;
+      static_assert(sizeof(u) == sizeof(float), "float size");
+      __builtin_memcpy(&u, &v[m], sizeof(u));
+      a.wP[q][m] = ((unsigned long long)u << 32) | u;
+    }
+  }
+}
 
 // Field geometry: (nx, ny, nz) with x contiguous, lines along `dir`.
 struct Geom {
@@ -113,6 +129,51 @@ __device__ __forceinline__ f2 two_prod(float a, float b) {
 __device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // |a| >= |b|
   const float s = __fadd_rn(a, b);
   return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// ---------------------------------------------------------------- paired FP32
+// Two FP32 lanes per instruction (add/sub/mul/fma .f32x2, round to nearest,
+// no contraction): the error-free transformations of two rows at once, bit
+// for bit the same results as the scalar forms above.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpk(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// s + e = a + b exactly (two-sum) and a - b exactly (two-sum of a and -b)
+__device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2& s, f32x2& e) {
+  s = add2(a, b);
+  const f32x2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void two_diff2(f32x2 a, f32x2 b, f32x2& s, f32x2& e) {
+  s = sub2(a, b);
+  const f32x2 bb = sub2(s, a);
+  e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
 }
 // FP64 <-> FP32-pair conversions with integer operations.  On this GPU the
 // f32<->f64 conversion instructions and every FP64 add issue on the FP64
@@ -307,6 +368,74 @@ __device__ __forceinline__ void residual_sym(const float (&bh)[M], const float (
       al += lo;
     }
     res[k] = ah + al;
+  }
+}
+
+// Window row r in [-KS, M + KS) of a partition: rows below M from the window
+// w (w[KS + r]), the rest from the upper halo hh (r compile-time).
+template <int M, int KS, int KA>
+__device__ __forceinline__ float win_row(const float (&w)[M + KS], const float (&hh)[KA], int r) {
+  return (r < M) ? w[(r < M) ? KS + r : 0] : hh[(r >= M) ? r - M : 0];
+}
+
+// x at row offset r in [-R, M + R) of a partition: its own rows, the last R
+// rows of the previous partition (lo) or the first R of the next (hi); r is a
+// compile-time constant after unrolling.
+template <int R, int M>
+__device__ __forceinline__ float row_at(const float (&x)[M], const float (&lo)[R], const float (&hi)[R], int r) {
+  return (r < 0) ? lo[(r < 0) ? R + r : 0] : (r >= M) ? hi[(r >= M) ? r - M : 0] : x[(r >= 0 && r < M) ? r : 0];
+}
+
+// residual_sym with two rows per instruction (M even); same results.
+template <int R, int M, bool XLO, typename X>
+__device__ __forceinline__ void residual_sym2(const float (&bh)[M], const float (&bl)[M], const float (&xh)[M],
+                                              const float (&xl)[M], float (&res)[M], const int i,
+                                              const DevLineTables& t, X& xch) {
+  static_assert(M % 2 == 0, "paired rows");
+  const int p = t.p;
+  const int prev = (i == 0) ? p - 1 : i - 1;
+  const int next = (i + 1 >= p) ? 0 : i + 1;
+  float ph[R], pl[R], nh[R], nl[R];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    xch.get_two(xh[M - R + e], prev, xh[e], next, ph[e], nh[e]);
+    pl[e] = nl[e] = 0.f;
+    if (XLO) xch.get_two(xl[M - R + e], prev, xl[e], next, pl[e], nl[e]);
+    if (!t.cyclic) {
+      if (i == 0) ph[e] = pl[e] = 0.f;
+      if (i + 1 >= p) nh[e] = nl[e] = 0.f;
+    }
+  }
+  // rows j and j + M/2 share an instruction, so a neighbour pair (j +- q,
+  // j + M/2 +- q) is again a pair of the same layout except at the ends
+  constexpr int H = M / 2;
+#pragma unroll
+  for (int k = 0; k < H; k++) {
+    f32x2 ah, ae;
+    two_diff2(pk(bh[k], bh[k + H]), pk(xh[k], xh[k + H]), ah, ae);
+    f32x2 al = add2(pk(bl[k], bl[k + H]), ae);
+    if (XLO) al = sub2(al, pk(xl[k], xl[k + H]));
+#pragma unroll
+    for (int q = 1; q <= R; q++) {
+      const f32x2 mh = pk(row_at<R, M>(xh, ph, nh, k - q), row_at<R, M>(xh, ph, nh, k + H - q));
+      const f32x2 uh = pk(row_at<R, M>(xh, ph, nh, k + q), row_at<R, M>(xh, ph, nh, k + H + q));
+      f32x2 sxh, sxe;
+      two_sum2(mh, uh, sxh, sxe);
+      const float aH = t.bandHi[R + q], aL = t.bandLo[R + q];
+      const f32x2 AH = pk(aH, aH), NAH = pk(-aH, -aH), AL = pk(aL, aL);
+      const f32x2 P = mul2(AH, sxh);
+      const f32x2 Pen = fma2(NAH, sxh, P);  // -(error of P)
+      f32x2 e1;
+      two_diff2(ah, P, ah, e1);
+      f32x2 lo = sub2(add2(e1, Pen), fma2(AH, sxe, mul2(AL, sxh)));
+      if (XLO) {
+        const f32x2 ml = pk(row_at<R, M>(xl, pl, nl, k - q), row_at<R, M>(xl, pl, nl, k + H - q));
+        const f32x2 ul = pk(row_at<R, M>(xl, pl, nl, k + q), row_at<R, M>(xl, pl, nl, k + H + q));
+        lo = sub2(lo, mul2(AH, add2(ml, ul)));
+      }
+      al = add2(al, lo);
+    }
+    unpk(add2(ah, al), res[k], res[k + H]);
   }
 }
 
@@ -1108,6 +1237,37 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         bh[k] = fh[KS + k];
         bl[k] = fl[KS + k];
       }
+    } else if constexpr (FULL && (M % 2) == 0) {
+      // a1 in double-float, rows k and k + M/2 in one instruction (same
+      // results as the scalar form below)
+      constexpr int H = M / 2;
+#pragma unroll
+      for (int k = 0; k < H; k++) {
+        f32x2 dh = 0ull, dl = 0ull;
+#pragma unroll
+        for (int q = 1; q <= KS; q++) {
+          const f32x2 uh = pk(win_row<M, KS, KA>(fh, hhh, k + q), win_row<M, KS, KA>(fh, hhh, k + H + q));
+          const f32x2 ul = pk(win_row<M, KS, KA>(fl, hhl, k + q), win_row<M, KS, KA>(fl, hhl, k + H + q));
+          f32x2 ds, de;
+          two_diff2(uh, pk(fh[KS + k - q], fh[KS + k + H - q]), ds, de);
+          const f32x2 dlo = add2(de, sub2(ul, pk(fl[KS + k - q], fl[KS + k + H - q])));
+          const f32x2 W = a.wP[q - 1][0], NW = a.wP[q - 1][1], WL = a.wP[q - 1][2];
+          const f32x2 pr = mul2(W, ds);
+          const f32x2 pen = fma2(NW, ds, pr);  // -(error of pr)
+          const f32x2 plo = sub2(fma2(W, dlo, mul2(WL, ds)), pen);
+          if (q == 1) {
+            dh = pr;
+            dl = plo;
+          } else {
+            f32x2 sh, se;
+            two_sum2(dh, pr, sh, se);
+            dh = sh;
+            dl = add2(dl, add2(se, plo));
+          }
+        }
+        unpk(dh, bh[k], bh[k + H]);  // unnormalised pair, as below
+        unpk(dl, bl[k], bl[k + H]);
+      }
     } else {
       // a1 in double-float: b = sum_q w_q (f_{k+q} - f_{k-q})
 #pragma unroll
@@ -1149,7 +1309,8 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
 #pragma unroll
     for (int k = 0; k < M; k++) xh[k] = v[k];
     // refinement sweep 1: x <- x0 + A^{-1}(b - A x0), residual to FP64 accuracy
-    if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
+    if constexpr (FULL && (M % 2) == 0) residual_sym2<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
+    else if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
     else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, xch);
     solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
     if (a.sweeps < 2) {
@@ -1170,7 +1331,8 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         xh[k] = sm.hi;
         xl[k] = sm.lo;
       }
-      if constexpr (FULL) residual_sym<R, M, true>(bh, bl, xh, xl, v, i, t, xch);
+      if constexpr (FULL && (M % 2) == 0) residual_sym2<R, M, true>(bh, bl, xh, xl, v, i, t, xch);
+      else if constexpr (FULL) residual_sym<R, M, true>(bh, bl, xh, xl, v, i, t, xch);
       else residual_df<R, M, true, FULL>(bh, bl, xh, xl, v, size, i, t, xch);
       solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
 #pragma unroll
