@@ -207,6 +207,23 @@ __device__ __forceinline__ f2 split_f64(double x) {
   else hb = sign | 0x7f800000u;                                        // inf / overflow
   return {__uint_as_float(hb), 0.f};
 }
+// Fast path of split_f64 alone, for 2^-103 <= |x| < 2^128: the same pair in
+// fewer integer operations (the float's exponent field is the double's low 8
+// exponent bits minus 128, taken from a funnel shift of the two words).
+// Returns nonzero when x is outside that range (zero, tiny, huge, inf, nan);
+// the pair is then meaningless and split_f64 must be used instead.
+__device__ __forceinline__ unsigned split_fast(double x, f2& r) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned e = (hw >> 20) & 0x7ffu;
+  const unsigned F = __funnelshift_l(lw, hw, 3);  // (hw << 3) | (lw >> 29)
+  const unsigned sign = hw & 0x80000000u;
+  r.hi = __uint_as_float(((F - 0x40000000u) & 0x7fffffffu) | sign);
+  const unsigned SE = sign | ((e - 919u) << 23);
+  r.lo = __fsub_rn(__uint_as_float(SE | ((lw >> 6) & 0x7fffffu)), __uint_as_float(SE));
+  return (e - 920u) >= 231u ? 1u : 0u;
+}
+
 // FP32 -> FP64 bit pattern (exact for every float).
 __device__ __forceinline__ double f32_to_f64(float v) {
   const unsigned u = __float_as_uint(v);
@@ -465,10 +482,13 @@ struct WarpXchg {
   }
 };
 constexpr int kCtaXchgSlots = 4;  // 64-bit slots per thread: 2 buffers x 2 values
-struct CtaXchg {
+// STRIDE > 0: compile-time stride (the `stride` member is then unused).
+template <int STRIDE = 0>
+struct CtaXchgT {
   unsigned long long* buf;  // kCtaXchgSlots * blockDim.x slots
   int flip;
   int stride = 1, offset = 0;  // partition src lives in thread src * stride + offset
+  __device__ __forceinline__ int thread_of(int src) const { return (STRIDE > 0 ? src * STRIDE : src * stride) + offset; }
   template <typename V>
   static __device__ __forceinline__ unsigned long long bits(V v) {
     if constexpr (sizeof(V) == 8) return (unsigned long long)__double_as_longlong((double)v);
@@ -490,15 +510,15 @@ struct CtaXchg {
     unsigned long long* b = round();
     b[threadIdx.x] = bits(v);
     __syncthreads();
-    return value<V>(b[src * stride + offset]);
+    return value<V>(b[thread_of(src)]);
   }
   template <typename V>
   __device__ __forceinline__ void get2(V v, int a, int b_, V& ra, V& rb) {
     unsigned long long* b = round();
     b[threadIdx.x] = bits(v);
     __syncthreads();
-    ra = value<V>(b[a * stride + offset]);
-    rb = value<V>(b[b_ * stride + offset]);
+    ra = value<V>(b[thread_of(a)]);
+    rb = value<V>(b[thread_of(b_)]);
   }
   template <typename V>
   __device__ __forceinline__ void get_two(V va, int a, V vb, int b_, V& ra, V& rb) {
@@ -507,10 +527,11 @@ struct CtaXchg {
     b[threadIdx.x] = bits(va);
     b[n + threadIdx.x] = bits(vb);
     __syncthreads();
-    ra = value<V>(b[a * stride + offset]);
-    rb = value<V>(b[n + b_ * stride + offset]);
+    ra = value<V>(b[thread_of(a)]);
+    rb = value<V>(b[n + thread_of(b_)]);
   }
 };
+using CtaXchg = CtaXchgT<0>;
 
 // ------------------------------------------------- per-partition solve (a2-a4)
 // v[0..size) holds b of this partition on entry and x on exit.  Must be
@@ -911,16 +932,19 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //  kDirectX: x-lines, a warp holds one line and each lane reads and writes
 //    its own contiguous rows with 16-byte vector accesses (no staging).
 //  kDirectStrided: y/z lines, thread = (partition i, line g) with g fastest,
-//    so one warp-wide access of a row covers TL consecutive x positions of
-//    32 / TL partitions (full 32-byte sectors, no staging); the interface
-//    messages between partitions then cross warps through shared memory.
+//    so one warp-wide access of a row covers kStridedLines consecutive x
+//    positions of 32 / kStridedLines partitions (full 32-byte sectors, no
+//    staging); the interface messages between partitions then cross warps
+//    through shared memory.  The CTA has kStridedLines x pw threads.
 constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2;
+constexpr int kStridedLines = 8;
 
 // Exchanger of the interface messages for a layout: warp shuffles when a
-// warp holds a whole line, shared memory otherwise.
+// warp holds a whole line, shared memory otherwise (strided layout: partition
+// src of line g is thread src * kStridedLines + g).
 template <bool CTA>
-__device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int stride, int offset) {
-  if constexpr (CTA) return CtaXchg{reinterpret_cast<unsigned long long*>(smem), 0, stride, offset};
+__device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int offset) {
+  if constexpr (CTA) return CtaXchgT<kStridedLines>{reinterpret_cast<unsigned long long*>(smem), 0, 1, offset};
   else return WarpXchg{pw};
 }
 
@@ -952,9 +976,9 @@ struct ThreadPart {
 template <int M, bool FULL, int LAYOUT>
 __device__ __forceinline__ ThreadPart thread_part(const DevLineTables& t) {
   ThreadPart r;
-  const int pw = t.pw, TL = blockDim.x / pw;
-  r.g = LAYOUT == kDirectStrided ? threadIdx.x % TL : threadIdx.x / pw;
-  r.i = LAYOUT == kDirectStrided ? threadIdx.x / TL : threadIdx.x % pw;
+  const int pw = t.pw;
+  r.g = LAYOUT == kDirectStrided ? threadIdx.x % kStridedLines : threadIdx.x / pw;
+  r.i = LAYOUT == kDirectStrided ? threadIdx.x / kStridedLines : threadIdx.x % pw;
   r.lane_ok = r.i < t.p;
   r.start = 0;
   r.size = 2 * t.r;
@@ -1017,7 +1041,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   constexpr int KA = KS > 0 ? KS : 1;  // halo array size (KS = 0 compiles no stencil)
   TT* S = reinterpret_cast<TT*>(smem_raw);
   const int pw = t.pw;
-  const int TL = blockDim.x / pw;
+  const int TL = DSTR ? kStridedLines : blockDim.x / pw;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
   const int nl = tr.nl;
   const ThreadPart tp = thread_part<M, FULL, LAYOUT>(t);
@@ -1107,7 +1131,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   }
 
   TOut xo[M];
-  auto xch = make_xchg<DSTR>(pw, smem_raw, TL, g);
+  auto xch = make_xchg<DSTR>(pw, smem_raw, g);
   if constexpr (MODE != kModeRefine) {
     T v[M];
 #pragma unroll
@@ -1131,7 +1155,62 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     // into an FP32 pair as soon as it is loaded.
     float bh[M], bl[M];
     float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
-    if constexpr (PIPE) {
+    if constexpr (PIPE && sizeof(TIn) == 8) {
+      // whole-size partitions only (PIPE implies FULL)
+      const TIn* s0 = pslots + threadIdx.x;
+      const int bd = blockDim.x;
+      TIn own[M], lo_h[KA], hi_h[KA];
+      pipe_rows<M, TIn, DIRECT>(pslots, own);
+#pragma unroll
+      for (int q = 0; q < KS; q++) {
+        lo_h[q] = s0[(M + q) * bd];
+        hi_h[q] = s0[(M + KS + q) * bd];
+      }
+      if (ok) {
+        unsigned bad = 0u;
+        f2 sv;
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+          bad |= split_fast((double)own[k], sv);
+          fh[KS + k] = sv.hi;
+          fl[KS + k] = sv.lo;
+        }
+#pragma unroll
+        for (int q = 0; q < KS; q++) {
+          bad |= split_fast((double)lo_h[q], sv);
+          fh[q] = sv.hi;
+          fl[q] = sv.lo;
+          bad |= split_fast((double)hi_h[q], sv);
+          hhh[q] = sv.hi;
+          hhl[q] = sv.lo;
+        }
+        if (bad) {  // a zero or a value outside [2^-103, 2^128) in this thread's rows:
+                    // split them again (re-read from the slots) the general way
+          TIn again[M];
+          pipe_rows<M, TIn, DIRECT>(pslots, again);
+#pragma unroll
+          for (int k = 0; k < M; k++) {
+            sv = split_f64((double)again[k]);
+            fh[KS + k] = sv.hi;
+            fl[KS + k] = sv.lo;
+          }
+#pragma unroll
+          for (int q = 0; q < KS; q++) {
+            sv = split_f64((double)s0[(M + q) * bd]);
+            fh[q] = sv.hi;
+            fl[q] = sv.lo;
+            sv = split_f64((double)s0[(M + KS + q) * bd]);
+            hhh[q] = sv.hi;
+            hhl[q] = sv.lo;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < M + KS; k++) fh[k] = fl[k] = 0.f;
+#pragma unroll
+        for (int q = 0; q < KA; q++) hhh[q] = hhl[q] = 0.f;
+      }
+    } else if constexpr (PIPE) {
       const TIn* s0 = pslots + threadIdx.x;
       const int bd = blockDim.x;
       TIn own[M];
@@ -1314,11 +1393,11 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, xch);
     solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
     if (a.sweeps < 2) {
-      // x = x0 + delta: one FP64 add per unknown (the FP32 path leaves the
-      // FP64 pipe idle otherwise); exact integer conversions
+      // x = x0 + delta: the FP64 pipe (idle otherwise on this path) takes the
+      // add and delta's conversion, x0 is converted with integer operations
 #pragma unroll
       for (int k = 0; k < M; k++) {
-        const double xd = f32_to_f64_normal(xh[k]) + f32_to_f64_normal(v[k]);
+        const double xd = f32_to_f64_normal(xh[k]) + (double)v[k];
         if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
         else xo[k] = (TOut)(xh[k] + v[k]);
       }
@@ -1392,7 +1471,7 @@ template <int M, int KS, typename TIn, int LAYOUT>
 __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTables& t, const ThreadPart& tp,
                                               const int gx, const int tile, TIn* slots, const int buf) {
   constexpr int NS = M + 2 * KS;
-  const int bd = blockDim.x, TL = bd / t.pw;
+  const int bd = blockDim.x, TL = LAYOUT == kDirectStrided ? kStridedLines : bd / t.pw;
   const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
   if (tp.lane_ok && tp.g < tr.nl) {

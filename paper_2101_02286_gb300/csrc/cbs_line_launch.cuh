@@ -32,10 +32,10 @@ cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s
   if (a.nlines <= 0) return cudaSuccess;
   // 256 threads per CTA; small problems shrink the CTA (down to 64 threads)
   // until the grid covers every SM at least twice
-  int threads = kLineThreads;
+  int threads = LAYOUT == kDirectStrided ? kStridedLines * t.pw : kLineThreads;
   dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
   const int64_t want = 2 * (int64_t)sm_count();
-  while (threads > 64 && threads > t.pw && (int64_t)grid.x * grid.y < want) {
+  while (LAYOUT != kDirectStrided && threads > 64 && threads > t.pw && (int64_t)grid.x * grid.y < want) {
     threads /= 2;
     grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
   }
@@ -61,7 +61,7 @@ template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOU
 cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if (a.nlines <= 0) return cudaSuccess;
   constexpr int NS = M + 2 * KS;
-  const int threads = kLineThreads;
+  const int threads = LAYOUT == kDirectStrided ? kStridedLines * t.pw : kLineThreads;
   const dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
   const int64_t ntiles = (int64_t)grid.x * grid.y;
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;

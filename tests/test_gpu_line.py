@@ -168,3 +168,19 @@ def test_interface_stages_below_rounding_skip_messages(cuda):
     li = long_plan.info()
     assert li["kernel"] == 1 and li["message_stages"] == 0 and li["inner_message_stages"] >= 1
     long_plan.close()
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_refine_zeros_and_tiny_values(cuda, direction):
+    # whole-size partitions (n = 32 x 16): exact zeros and values far below
+    # the FP32 range take the general FP64 -> FP32-pair split
+    rng = np.random.default_rng(21 + direction)
+    shape = [6, 10, 16]
+    shape[2 - direction] = 512
+    f = rng.uniform(-1, 1, size=tuple(shape))
+    mask = rng.random(f.shape)
+    f[mask < 0.1] = 0.0
+    f[(mask >= 0.1) & (mask < 0.12)] *= 1e-35
+    got, info = gpu_derivative(f, direction, "tri6", precision="fp32_refine", segments=32)
+    assert info["rows_big"] == 16
+    assert oracle.rel_err(got, oracle_derivative(f, direction, "tri6")) < 1e-12
