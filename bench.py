@@ -57,6 +57,10 @@ def parse():
                     help="headline solves only (W + K steps of x, y, z), for profiler captures")
     ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64", "fp32"],
                     help="path run by --profile (the timed headline is always fp32_refine)")
+    ap.add_argument("--workload", default="cube", choices=["cube", "long", "var"],
+                    help="what --profile runs: the n^3 field (cube), the 32 x 2^22 pentadiagonal lines "
+                         "(long, FP32 right-hand side, refinement with 2 sweeps, 1024 segments) or the "
+                         "256^3 variable-alpha forward + adjoint (var)")
     ap.add_argument("--segments", default="tune",
                     help="partitions per line: 'tune' (autotuner) or a fixed count")
     ap.add_argument("--no-configs", action="store_true",
@@ -344,7 +348,7 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     gseed = np.random.default_rng(18).standard_normal(f.shape)
     for prec, dt, bpu_f, bpu_b in (("fp64", torch.float64, 24, 40), ("fp32", torch.float32, 12, 20)):
         fa, aa, ga = (torch.from_numpy(a).to(dev, dt) for a in (f, al, gseed))
-        pl = variable_plan(f.shape, 0, aa, c4, hv, prec)
+        pl = variable_plan(f.shape, 0, aa, c4, hv, prec, segments="tune")
         x = torch.empty_like(fa)
         gf, gal = torch.empty_like(fa), torch.empty_like(fa)
         ms_f = time_ms(lambda: pl.solve(fa, x, stream), stream, steps)
@@ -364,6 +368,45 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
         res.append(_entry(w + ", adjoint (grad f and grad alpha)", 256 ** 3, ms_b, bpu_b, hbm, eb, sampled_lines=32))
         pl.close()
     return res
+
+def profile_other(args, dev, stream, rank):
+    """--profile for the long-line or variable-alpha workload: W warm-up
+    and K further solves, nothing timed, for profiler captures."""
+    import torch
+    from paper_2101_02286_gb300 import abi
+    from paper_2101_02286_gb300 import workloads as W
+    from paper_2101_02286_gb300.autograd import variable_plan
+    from paper_2101_02286_gb300.solver import Plan
+    if args.workload == "long":
+        d = W.long_lines()
+        lines, n = d.shape
+        di = torch.from_numpy(d.reshape(1, lines, n)).to(dev)
+        do = torch.empty((1, lines, n), dtype=torch.float64, device=dev)
+        prec = args.precision
+        pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=1024, precision=prec,
+                  sweeps=2 if prec == "fp32_refine" else 1, in_dtype=torch.float32)
+        for _ in range(args.warmup + args.steps):
+            pl.solve(di, do, stream)
+        info = pl.info()
+    else:
+        f, al = W.variable_alpha_cube(256)
+        dt = torch.float64 if args.precision != "fp32" else torch.float32
+        fa, aa = (torch.from_numpy(a).to(dev, dt) for a in (f, al))
+        pl = variable_plan(f.shape, 0, aa, W.CENTRAL4["rhs"], W.grid_spacing(256),
+                           "fp64" if dt == torch.float64 else "fp32")
+        x, g, gf, ga = (torch.empty_like(fa) for _ in range(4))
+        g.copy_(fa)
+        for _ in range(args.warmup + args.steps):  # forward, then adjoint
+            pl.solve(fa, x, stream)
+            abi.cbs_solve_transpose(pl.handle, g.data_ptr(), x.data_ptr(), None, gf.data_ptr(), ga.data_ptr(),
+                                    stream.cuda_stream)
+        info = pl.info()
+    torch.cuda.synchronize(dev)
+    if rank == 0:
+        print(json.dumps({"profile": True, "workload": args.workload, "precision": args.precision,
+                          "steps": args.steps, "warmup": args.warmup, "segments": info["segments"]}))
+    pl.close()
+
 
 # ---------------------------------------------------------------- GPU
 def main():
@@ -386,6 +429,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.profile and args.workload != "cube":
+        profile_other(args, dev, stream, rank)
+        return
     n = args.size
     f_host, modes = W.noisy_cube(n)  # seeded: U(-1,1) + one plane wave
     f_pin = torch.from_numpy(f_host).pin_memory()

@@ -33,8 +33,28 @@ struct VarArgs {
   int* status;
 };
 
-__device__ __forceinline__ double rcp_(double v) { return 1.0 / v; }
-__device__ __forceinline__ float rcp_(float v) { return 1.0f / v; }
+// Pivot reciprocals of the per-line factorisation.  The FP64 pipe bounds
+// this kernel, and an IEEE division costs several FP64 instructions more
+// than Newton-Raphson on the hardware's approximate reciprocal: r <- r + r e
+// with e = 1 - v r squares the relative error at every step, so two steps
+// from the approximation reach FP64 rounding (within an ulp or two; not
+// correctly rounded).  The pivots are normal numbers (|1 - alpha^2 ...| of a
+// diagonally dominant band), where the flush-to-zero variant is exact.
+__device__ __forceinline__ double rcp_(double v) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+  double e = fma(-v, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-v, r, 1.0);
+  return fma(r, e, r);
+}
+// FP32: the hardware reciprocal (about one ulp) is accurate enough for the
+// FP32 solve.
+__device__ __forceinline__ float rcp_(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 
 // Variable-band line kernel.  ADJ = false: forward solve; ADJ = true:
 // transposed solve + S^T + band gradient.  T: arithmetic type, TG: element
@@ -194,13 +214,33 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
   // interface row `start`: lo couples to the previous partition's last bulk
   // row (L~_i), up to this partition's first bulk row (U~_i)
   const T Lt = lo[0], Ut = upb[0];
-  double W = 1.0 - (double)Lt * (double)rp - (double)Ut * (double)sc[1];
-  double Lh = -(double)Lt * (double)sp_;
-  double Uh = -(double)Ut * (double)rc[1];
-  double xt = (double)b[0] - (double)Lt * (double)yp - (double)Ut * (double)y[1];
+  T W = T(1) - Lt * rp - Ut * sc[1];
+  T Lh = -Lt * sp_;
+  T Uh = -Ut * rc[1];
+  T xt = b[0] - Lt * yp - Ut * y[1];
 
-  // ---- Algorithms 1-4 on (L-hat, W, U-hat, x~), FP64 ----
+  // ---- Algorithms 1-4 on (L-hat, W, U-hat, x~), in the solve's precision ----
+  // Once every coupling block of every line in the warp is below 2^-60
+  // (FP64) / 2^-30 (FP32) of its diagonal block, the remaining steps change
+  // nothing above rounding: PCR and detach steps are skipped and reattach /
+  // final steps keep only their diagonal division.  The blocks shrink
+  // geometrically with the partition size (diagonal dominance) and square at
+  // every PCR step, so this usually ends the loop after a few steps.
+  const T tiny = sizeof(T) == 8 ? T(8.673617379884035e-19) : T(9.313225746154785e-10);  // 2^-60, 2^-30
+  bool decoupled = false;
   for (int st = 0; st < t.nstage; st++) {
+    if (!decoupled)
+      decoupled = __all_sync(kFull, !lane_ok || (fabs(Lh) <= tiny * fabs(W) && fabs(Uh) <= tiny * fabs(W)));
+    if (decoupled) {
+      const int type = a.stage_type[st], s = a.stage_s[st], na = a.stage_na[st];
+      if (!lane_ok) continue;
+      if (type == kFinal) {
+        if (i < na) xt = xt * rcp_(t.cyclic ? (W + Lh + Uh) : W);
+      } else if (type == kReattach) {
+        if (i >= na && i < na + s) xt = xt * rcp_(W);
+      }
+      continue;
+    }
     const int type = a.stage_type[st], s = a.stage_s[st], na = a.stage_na[st];
     int src1 = i, src2 = i;
     if (type == kDetach) {
@@ -214,43 +254,43 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
       src2 = (i >= na && i < na + s) ? i - na : i;  // x~_{i+s} lives at i - na
     }
     if (!lane_ok) src1 = src2 = i;
-    const double L1 = __shfl_sync(kFull, Lh, src1, pw), W1 = __shfl_sync(kFull, W, src1, pw);
-    const double U1 = __shfl_sync(kFull, Uh, src1, pw), X1 = __shfl_sync(kFull, xt, src1, pw);
-    const double L2 = __shfl_sync(kFull, Lh, src2, pw), W2 = __shfl_sync(kFull, W, src2, pw);
-    const double U2 = __shfl_sync(kFull, Uh, src2, pw), X2 = __shfl_sync(kFull, xt, src2, pw);
+    const T L1 = __shfl_sync(kFull, Lh, src1, pw), W1 = __shfl_sync(kFull, W, src1, pw);
+    const T U1 = __shfl_sync(kFull, Uh, src1, pw), X1 = __shfl_sync(kFull, xt, src1, pw);
+    const T L2 = __shfl_sync(kFull, Lh, src2, pw), W2 = __shfl_sync(kFull, W, src2, pw);
+    const T U2 = __shfl_sync(kFull, Uh, src2, pw), X2 = __shfl_sync(kFull, xt, src2, pw);
     if (!lane_ok) continue;
     if (type == kDetach) {
       if (i >= na - s && i < na) {
-        const double k = Uh / W1;
+        const T k = Uh * rcp_(W1);
         W -= k * L1;
         xt -= k * X1;
         Uh = -k * U1;
       }
       if (i < s) {
-        const double k = Lh / W2;
+        const T k = Lh * rcp_(W2);
         W -= k * U2;
         xt -= k * X2;
         Lh = -k * L2;
       }
     } else if (type == kPcr) {
       if (i < na) {
-        const double kp = Uh / W1, km = Lh / W2;
-        const double Wn = W - kp * L1 - km * U2;
-        const double xn = xt - kp * X1 - km * X2;
-        const double Ln = -km * L2, Un = -kp * U1;
+        const T kp = Uh * rcp_(W1), km = Lh * rcp_(W2);
+        const T Wn = W - kp * L1 - km * U2;
+        const T xn = xt - kp * X1 - km * X2;
+        const T Ln = -km * L2, Un = -kp * U1;
         W = Wn;
         xt = xn;
         Lh = Ln;
         Uh = Un;
       }
     } else if (type == kFinal) {
-      if (i < na) xt = xt / (t.cyclic ? (W + Lh + Uh) : W);
+      if (i < na) xt = xt * rcp_(t.cyclic ? (W + Lh + Uh) : W);
     } else {
-      if (i >= na && i < na + s) xt = (xt - Lh * X1 - Uh * X2) / W;
+      if (i >= na && i < na + s) xt = (xt - Lh * X1 - Uh * X2) * rcp_(W);
     }
   }
-  const double xn = __shfl_sync(kFull, xt, next, pw);
-  const T xa = (T)xt, xb = (T)xn;
+  const T xn = __shfl_sync(kFull, xt, next, pw);
+  const T xa = xt, xb = xn;
   // back-substitution (Eq. 22); row 0 is the interface unknown
   T x[M];
   x[0] = xa;
