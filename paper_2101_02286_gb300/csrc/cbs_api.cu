@@ -259,34 +259,11 @@ cbs_status fill_dev_tables(DevLineTables& D, const LineTables& T, const Bands& A
   return CBS_OK;
 }
 
-// Long lines: p segments per line, one CTA per segment (cbs_long.cu).
-cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
-  if (d->direction != 0 || d->rhs_kind != CBS_RHS_NONE || !d->cyclic || d->lhs_kind != CBS_LHS_TOEPLITZ)
-    return fail(CBS_ERR_UNSUPPORTED, "long lines: x-lines, right-hand side given, cyclic Toeplitz bands");
-  const int n = P->n, r = P->r;
-  int p = d->segments;
-  if (!p) {  // segments of about 4096 rows that divide the line
-    p = (n + 4095) / 4096;
-    while (p < n && n % p) p++;
-  }
-  if (n % p) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments must divide n");
-  const int m = n / p, N = m - r;
-  const int pin = (N + 15) / 16;
-  if (pin > 512) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments above 8192 rows (raise segments)");
-  if (N < 2 * r * pin || m < 4 * r) return fail(CBS_ERR_INVALID_ARG, "long lines: segments too short");
-  Bands A;
-  A.r = r;
-  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
-  A.v[r] = 1.0;
-  A.v[r - 1] = A.v[r + 1] = d->alpha;
-  if (r == 2) A.v[0] = A.v[4] = d->beta;
-  bool singular = false;
-  std::string msg = build_line_tables(P->host, n, A, p, true, &singular, 1 << 30);
-  if (msg.empty()) msg = build_line_tables(P->inner, N, A, pin, false, &singular, 1 << 30);
-  if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
-  // leading entries of the first r rows of D^{-1}: keep K with a tail below
-  // 2^-60 of each row's l1 norm (all K = N when the rows do not decay)
-  std::vector<double> Gfull = bulk_inverse_rows(P->host, N, r);
+// Leading entries of the first r rows of D^{-1} for a bulk block of N rows:
+// keeps K entries per row with a tail below 2^-60 of the row's l1 norm (K = N
+// when the rows do not decay).  G is [q][K].
+static int truncated_inverse_rows(const LineTables& T, int N, int r, std::vector<double>& G) {
+  std::vector<double> Gfull = bulk_inverse_rows(T, N, r);
   int K = 1;
   for (int q = 0; q < r; q++) {
     double tot = 0.0;
@@ -302,14 +279,97 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
     }
     K = std::max(K, kq);
   }
-  std::vector<double> G((size_t)r * K);
+  G.assign((size_t)r * K, 0.0);
   for (int q = 0; q < r; q++)
     for (int j = 0; j < K; j++) G[(size_t)q * K + j] = Gfull[(size_t)q * N + j];
+  return K;
+}
+
+// Long lines: p segments per line, one CTA per segment (cbs_long.cu).
+//
+// Segment layout.  When n - p r is a multiple of 16, the segments get
+// 16 K + r rows (the first cbig of them) or 16 (K - 1) + r rows, so every
+// segment's bulk is a whole number of 16-row inner partitions and the segment
+// kernel runs with compile-time partition sizes; a segment's end rows are
+// computed from the same truncated rows of D^{-1} when both sizes agree on
+// them to 2^-60.  Otherwise p must divide n and the segments are equal, with
+// ragged inner partitions.
+cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
+  if (d->direction != 0 || d->rhs_kind != CBS_RHS_NONE || !d->cyclic || d->lhs_kind != CBS_LHS_TOEPLITZ)
+    return fail(CBS_ERR_UNSUPPORTED, "long lines: x-lines, right-hand side given, cyclic Toeplitz bands");
+  const int n = P->n, r = P->r;
+  int p = d->segments;
+  if (!p) {  // segments of about 4096 rows
+    p = (n + 4095) / 4096;
+    if ((n - (int64_t)p * r) % 16 != 0)
+      while (p < n && n % p) p++;
+  }
+  Bands A;
+  A.r = r;
+  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
+  A.v[r] = 1.0;
+  A.v[r - 1] = A.v[r + 1] = d->alpha;
+  if (r == 2) A.v[0] = A.v[4] = d->beta;
+  bool singular = false;
+  std::string msg;
+  std::vector<double> G;
+  int K = 0;
+  bool full = false;
+  int sizes[3] = {p, 0, 0};
+  // whole 16-row inner partitions
+  if (p >= 1 && (n - (int64_t)p * r) % 16 == 0 && n - (int64_t)p * r >= 32 * (int64_t)p) {
+    const int64_t T16 = (n - (int64_t)p * r) / 16;        // 16-row blocks of all bulks
+    const int64_t K16 = (T16 + p - 1) / p;                 // blocks of a big segment
+    const int64_t cbig = T16 - (int64_t)p * (K16 - 1);     // in [1, p]
+    if (K16 <= 512 && K16 - 1 >= 2 * r) {
+      sizes[0] = (int)cbig;
+      sizes[1] = (int)(16 * K16 + r);
+      sizes[2] = (int)(16 * (K16 - 1) + r);
+      msg = build_line_tables(P->host, n, A, p, true, &singular, 1 << 30, sizes);
+      if (msg.empty())
+        msg = build_line_tables(P->inner, (int)(16 * K16), A, (int)K16, false, &singular, 1 << 30);
+      if (msg.empty() && cbig < p)
+        msg = build_line_tables(P->inner_small, (int)(16 * (K16 - 1)), A, (int)(K16 - 1), false, &singular,
+                                1 << 30);
+      if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
+      K = truncated_inverse_rows(P->host, (int)(16 * K16), r, G);
+      full = true;
+      if (cbig < p) {  // the small segments must share the truncated rows
+        std::vector<double> G2;
+        const int K2 = truncated_inverse_rows(P->host, (int)(16 * (K16 - 1)), r, G2);
+        double tot = 0.0, diff = 0.0;
+        for (size_t k = 0; k < G.size(); k++) tot += std::fabs(G[k]);
+        if (K2 != K || K >= 16 * (K16 - 1)) full = false;
+        for (size_t k = 0; full && k < G.size(); k++) diff = std::fmax(diff, std::fabs(G[k] - G2[k]));
+        if (diff > std::ldexp(tot, -60)) full = false;
+      }
+    }
+  }
+  if (!full) {
+    if (p < 1 || n % p) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments must divide n");
+    sizes[0] = p;
+    sizes[1] = sizes[2] = n / p;
+  }
+  const int m = sizes[1], N = m - r;
+  const int pin = full ? N / 16 : (N + 15) / 16;
+  if (pin > 512) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments above 8192 rows (raise segments)");
+  if (N < 2 * r * pin || m < 4 * r) return fail(CBS_ERR_INVALID_ARG, "long lines: segments too short");
+  if (!full) {
+    msg = build_line_tables(P->host, n, A, p, true, &singular, 1 << 30);
+    if (msg.empty()) msg = build_line_tables(P->inner, N, A, pin, false, &singular, 1 << 30);
+    if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
+    K = truncated_inverse_rows(P->host, N, r, G);
+  }
   cbs_status st = fill_dev_tables(P->dev, P->host, A, d, 0, &P->dbuf, false);
   if (st) return st;
   const int threads = ((pin + 31) / 32) * 32;
   st = fill_dev_tables(P->dev_inner, P->inner, A, d, threads, &P->lbuf, true);
   if (st) return st;
+  if (full && sizes[0] < p) {
+    st = fill_dev_tables(P->dev_inner_small, P->inner_small, A, d, threads, &P->lbuf_small, true);
+    if (st) return st;
+  }
+  P->inner_full = full;
   // scratch: yb, cc (2r per segment), xt (r per segment), then G
   const size_t nseg = (size_t)P->nlines * p;
   const size_t bytes = (nseg * (5 * r) + G.size()) * sizeof(double);
@@ -332,6 +392,8 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   a.p = p;
   a.m = m;
   a.r = r;
+  a.cbig = sizes[0];
+  a.msmall = sizes[2];
   a.sweeps = d->refine_sweeps;
   for (int k = 0; k < 2 * kMaxR + 1; k++) a.band[k] = A.v[k];
   P->kind = 1;
@@ -450,6 +512,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
       if (st) {
         if (P->dbuf) cudaFree(P->dbuf);
         if (P->lbuf) cudaFree(P->lbuf);
+        if (P->lbuf_small) cudaFree(P->lbuf_small);
         if (P->sbuf) cudaFree(P->sbuf);
         if (P->dstatus) cudaFree(P->dstatus);
         delete P;
@@ -561,6 +624,7 @@ cbs_status cbs_plan_destroy(cbs_plan* P) {
   cudaDeviceSynchronize();
   if (P->dbuf) cudaFree(P->dbuf);
   if (P->lbuf) cudaFree(P->lbuf);
+  if (P->lbuf_small) cudaFree(P->lbuf_small);
   if (P->sbuf) cudaFree(P->sbuf);
   if (P->dstatus) cudaFree(P->dstatus);
   delete P;
@@ -619,7 +683,8 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     la.out = out;
     int launches = 0;
     cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->dev,
-                                P->dev_inner, (cudaStream_t)stream, &launches);
+                                P->dev_inner, (P->inner_full && la.cbig < la.p) ? &P->dev_inner_small : nullptr,
+                                P->inner_full, (cudaStream_t)stream, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "long-line kernel launch");
     g_launches = launches;
     return CBS_OK;
@@ -840,7 +905,7 @@ cbs_status cbs_autotune(const cbs_desc* d, int32_t reps, int32_t* best_segments,
   for (int p = 1; p <= kMaxLanes; p++)
     if (n >= 2 * r * p) cand.push_back(p);
   for (int p = kMaxLanes + 1; p <= n / 64 && (int)cand.size() < 256; p++)
-    if (n % p == 0 && n / p <= 8192 + r) cand.push_back(p);
+    if ((n % p == 0 || (n - p * r) % 16 == 0) && n / p <= 8192 + r) cand.push_back(p);
   const int64_t elems = d->dims[0] * d->dims[1] * d->dims[2];
   const size_t isz = d->in_dtype == CBS_DTYPE_F64 ? 8 : 4, osz = d->out_dtype == CBS_DTYPE_F64 ? 8 : 4;
   void *in = nullptr, *out = nullptr, *bands = nullptr;

@@ -70,8 +70,10 @@ struct LineTables {
 
 // Build the tables. Returns "" on success or an error message; *singular is
 // set when a pivot or interface block is zero / non-finite.
+// sizes (optional): {count_big, rows_big, rows_small} instead of the default
+// rule (first n mod p partitions get ceil(n / p) rows, the rest floor).
 std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool cyclic,
-                              bool* singular, int max_lanes);
+                              bool* singular, int max_lanes, const int* sizes = nullptr);
 
 // Rows q < nrows of D^{-1} for the bulk block of N rows of plan tables T
 // (forward/backward elimination with T.fac), row-major nrows x N.

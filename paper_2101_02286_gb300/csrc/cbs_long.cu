@@ -1,7 +1,8 @@
 // cbs_long.cu -- lines too long for one warp: p segments per line, one CTA
 // per segment (the paper's distributed level across thread blocks).
 //
-// A solve is three launches on one stream:
+// A solve is three launches on one stream (four when the segments come in
+// two sizes, see create_long: the segment kernel then runs once per size):
 //   1. ends:  for every segment only the first r and last r rows of
 //             y_i = D_i^{-1} b_i are needed (Sec. 4: only those rows cross
 //             partitions).  They are dot products of the segment's right-hand
@@ -18,7 +19,10 @@
 //             CTA's threads are acyclic sub-partitions exchanging through
 //             shared memory; FP64, FP32, or FP32 + refinement with an
 //             FP64-accurate residual.  Writes every row of x, interface rows
-//             included.
+//             included.  When every segment's bulk is a whole number of
+//             16-row inner partitions, the partition sizes are compile-time
+//             constants and the refinement residual runs two rows per
+//             instruction.
 // Scratch: yb and cc (2r doubles per segment) and xt (r doubles per segment).
 #include <mutex>
 #include <string>
@@ -31,13 +35,20 @@ namespace cbs {
 
 
 
+// First row and row count of segment s (the first cbig segments have m rows,
+// the rest msmall).
+__device__ __forceinline__ int64_t seg_start(const LongArgs& a, int s) {
+  return s < a.cbig ? (int64_t)s * a.m : (int64_t)a.cbig * a.m + (int64_t)(s - a.cbig) * a.msmall;
+}
+__device__ __forceinline__ int seg_rows(const LongArgs& a, int s) { return s < a.cbig ? a.m : a.msmall; }
+
 // ---------------------------------------------------------------- 1. ends
 template <typename TIn>
 __global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a) {
   const int seg = blockIdx.x;
   const int64_t line = blockIdx.y;
-  const int r = a.r, N = a.m - r;
-  const TIn* b = (const TIn*)a.in + line * a.n + (int64_t)seg * a.m + r;  // first bulk row
+  const int r = a.r, N = seg_rows(a, seg) - r;
+  const TIn* b = (const TIn*)a.in + line * a.n + seg_start(a, seg) + r;  // first bulk row
   double accF[kMaxR], accL[kMaxR];
 #pragma unroll
   for (int q = 0; q < kMaxR; q++) accF[q] = accL[q] = 0.0;
@@ -83,7 +94,7 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
     const int im = (i == 0) ? p - 1 : i - 1;
     for (int q = 0; q < r; q++) {
-      double v = (double)__ldg(bl + (int64_t)i * a.m + q);
+      double v = (double)__ldg(bl + seg_start(a, i) + q);
       for (int e = 0; e < r; e++) {
         v -= t.Lt[q][e] * yb[im * 2 * r + r + e];
         v -= t.Ut[q][e] * yb[i * 2 * r + e];
@@ -137,19 +148,21 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 
 // ---------------------------------------------------------------- 3. segments
 // One CTA per (segment, line); thread i = inner partition i of the segment's
-// bulk rows (acyclic, tables `tin`).
-template <int R, int M, int MODE, typename TIn, typename TOut>
-__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin) {
+// bulk rows (acyclic, tables `tin`).  Segments seg0 + blockIdx.x.  FULL: every
+// inner partition has exactly M rows (whole-16-row layout): sizes are
+// compile-time and the refinement uses the paired residual.
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL>
+__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin, const int seg0) {
   extern __shared__ __align__(16) unsigned long long xbuf[];  // kCtaXchgSlots * blockDim slots
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
-  const int seg = blockIdx.x;
+  const int seg = seg0 + blockIdx.x;
   const int64_t line = blockIdx.y;
   const int i = threadIdx.x, P = tin.p;
   const bool lane_ok = i < P;
-  int start = 0, size = 2 * R;
-  if (lane_ok) partition_of(tin, i, start, size);
-  const int N = a.m - R;
-  const int64_t row0 = line * a.n + (int64_t)seg * a.m;  // segment's first row
+  int start = 0, size = FULL ? M : 2 * R;
+  if (FULL) start = i * M;
+  else if (lane_ok) partition_of(tin, i, start, size);
+  const int64_t row0 = line * a.n + seg_start(a, seg);  // segment's first row
   const TIn* b = (const TIn*)a.in + row0 + R + start;   // this partition's bulk rows
   TOut* x = (TOut*)a.out + row0 + R + start;
   const double* xt_here = a.xt + (line * a.p + seg) * R;
@@ -167,17 +180,23 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
     T v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-      T val = (lane_ok && k < size) ? conv<T>(__ldg(b + k)) : T(0);
+      T val = (lane_ok && (FULL || k < size)) ? conv<T>(__ldg(b + k)) : T(0);
       if (k < R) val -= conv<T>(cF[k]);
 #pragma unroll
-      for (int e = 0; e < R; e++) val -= sel(k == size - R + e, conv<T>(cL[e]), T(0));
+      for (int e = 0; e < R; e++) {
+        if (FULL) {
+          if (k == M - R + e) val -= conv<T>(cL[e]);
+        } else {
+          val -= sel(k == size - R + e, conv<T>(cL[e]), T(0));
+        }
+      }
       v[k] = val;
     }
-    solve_partition<T, R, M, T, false>(v, size, i, lane_ok, tin, xch);
+    solve_partition<T, R, M, T, FULL>(v, size, i, lane_ok, tin, xch);
     if (lane_ok) {
 #pragma unroll
       for (int k = 0; k < M; k++)
-        if (k < size) x[k] = conv<TOut>(v[k]);
+        if (FULL || k < size) x[k] = conv<TOut>(v[k]);
     }
   } else {
     float bh[M], bl[M], xh[M], xl[M], v[M];
@@ -190,30 +209,39 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
 #pragma unroll
     for (int k = 0; k < M; k++) {
       f2 s = {0.f, 0.f};
-      if (lane_ok && k < size) s = split_in(__ldg(b + k));
+      if (lane_ok && (FULL || k < size)) s = split_in(__ldg(b + k));
       // subtract the correction (zero on all but the edge rows) exactly
       f2 c = {0.f, 0.f};
       if (k < R) c = sF[k];
 #pragma unroll
       for (int e = 0; e < R; e++) {
-        c.hi = sel(k == size - R + e, sL[e].hi, c.hi);
-        c.lo = sel(k == size - R + e, sL[e].lo, c.lo);
+        if (FULL) {
+          if (k == M - R + e) c = sL[e];
+        } else {
+          c.hi = sel(k == size - R + e, sL[e].hi, c.hi);
+          c.lo = sel(k == size - R + e, sL[e].lo, c.lo);
+        }
       }
       const f2 d = two_sum(s.hi, -c.hi);
       bh[k] = d.hi;
       bl[k] = d.lo + (s.lo - c.lo);
       v[k] = d.hi;
     }
-    solve_partition<float, R, M, float, false>(v, size, i, lane_ok, tin, xch);
+    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, tin, xch);
 #pragma unroll
     for (int k = 0; k < M; k++) {
       xh[k] = v[k];
       xl[k] = 0.f;
     }
     for (int sw = 0; sw < a.sweeps; sw++) {
-      if (sw == 0) residual_df<R, M, false, false>(bh, bl, xh, xl, v, size, i, tin, xch);
-      else residual_df<R, M, true, false>(bh, bl, xh, xl, v, size, i, tin, xch);
-      solve_partition<float, R, M, float, false>(v, size, i, lane_ok, tin, xch);
+      if constexpr (FULL && (M % 2) == 0) {
+        if (sw == 0) residual_sym2<R, M, false>(bh, bl, xh, xl, v, i, tin, xch);
+        else residual_sym2<R, M, true>(bh, bl, xh, xl, v, i, tin, xch);
+      } else {
+        if (sw == 0) residual_df<R, M, false, false>(bh, bl, xh, xl, v, size, i, tin, xch);
+        else residual_df<R, M, true, false>(bh, bl, xh, xl, v, size, i, tin, xch);
+      }
+      solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, tin, xch);
 #pragma unroll
       for (int k = 0; k < M; k++) {
         const f2 s = two_sum(xh[k], v[k]);
@@ -224,7 +252,7 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
     if (lane_ok) {
 #pragma unroll
       for (int k = 0; k < M; k++)
-        if (k < size) x[k] = (TOut)(f32_to_f64(xh[k]) + f32_to_f64(xl[k]));
+        if (FULL || k < size) x[k] = (TOut)(f32_to_f64(xh[k]) + f32_to_f64(xl[k]));
     }
   }
   // the segment's interface rows
@@ -233,7 +261,8 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
-                        const DevLineTables& inner, cudaStream_t s, int* launches) {
+                        const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
+                        int* launches) {
   *launches = 0;
   const dim3 gs((unsigned)a.p, (unsigned)a.lines);
   if (in64) long_ends_kernel<double><<<gs, 128, 0, s>>>(a);
@@ -254,23 +283,37 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
   else long_iface_kernel<float><<<(unsigned)a.lines, ithreads, ismem, s>>>(a, outer);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int threads = ((inner.p + 31) / 32) * 32;
-  const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
-#define CBS_SEG(MO, RR, TI, TO) long_seg_kernel<RR, 16, MO, TI, TO><<<gs, threads, smem, s>>>(a, inner)
-  if (mode == kModeRefine) {
-    if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }
-    else { if (in64) CBS_SEG(kModeRefine, 2, double, double); else CBS_SEG(kModeRefine, 2, float, double); }
-  } else if (mode == kModeF64) {
-    if (R == 1) { if (in64) CBS_SEG(kModeF64, 1, double, double); else CBS_SEG(kModeF64, 1, float, double); }
-    else { if (in64) CBS_SEG(kModeF64, 2, double, double); else CBS_SEG(kModeF64, 2, float, double); }
-  } else {
-    if (R == 1) { if (in64) CBS_SEG(kModeF32, 1, double, float); else CBS_SEG(kModeF32, 1, float, float); }
-    else { if (in64) CBS_SEG(kModeF32, 2, double, float); else CBS_SEG(kModeF32, 2, float, float); }
-  }
+  *launches = 2;
+  // segment launches: the first cbig segments with `inner`, the rest with
+  // `inner_small` (whole-16-row layout with two sizes)
+  const int nbig = inner_small ? a.cbig : a.p;
+  for (int part = 0; part < (inner_small ? 2 : 1); part++) {
+    const DevLineTables& tin = part == 0 ? inner : *inner_small;
+    const int seg0 = part == 0 ? 0 : nbig, nseg = part == 0 ? nbig : a.p - nbig;
+    if (nseg <= 0) continue;
+    const dim3 g((unsigned)nseg, (unsigned)a.lines);
+    const int threads = ((tin.p + 31) / 32) * 32;
+    const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
+#define CBS_SEG(MO, RR, TI, TO)                                                                   \
+  do {                                                                                            \
+    if (full) long_seg_kernel<RR, 16, MO, TI, TO, true><<<g, threads, smem, s>>>(a, tin, seg0);   \
+    else long_seg_kernel<RR, 16, MO, TI, TO, false><<<g, threads, smem, s>>>(a, tin, seg0);       \
+  } while (0)
+    if (mode == kModeRefine) {
+      if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }
+      else { if (in64) CBS_SEG(kModeRefine, 2, double, double); else CBS_SEG(kModeRefine, 2, float, double); }
+    } else if (mode == kModeF64) {
+      if (R == 1) { if (in64) CBS_SEG(kModeF64, 1, double, double); else CBS_SEG(kModeF64, 1, float, double); }
+      else { if (in64) CBS_SEG(kModeF64, 2, double, double); else CBS_SEG(kModeF64, 2, float, double); }
+    } else {
+      if (R == 1) { if (in64) CBS_SEG(kModeF32, 1, double, float); else CBS_SEG(kModeF32, 1, float, float); }
+      else { if (in64) CBS_SEG(kModeF32, 2, double, float); else CBS_SEG(kModeF32, 2, float, float); }
+    }
 #undef CBS_SEG
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  *launches = 3;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++*launches;
+  }
   return cudaSuccess;
 }
 
@@ -350,7 +393,8 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
   const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
   int launches = 0;
   cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->dev,
-                              P->dev_inner, (cudaStream_t)stream, &launches);
+                              P->dev_inner, (P->inner_full && a.cbig < a.p) ? &P->dev_inner_small : nullptr,
+                              P->inner_full, (cudaStream_t)stream, &launches);
   if (e != cudaSuccess) return set_error(CBS_ERR_CUDA, std::string("long-line kernel launch: ") + cudaGetErrorString(e));
   set_launch_count(launches);
   return CBS_OK;

@@ -15,7 +15,8 @@ struct LongArgs {
   const double* G;    // [q][K]: leading entries of rows q < r of D^{-1}
   int K;              // kept entries per row
   int64_t lines;
-  int n, p, m, r;     // line length, segments, rows per segment, half bandwidth
+  int n, p, m, r;     // line length, segments, rows of the first cbig segments, half bandwidth
+  int cbig, msmall;   // segments cbig.. have msmall rows
   int sweeps;
   double band[2 * kMaxR + 1];
 };

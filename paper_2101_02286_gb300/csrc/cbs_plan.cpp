@@ -128,7 +128,7 @@ bool inv(const Blk& x, Blk& out, double scale = 0.0) {
 }  // namespace
 
 std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool cyclic,
-                              bool* singular, int max_lanes) {
+                              bool* singular, int max_lanes, const int* sizes) {
   *singular = false;
   const int r = A.r;
   T = LineTables();
@@ -137,10 +137,20 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
   T.p = p;
   T.cyclic = cyclic;
   if (p < 1 || p > max_lanes) return "segments out of range";
-  T.rows_small = n / p;
-  T.count_big = n % p;
-  T.rows_big = T.rows_small + (T.count_big ? 1 : 0);
-  if (T.count_big == 0) T.count_big = p;  // all partitions equal
+  if (sizes) {
+    T.count_big = sizes[0];
+    T.rows_big = sizes[1];
+    T.rows_small = sizes[2];
+    if (T.count_big < 1 || T.count_big > p || T.rows_small > T.rows_big ||
+        (int64_t)T.count_big * T.rows_big + (int64_t)(p - T.count_big) * T.rows_small != n)
+      return "inconsistent partition sizes";
+    if (T.count_big == p) T.rows_small = T.rows_big;
+  } else {
+    T.rows_small = n / p;
+    T.count_big = n % p;
+    T.rows_big = T.rows_small + (T.count_big ? 1 : 0);
+    if (T.count_big == 0) T.count_big = p;  // all partitions equal
+  }
   if (T.rows_small < 2 * r) return "partitions need at least 2r rows (n >= 2 r p)";
   T.start.resize(p);
   T.size.resize(p);

@@ -36,10 +36,12 @@ struct cbs_plan {
   bool var = false;
   VarArgs vargs;
   // long lines (kind 1): segments across CTAs
-  LineTables inner;
-  DevLineTables dev_inner;
+  LineTables inner, inner_small;      // segment-level tables (the second for msmall-row segments)
+  DevLineTables dev_inner, dev_inner_small;
+  bool inner_full = false;            // every segment's bulk is a whole number of 16-row partitions
   LongArgs largs;
   void* lbuf = nullptr;
+  void* lbuf_small = nullptr;
   void* sbuf = nullptr;
   int inner_threads = 0;
 };
@@ -49,6 +51,9 @@ namespace cbs {
 // launch count of the last solve; return `s`.
 cbs_status set_error(cbs_status s, const std::string& msg);
 void set_launch_count(int n);
+// inner_small: tables of the msmall-row segments (whole-16-row layout), or
+// null when every segment uses `inner`.
 cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
-                        const DevLineTables& inner, cudaStream_t s, int* launches);
+                        const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
+                        int* launches);
 }  // namespace cbs

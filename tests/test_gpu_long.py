@@ -66,3 +66,20 @@ def test_long_full_workload_sampled(cuda):
     for l in (0, 17, 31):
         ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d[l:l + 1].astype(np.float64))
         assert oracle.rel_err(x[0, l].cpu().numpy(), ref[0]) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol,sweeps,r_lhs", [("fp32_refine", 1e-12, 2, W.PENTA10["lhs"]),
+                                                         ("fp64", 1e-12, 1, W.PENTA10["lhs"]),
+                                                         ("fp32", 2e-5, 1, W.LELE6_TRI["lhs"])])
+def test_long_two_segment_sizes(cuda, precision, tol, sweeps, r_lhs):
+    # p segments of 2^16 rows that do not divide n; with n - p r a multiple of 16
+    # the segments get 16 K + r or 16 (K - 1) + r rows (whole 16-row inner
+    # partitions), both sizes present
+    r = len(r_lhs)
+    n, p = 1 << 16, (24 if r == 2 else 48)  # n - p r divisible by 16, n by neither p
+    d = np.random.default_rng(31).standard_normal((2, n)).astype(np.float32)
+    x, info = _solve(d, r_lhs, p, precision=precision, sweeps=sweeps)
+    assert info["kernel"] == 1 and info["segments"] == p
+    assert info["rows_big"] - info["rows_small"] == 16 and (info["rows_big"] - r) % 16 == 0
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, r_lhs), d.astype(np.float64))
+    assert oracle.rel_err(x, ref) < tol

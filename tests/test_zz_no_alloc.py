@@ -29,9 +29,10 @@ def test_noalloc_matches_solve_twice(cuda):
         d = rng.standard_normal((1, lines, n)).astype(np.float32)
         x = torch.from_numpy(d).cuda()
         ref = plan.solve(x)
+        solve_launches = abi.cbs_last_launch_count()  # 3, or 4 with two segment sizes
         out = torch.full_like(ref, float("nan"))
         abi.cbs_solve_noalloc(plan.handle, x.data_ptr(), out.data_ptr(), 0)
-        assert abi.cbs_last_launch_count() == 3
+        assert abi.cbs_last_launch_count() == solve_launches >= 3
         torch.cuda.synchronize()
         got, want = out.cpu().numpy(), ref.cpu().numpy()
         assert np.isfinite(got).all()
