@@ -25,6 +25,7 @@ cudaError_t launch_band_grad(bool f64, const void* lam, const void* x, void* ga,
 struct BatchProblem;
 int batch_variant_host(int R, int KS, int M, int MODE);
 cudaError_t batch_configure(size_t smem);
+size_t batch_smem(size_t tile_bytes);
 cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitems, const void* const* ins,
                          void* const* outs, int count, int grid, size_t smem, cudaStream_t s);
 size_t batch_problem_bytes();
@@ -849,6 +850,7 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   for (size_t q = 0; q < order.size(); q++) sorted[q] = items[order[q]];
   B->nitems = (int)sorted.size();
   B->count = count;
+  B->smem = batch_smem(B->smem);  // + the current problem's tables
   cudaError_t e = batch_configure(B->smem);
   if (e == cudaSuccess) e = cudaMalloc(&B->dprobs, probs.size());
   if (e == cudaSuccess) e = cudaMalloc(&B->ditems, sorted.size() * sizeof(int4));

@@ -13,7 +13,7 @@
 
 namespace cbs {
 
-struct BatchProblem {
+struct alignas(16) BatchProblem {
   LineArgs args;
   DevLineTables tab;
   int variant;
@@ -42,14 +42,29 @@ __host__ __device__ constexpr int batch_variant(int R, int KS, int M, int MODE) 
 #define CBS_BV(R, KS, M, MODE)                                                                   \
   case batch_variant(R, KS, M, MODE):                                                            \
     line_tile<R, M, MODE, KS, double, double>(P.args, P.tab, bp.in[w.x], bp.out[w.x], w.y, w.z, \
-                                              smem_raw);                                         \
+                                              tile_smem);                                        \
     break;
+
+// Shared memory: the current problem's BatchProblem (its tables are read by
+// every row operation, so they live on chip instead of in global memory),
+// then the tile.
+static_assert(sizeof(BatchProblem) % sizeof(int4) == 0, "copied in 16-byte units");
+constexpr size_t kBatchProblemBytes = (sizeof(BatchProblem) + 127) / 128 * 128;
 
 __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ BatchParams bp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  BatchProblem& P = *reinterpret_cast<BatchProblem*>(smem_raw);
+  unsigned char* tile_smem = smem_raw + kBatchProblemBytes;
+  int loaded = -1;
   for (int it = blockIdx.x; it < bp.nitems; it += gridDim.x) {
     const int4 w = bp.items[it];
-    const BatchProblem& P = bp.probs[w.x];
+    if (w.x != loaded) {  // uniform over the CTA
+      const int4* src = reinterpret_cast<const int4*>(bp.probs + w.x);
+      int4* dst = reinterpret_cast<int4*>(smem_raw);
+      for (int k = threadIdx.x; k < (int)(sizeof(BatchProblem) / sizeof(int4)); k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      loaded = w.x;
+    }
     switch (P.variant) {
       CBS_BV(1, 2, 8, kModeF64)
       CBS_BV(1, 2, 8, kModeRefine)
@@ -76,6 +91,8 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
 #undef CBS_BV
 
 int batch_variant_host(int R, int KS, int M, int MODE) { return batch_variant(R, KS, M, MODE); }
+
+size_t batch_smem(size_t tile_bytes) { return kBatchProblemBytes + tile_bytes; }
 
 cudaError_t batch_configure(size_t smem) {
   static size_t configured = 0;
