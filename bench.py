@@ -487,6 +487,7 @@ def main():
                               "segments": [p.info()["segments"] for p in plans[args.precision]]}))
         return
     plans["fp64"] = make("fp64")
+    plans["fp32_refine_i64"] = make("fp32_refine_i64")
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -522,6 +523,7 @@ def main():
         time.sleep(0.3)
         ms_ref, dir_ref = timed(plans["fp32_refine"], args.steps, max(args.warmup, 3), "headline")
         ms_64, dir_64 = timed(plans["fp64"], max(3, args.steps // 2), 3, "fp64_path")
+        ms_i64, dir_i64 = timed(plans["fp32_refine_i64"], max(3, args.steps // 2), 3, "refine_fp64_interface")
         for _ in range(max(1, int(0.3 / max(ms_ref * 1e-3, 1e-4)))):  # keep the GPU busy while sampling
             step(plans["fp32_refine"])
         barrier()
@@ -531,7 +533,7 @@ def main():
     if rank == 0:
         import oracle
         rng = np.random.default_rng(7)
-        for prec in ("fp32_refine", "fp64"):
+        for prec in ("fp32_refine", "fp64", "fp32_refine_i64"):
             step(plans[prec])
             torch.cuda.synchronize(dev)
             e = 0.0
@@ -636,6 +638,11 @@ def main():
             "roofline_x": {"bound": "hbm", "achieved": achieved_x, "peak": hbm, "unit": "GB/s",
                            "frac": achieved_x / hbm, "kernel": "line_kernel_pipe refine, 16-byte prefetch (x lines)",
                            "ms_per_launch": dir_ref[0]},
+            "refine_fp64_interface": {"value": job_throughput(units, world, ms_i64), "unit": "Gunknowns/s",
+                                      "ms_per_step": ms_i64, "ms_per_direction": dir_i64,
+                                      "max_rel_err": err.get("fp32_refine_i64"),
+                                      "note": "same refinement with the interface system of each FP32 "
+                                              "solve in FP64"},
             "fp64_path": {"value": job_throughput(units, world, ms_64), "unit": "Gunknowns/s",
                           "ms_per_step": ms_64, "ms_per_direction": dir_64, "max_rel_err": err.get("fp64"),
                           "segments": [p.info()["segments"] for p in plans["fp64"]],

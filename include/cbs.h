@@ -56,13 +56,20 @@ enum {
     CBS_ERR_NO_MEMORY = 6    /* host or device allocation failed              */
 };
 
-/* Arithmetic of the bulk solve.  The interface system is FP64 in all modes. */
+/* Arithmetic of the solve. */
 enum {
     CBS_FP64 = 0,        /* everything in FP64                                    */
-    CBS_FP32 = 1,        /* bulk in FP32, no refinement (error ~ cond * 2^-24)    */
-    CBS_FP32_REFINE = 2  /* FP32 bulk + `refine_sweeps` iterative-refinement
+    CBS_FP32 = 1,        /* FP32 (interface system included), no refinement
+                            (error ~ cond * 2^-24)                                */
+    CBS_FP32_REFINE = 2, /* FP32 solves + `refine_sweeps` iterative-refinement
                             sweeps whose residual b - A x is evaluated to FP64
-                            accuracy; output FP64                                 */
+                            accuracy; output FP64.  The interface system of each
+                            FP32 solve is FP32 too: the refinement, not the
+                            correction solve, carries the accuracy             */
+    CBS_FP32_REFINE_I64 = 3 /* as CBS_FP32_REFINE, with the interface system of
+                            every FP32 solve in FP64 (slower, same accuracy;
+                            on-chip and long-line plans, not batches or
+                            variable bands)                                      */
 };
 
 /* Element type of the caller's arrays. */
@@ -100,8 +107,8 @@ typedef struct cbs_desc {
     double  h;              /* grid spacing (> 0)                                  */
     /* solver */
     int32_t segments;       /* p partitions per line; 0 = choose automatically     */
-    int32_t precision;      /* CBS_FP64 / CBS_FP32 / CBS_FP32_REFINE               */
-    int32_t refine_sweeps;  /* CBS_FP32_REFINE: 1 or 2                              */
+    int32_t precision;      /* CBS_FP64 / CBS_FP32 / CBS_FP32_REFINE(_I64)         */
+    int32_t refine_sweeps;  /* refinement modes: 1 or 2                             */
     int32_t in_dtype;       /* CBS_DTYPE_* of the input (f or b)                   */
     int32_t out_dtype;      /* CBS_DTYPE_* of the output x (F64 for FP32_REFINE)   */
 } cbs_desc;

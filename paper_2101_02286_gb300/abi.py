@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libcbs.so")
 # status codes (cbs.h)
 CBS_OK, CBS_ERR_INVALID_ARG, CBS_ERR_UNSUPPORTED, CBS_ERR_SINGULAR, CBS_ERR_TIMEOUT, CBS_ERR_CUDA, \
     CBS_ERR_NO_MEMORY = range(7)
-CBS_FP64, CBS_FP32, CBS_FP32_REFINE = 0, 1, 2
+CBS_FP64, CBS_FP32, CBS_FP32_REFINE, CBS_FP32_REFINE_I64 = 0, 1, 2, 3
 CBS_DTYPE_F64, CBS_DTYPE_F32 = 0, 1
 CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE = 0, 1
 CBS_RHS_NONE, CBS_RHS_CENTRAL = 0, 1

@@ -23,7 +23,7 @@ cudaError_t launch_var(int M, int KS, bool adj, bool f64, const VarArgs& a, cons
 cudaError_t launch_band_grad(bool f64, const void* lam, const void* x, void* ga, int64_t nx, int64_t ny,
                              int64_t nz, int dir, cudaStream_t s);
 struct BatchProblem;
-int batch_variant_host(int R, int KS, int M, int MODE);
+int batch_variant_host(int R, int KS, int M, int MODE, bool full);
 cudaError_t batch_configure(size_t smem);
 size_t batch_smem(size_t tile_bytes);
 cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitems, const void* const* ins,
@@ -73,6 +73,14 @@ int next_pow2(int p) {
 
 namespace {
 
+bool is_refine(int precision) { return precision == CBS_FP32_REFINE || precision == CBS_FP32_REFINE_I64; }
+int mode_of(int precision) {
+  return precision == CBS_FP64 ? kModeF64
+         : precision == CBS_FP32 ? kModeF32
+         : precision == CBS_FP32_REFINE ? kModeRefine
+                                        : kModeRefineI64;
+}
+
 cbs_status validate(const cbs_desc* d) {
   if (!d) return fail(CBS_ERR_INVALID_ARG, "null descriptor");
   for (int k = 0; k < 3; k++)
@@ -88,8 +96,8 @@ cbs_status validate(const cbs_desc* d) {
     if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(CBS_ERR_INVALID_ARG, "h must be positive");
     if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the central stencil is periodic: needs cyclic = 1");
   }
-  if (d->precision < CBS_FP64 || d->precision > CBS_FP32_REFINE) return fail(CBS_ERR_INVALID_ARG, "bad precision");
-  if (d->precision == CBS_FP32_REFINE && (d->refine_sweeps < 1 || d->refine_sweeps > 2))
+  if (d->precision < CBS_FP64 || d->precision > CBS_FP32_REFINE_I64) return fail(CBS_ERR_INVALID_ARG, "bad precision");
+  if (is_refine(d->precision) && (d->refine_sweeps < 1 || d->refine_sweeps > 2))
     return fail(CBS_ERR_INVALID_ARG, "refine_sweeps must be 1 or 2");
   if (d->in_dtype != CBS_DTYPE_F64 && d->in_dtype != CBS_DTYPE_F32) return fail(CBS_ERR_INVALID_ARG, "bad in_dtype");
   if (d->out_dtype != CBS_DTYPE_F64 && d->out_dtype != CBS_DTYPE_F32) return fail(CBS_ERR_INVALID_ARG, "bad out_dtype");
@@ -108,7 +116,7 @@ cbs_status validate(const cbs_desc* d) {
     if (d->bandwidth != 3) return fail(CBS_ERR_UNSUPPORTED, "variable bands: tridiagonal only");
     if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "variable bands: cyclic only");
     if (!d->bands) return fail(CBS_ERR_INVALID_ARG, "variable bands need the alpha field pointer");
-    if (d->precision == CBS_FP32_REFINE) return fail(CBS_ERR_UNSUPPORTED, "variable bands: FP64 or FP32");
+    if (is_refine(d->precision)) return fail(CBS_ERR_UNSUPPORTED, "variable bands: FP64 or FP32");
     const int want = d->precision == CBS_FP64 ? CBS_DTYPE_F64 : CBS_DTYPE_F32;
     if (d->in_dtype != want || d->out_dtype != want)
       return fail(CBS_ERR_INVALID_ARG, "variable bands: input, output and alpha share the precision's dtype");
@@ -119,7 +127,10 @@ cbs_status validate(const cbs_desc* d) {
 // Default partition count for the on-chip kernel: the fewest partitions
 // (<= 32 lanes) whose size fits the register budget of the mode.
 int default_segments(int n, int r, int precision) {
-  const int target = (precision == CBS_FP32_REFINE) ? 16 : 16;
+  const int target = 16;
+  (void)precision;
+  // whole 16-row partitions (compile-time partition sizes in the kernels)
+  if (n % 16 == 0 && n / 16 <= kMaxLanes && 16 >= 2 * r) return n / 16;
   for (int p = 1; p <= kMaxLanes; p *= 2)
     if ((n + p - 1) / p <= target && n / p >= 2 * r) return p;
   for (int p = kMaxLanes; p >= 1; p /= 2)
@@ -504,7 +515,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
     }
   }
   {
-    const int maxM0 = (d->precision == CBS_FP32_REFINE || P->var) ? 16 : 32;
+    const int maxM0 = (is_refine(d->precision) || P->var) ? 16 : 32;
     // a line whose partitions do not fit one lane's registers goes to the
     // segment-per-CTA path
     const bool use_long = !P->var && (d->segments > kMaxLanes || p < 1 || (P->n + p - 1) / p > maxM0);
@@ -548,7 +559,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
     return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
   }
   const LineTables& T = P->host;
-  const int maxM = (d->precision == CBS_FP32_REFINE || P->var) ? 16 : 32;
+  const int maxM = (is_refine(d->precision) || P->var) ? 16 : 32;
   int M = 8;
   while (M < T.rows_big) M *= 2;
   if (M > maxM || T.nmax > kMaxBulk) {
@@ -677,7 +688,7 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     g_launches = 1;
     return CBS_OK;
   }
-  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  const int mode = mode_of(d.precision);
   if (P->kind == 1) {
     LongArgs la = P->largs;
     la.in = in;
@@ -699,7 +710,8 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
 #define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, P->ks, d.in_dtype, d.out_dtype, a, P->dev, s)
   if (mode == kModeF64) e = (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
   else if (mode == kModeF32) e = (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
-  else e = (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+  else if (mode == kModeRefine) e = (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+  else e = (R == 1) ? CBS_L(3, 1) : CBS_L(3, 2);
 #undef CBS_L
   if (e == cudaErrorNotSupported) return fail(CBS_ERR_UNSUPPORTED, "no kernel variant for these element types");
   if (e != cudaSuccess) return cuda_fail(e, "line kernel launch");
@@ -734,14 +746,15 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
   if (d.in_dtype != d.out_dtype) return fail(CBS_ERR_UNSUPPORTED, "transpose needs in_dtype == out_dtype");
   if (!d.cyclic) return fail(CBS_ERR_UNSUPPORTED, "transpose of acyclic plans");
   if (grad_bands) return fail(CBS_ERR_INVALID_ARG, "Toeplitz plans have no band field");
-  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  const int mode = mode_of(d.precision);
   const int R = P->r;
   int launches = 0;
   auto run = [&](const LineArgs& a, int ks) -> cudaError_t {
 #define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, d.out_dtype, d.in_dtype, a, P->dev, s)
     if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
     if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
-    return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+    if (mode == kModeRefine) return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+    return (R == 1) ? CBS_L(3, 1) : CBS_L(3, 2);
 #undef CBS_L
   };
   if (lambda) {
@@ -825,7 +838,9 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": lines too long for one warp");
     }
     const int mode = d.precision == CBS_FP64 ? kModeF64 : kModeRefine;
-    const int variant = batch_variant_host(P->r, P->ks, P->M, mode);
+    const bool full = P->dev.count_big == P->dev.p && P->dev.rows_big == 16 && P->M == 16;
+    int variant = full ? batch_variant_host(P->r, P->ks, P->M, mode, true) : -1;
+    if (variant < 0) variant = batch_variant_host(P->r, P->ks, P->M, mode, false);
     if (variant < 0) {
       cbs_batch_destroy(B);
       return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": tile variant not compiled");

@@ -30,19 +30,25 @@ struct BatchParams {
 };
 
 // The tile variants compiled into the persistent kernel: (R, KS) in
-// {(1,2), (2,3), (1,0), (2,0)} x M in {8, 16} x {FP64, FP32 + refinement};
-// FP64 input and output.
-__host__ __device__ constexpr int batch_variant(int R, int KS, int M, int MODE) {
+// {(1,2), (2,3), (1,0), (2,0)} x M in {8, 16} x {FP64, FP32 + refinement},
+// plus whole-size 16-row partitions (FULL: compile-time sizes) of the same
+// (R, KS, mode); FP64 input and output.
+__host__ __device__ constexpr int batch_variant(int R, int KS, int M, int MODE, bool FULL = false) {
   const int rk = (R == 1 && KS == 2) ? 0 : (R == 2 && KS == 3) ? 1 : (R == 1 && KS == 0) ? 2 : (R == 2 && KS == 0) ? 3 : -1;
-  const int mi = (M == 8) ? 0 : (M == 16) ? 1 : -1;
+  const int mi = FULL ? (M == 16 ? 2 : -1) : (M == 8) ? 0 : (M == 16) ? 1 : -1;
   const int mo = (MODE == kModeF64) ? 0 : (MODE == kModeRefine) ? 1 : -1;
-  return (rk < 0 || mi < 0 || mo < 0) ? -1 : (rk * 2 + mi) * 2 + mo;
+  return (rk < 0 || mi < 0 || mo < 0) ? -1 : (rk * 3 + mi) * 2 + mo;
 }
 
 #define CBS_BV(R, KS, M, MODE)                                                                   \
   case batch_variant(R, KS, M, MODE):                                                            \
     line_tile<R, M, MODE, KS, double, double>(P.args, P.tab, bp.in[w.x], bp.out[w.x], w.y, w.z, \
                                               tile_smem);                                        \
+    break;
+#define CBS_BVF(R, KS, MODE)                                                                               \
+  case batch_variant(R, KS, 16, MODE, true):                                                               \
+    line_tile<R, 16, MODE, KS, double, double, true>(P.args, P.tab, bp.in[w.x], bp.out[w.x], w.y, w.z,   \
+                                                     tile_smem);                                           \
     break;
 
 // Shared memory: the current problem's BatchProblem (its tables are read by
@@ -82,6 +88,14 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
       CBS_BV(2, 0, 8, kModeRefine)
       CBS_BV(2, 0, 16, kModeF64)
       CBS_BV(2, 0, 16, kModeRefine)
+      CBS_BVF(1, 2, kModeF64)
+      CBS_BVF(1, 2, kModeRefine)
+      CBS_BVF(2, 3, kModeF64)
+      CBS_BVF(2, 3, kModeRefine)
+      CBS_BVF(1, 0, kModeF64)
+      CBS_BVF(1, 0, kModeRefine)
+      CBS_BVF(2, 0, kModeF64)
+      CBS_BVF(2, 0, kModeRefine)
       default:
         break;
     }
@@ -89,8 +103,9 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
   }
 }
 #undef CBS_BV
+#undef CBS_BVF
 
-int batch_variant_host(int R, int KS, int M, int MODE) { return batch_variant(R, KS, M, MODE); }
+int batch_variant_host(int R, int KS, int M, int MODE, bool full) { return batch_variant(R, KS, M, MODE, full); }
 
 size_t batch_smem(size_t tile_bytes) { return kBatchProblemBytes + tile_bytes; }
 

@@ -29,7 +29,10 @@ namespace cbs {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-enum Mode { kModeF64 = 0, kModeF32 = 1, kModeRefine = 2 };
+// kModeRefineI64: the refinement with the interface system of every FP32
+// solve in FP64.
+enum Mode { kModeF64 = 0, kModeF32 = 1, kModeRefine = 2, kModeRefineI64 = 3 };
+__host__ __device__ constexpr bool refine_mode(int m) { return m == kModeRefine || m == kModeRefineI64; }
 
 struct LineArgs {
   const void* in;
@@ -38,7 +41,7 @@ struct LineArgs {
   int64_t nlines;
   int dir;
   int K;                 // stencil terms actually used (<= template KS)
-  int sweeps;            // refinement sweeps (kModeRefine)
+  int sweeps;            // refinement sweeps (refinement modes)
   double w[kMaxRhsTerms];              // c_q / (2 q h)
   float wHi[kMaxRhsTerms], wLo[kMaxRhsTerms];
   // the same split weights as pairs for the two-rows-per-instruction
@@ -1058,7 +1061,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   // ---- gather: w[KS + k] = row start + k, w[q] = row start - KS + q, hh[q] = row start + size + q
   // (the refinement mode gathers straight into FP32 pairs below)
   TW w[M + KS], hh[KA];
-  if constexpr (MODE == kModeRefine) {
+  if constexpr (refine_mode(MODE)) {
     if constexpr (LAYOUT == kStaged) {
       tile_copy<true, const TIn, TT>(tr, t, S, (const TIn*)in_ptr);
       __syncthreads();
@@ -1132,7 +1135,8 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
 
   TOut xo[M];
   auto xch = make_xchg<DSTR>(pw, smem_raw, g);
-  if constexpr (MODE != kModeRefine) {
+  using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;  // interface of the FP32 solves
+  if constexpr (!refine_mode(MODE)) {
     T v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
@@ -1384,14 +1388,14 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     float xh[M], v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) v[k] = bh[k];
-    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
+    solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, t, xch);
 #pragma unroll
     for (int k = 0; k < M; k++) xh[k] = v[k];
     // refinement sweep 1: x <- x0 + A^{-1}(b - A x0), residual to FP64 accuracy
     if constexpr (FULL && (M % 2) == 0) residual_sym2<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
     else if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
     else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, xch);
-    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
+    solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, t, xch);
     if (a.sweeps < 2) {
       // x = x0 + delta: the FP64 pipe (idle otherwise on this path) takes the
       // add and delta's conversion, x0 is converted with integer operations
@@ -1413,7 +1417,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       if constexpr (FULL && (M % 2) == 0) residual_sym2<R, M, true>(bh, bl, xh, xl, v, i, t, xch);
       else if constexpr (FULL) residual_sym<R, M, true>(bh, bl, xh, xl, v, i, t, xch);
       else residual_df<R, M, true, FULL>(bh, bl, xh, xl, v, size, i, t, xch);
-      solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, t, xch);
+      solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, t, xch);
 #pragma unroll
       for (int k = 0; k < M; k++) {
         const double xd = f32_to_f64_normal(xh[k]) + f32_to_f64_normal(xl[k] + v[k]);
@@ -1460,7 +1464,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
 }
 
 template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL, int LAYOUT>
-__global__ void __launch_bounds__(256, (MODE == kModeRefine || M == 32) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
+__global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   line_tile<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
 }
@@ -1492,7 +1496,7 @@ __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTa
 // layout only, kCtaXchgSlots 64-bit slots per thread) followed by 2 x
 // (M + 2 KS) slots of TIn per thread.
 template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT>
-__global__ void __launch_bounds__(256, (MODE == kModeRefine || M == 32) ? 2 : 3)
+__global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
     line_kernel_pipe(const LineArgs a, const DevLineTables t, const int gx, const int ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NS = M + 2 * KS;

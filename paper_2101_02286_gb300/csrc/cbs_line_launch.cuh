@@ -1,5 +1,7 @@
 // cbs_line_launch.cuh -- template dispatch for the on-chip line kernel.
 #pragma once
+#include <mutex>
+
 #include "cbs_line.cuh"
 
 namespace cbs {
@@ -68,15 +70,32 @@ cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t 
   const size_t smem = (LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0) +
                       2 * (size_t)NS * threads * sizeof(TIn);
   auto kern = line_kernel_pipe<R, M, MODE, KS, TIn, TOut, LAYOUT>;
-  static int per_sm = 0;  // per instantiation (the shared-memory size only depends on it)
-  if (per_sm == 0) {
+  // per instantiation: the largest dynamic shared memory configured so far
+  // and the occupancy of the last (threads, smem) launched (both depend on
+  // the plan's lanes per line, not only on the instantiation)
+  static std::mutex mu;
+  static size_t attr_smem = 0, occ_smem = 0;
+  static int occ_threads = 0, per_sm = 0;
+  int blocks_per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
     cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (smem > 48 * 1024 && smem > attr_smem) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_smem = smem;
+    }
+    if (occ_smem != smem || occ_threads != threads) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+      if (e != cudaSuccess) return e;
+      occ_smem = smem;
+      occ_threads = threads;
+    }
+    blocks_per_sm = per_sm;
   }
-  const int64_t want = (int64_t)per_sm * sm_count();
+  if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int per_sm_now = blocks_per_sm;
+  const int64_t want = (int64_t)per_sm_now * sm_count();
   const unsigned blocks = (unsigned)(ntiles < want ? ntiles : want);
   kern<<<blocks, threads, smem, s>>>(a, t, (int)grid.x, (int)ntiles);
   return cudaGetLastError();
@@ -94,7 +113,7 @@ cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream
       // the refinement kernel holds 2 CTAs per SM (registers), too few to
       // hide HBM latency without the pipelined prefetch; the FP64 / FP32
       // kernels keep 3 CTAs per SM and load directly
-      if constexpr (MODE == kModeRefine) {
+      if constexpr (refine_mode(MODE)) {
         if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectX>(a, t, s);
         return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectStrided>(a, t, s);
       } else {
@@ -145,7 +164,7 @@ inline cudaError_t launch_line_mode_r(int M, int KS, int tin, int tout, const Li
     case 8: return launch_line_mrm<MODE, R, 8>(KS, tin, tout, a, t, s);
     case 16: return launch_line_mrm<MODE, R, 16>(KS, tin, tout, a, t, s);
     case 32:
-      if constexpr (MODE != kModeRefine) return launch_line_mrm<MODE, R, 32>(KS, tin, tout, a, t, s);
+      if constexpr (!refine_mode(MODE)) return launch_line_mrm<MODE, R, 32>(KS, tin, tout, a, t, s);
       break;
   }
   return cudaErrorNotSupported;

@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
     cF[e] = (lane_ok && i == 0) ? cc[e] : 0.0;
     cL[e] = (lane_ok && i == P - 1) ? cc[R + e] : 0.0;
   }
-  if constexpr (MODE != kModeRefine) {
+  using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;  // interface of the FP32 solves
+  if constexpr (!refine_mode(MODE)) {
     T v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
       bl[k] = d.lo + (s.lo - c.lo);
       v[k] = d.hi;
     }
-    solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, tin, xch);
+    solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, tin, xch);
 #pragma unroll
     for (int k = 0; k < M; k++) {
       xh[k] = v[k];
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
         if (sw == 0) residual_df<R, M, false, false>(bh, bl, xh, xl, v, size, i, tin, xch);
         else residual_df<R, M, true, false>(bh, bl, xh, xl, v, size, i, tin, xch);
       }
-      solve_partition<float, R, M, float, FULL>(v, size, i, lane_ok, tin, xch);
+      solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, tin, xch);
 #pragma unroll
       for (int k = 0; k < M; k++) {
         const f2 s = two_sum(xh[k], v[k]);
@@ -302,6 +303,9 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
     if (mode == kModeRefine) {
       if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }
       else { if (in64) CBS_SEG(kModeRefine, 2, double, double); else CBS_SEG(kModeRefine, 2, float, double); }
+    } else if (mode == kModeRefineI64) {
+      if (R == 1) { if (in64) CBS_SEG(kModeRefineI64, 1, double, double); else CBS_SEG(kModeRefineI64, 1, float, double); }
+      else { if (in64) CBS_SEG(kModeRefineI64, 2, double, double); else CBS_SEG(kModeRefineI64, 2, float, double); }
     } else if (mode == kModeF64) {
       if (R == 1) { if (in64) CBS_SEG(kModeF64, 1, double, double); else CBS_SEG(kModeF64, 1, float, double); }
       else { if (in64) CBS_SEG(kModeF64, 2, double, double); else CBS_SEG(kModeF64, 2, float, double); }
@@ -390,7 +394,10 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
   a.cc = scratch + nseg * 2 * a.r;
   a.xt = scratch + nseg * 4 * a.r;
   const cbs_desc& d = P->desc;
-  const int mode = d.precision == CBS_FP64 ? kModeF64 : (d.precision == CBS_FP32 ? kModeF32 : kModeRefine);
+  const int mode = d.precision == CBS_FP64 ? kModeF64
+                   : d.precision == CBS_FP32 ? kModeF32
+                   : d.precision == CBS_FP32_REFINE ? kModeRefine
+                                                    : kModeRefineI64;
   int launches = 0;
   cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->dev,
                               P->dev_inner, (P->inner_full && a.cbig < a.p) ? &P->dev_inner_small : nullptr,

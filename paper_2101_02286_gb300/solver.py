@@ -9,7 +9,8 @@ import torch
 
 from . import abi
 
-_PREC = {"fp64": abi.CBS_FP64, "fp32": abi.CBS_FP32, "fp32_refine": abi.CBS_FP32_REFINE}
+_PREC = {"fp64": abi.CBS_FP64, "fp32": abi.CBS_FP32, "fp32_refine": abi.CBS_FP32_REFINE,
+         "fp32_refine_i64": abi.CBS_FP32_REFINE_I64}  # refinement, FP64 interface system
 _DT = {torch.float64: abi.CBS_DTYPE_F64, torch.float32: abi.CBS_DTYPE_F32}
 
 

@@ -184,3 +184,26 @@ def test_refine_zeros_and_tiny_values(cuda, direction):
     got, info = gpu_derivative(f, direction, "tri6", precision="fp32_refine", segments=32)
     assert info["rows_big"] == 16
     assert oracle.rel_err(got, oracle_derivative(f, direction, "tri6")) < 1e-12
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+@pytest.mark.parametrize("scheme", ["tri6", "penta10"])
+def test_refine_fp64_interface_mode(cuda, direction, scheme):
+    # refinement whose correction solves keep the interface system in FP64
+    rng = np.random.default_rng(51 + direction)
+    shape = [10, 12, 14]
+    shape[2 - direction] = 256
+    f = rng.uniform(-1, 1, size=tuple(shape))
+    sweeps = 2 if scheme == "penta10" else 1
+    got, _ = gpu_derivative(f, direction, scheme, precision="fp32_refine_i64", sweeps=sweeps)
+    assert oracle.rel_err(got, oracle_derivative(f, direction, scheme)) < 1e-12
+
+
+def test_pipelined_plans_of_different_widths_in_sequence(cuda):
+    # strided y-line plans with 4 and then 32 lanes per line: the second needs
+    # more shared memory than the first configured for the same kernel
+    for n, p in ((48, 3), (512, 32), (48, 3)):
+        f = np.random.default_rng(n).uniform(-1, 1, size=(3, n, 24))
+        got, info = gpu_derivative(f, 1, "tri6", precision="fp32_refine", segments=p)
+        assert info["rows_big"] == 16
+        assert oracle.rel_err(got, oracle_derivative(f, 1, "tri6")) < 1e-12

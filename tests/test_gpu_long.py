@@ -83,3 +83,12 @@ def test_long_two_segment_sizes(cuda, precision, tol, sweeps, r_lhs):
     assert info["rows_big"] - info["rows_small"] == 16 and (info["rows_big"] - r) % 16 == 0
     ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, r_lhs), d.astype(np.float64))
     assert oracle.rel_err(x, ref) < tol
+
+
+def test_long_refine_fp64_interface(cuda):
+    n, p = 1 << 15, 16
+    d = np.random.default_rng(77).standard_normal((2, n)).astype(np.float32)
+    x, info = _solve(d, W.PENTA10["lhs"], p, precision="fp32_refine_i64", sweeps=2)
+    assert info["kernel"] == 1
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d.astype(np.float64))
+    assert oracle.rel_err(x, ref) < 1e-12
