@@ -207,3 +207,45 @@ def test_pipelined_plans_of_different_widths_in_sequence(cuda):
         got, info = gpu_derivative(f, 1, "tri6", precision="fp32_refine", segments=p)
         assert info["rows_big"] == 16
         assert oracle.rel_err(got, oracle_derivative(f, 1, "tri6")) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_identity_lhs_gives_explicit_stencil(cuda, precision):
+    # alpha = 0: A = I, every coupling block vanishes and x = S f exactly the
+    # explicit central difference (a degenerate case of the method)
+    rng = np.random.default_rng(61)
+    f = rng.uniform(-1, 1, size=(4, 6, 256))
+    h = W.grid_spacing(256)
+    plan = Plan(f.shape, 0, lhs=(0.0,), rhs=W.LELE6_TRI["rhs"], h=h, precision=precision)
+    y = plan.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    info = plan.info()
+    plan.close()
+    assert info["message_stages"] == 0
+    ref = oracle.central_rhs(f, W.LELE6_TRI["rhs"], h, axis=-1)
+    assert oracle.rel_err(y, ref) < 1e-12
+
+
+@pytest.mark.slow
+def test_full_512_cube_sampled(cuda):
+    # the 512^3 workload in the launch configuration bench.py times
+    # (32 partitions of 16 rows, pipelined kernels), 64 sampled lines per
+    # direction against the oracle, FP32 + refinement and FP64
+    n = 512
+    f_host, _ = W.noisy_cube(n)
+    f = torch.from_numpy(f_host).cuda()
+    out = torch.empty_like(f)
+    h = W.grid_spacing(n)
+    rng = np.random.default_rng(99)
+    for precision in ("fp32_refine", "fp64"):
+        for d in range(3):
+            plan = Plan(f.shape, d, lhs=W.LELE6_TRI["lhs"], rhs=W.LELE6_TRI["rhs"], h=h, precision=precision,
+                        segments=32)
+            plan.solve(f, out)
+            torch.cuda.synchronize()
+            ax = 2 - d
+            idx = rng.integers(0, n, size=(64, 2))
+            lines = np.moveaxis(f_host, ax, -1)[idx[:, 0], idx[:, 1]]
+            ref = oracle.derivative(lines, W.LELE6_TRI["lhs"], W.LELE6_TRI["rhs"], h)
+            got = np.moveaxis(out.cpu().numpy(), ax, -1)[idx[:, 0], idx[:, 1]]
+            assert oracle.rel_err(got, ref) < 1e-12, (precision, d)
+            plan.close()

@@ -118,3 +118,27 @@ def test_singular_interface_reported():
     with pytest.raises(abi.CbsError) as e:
         abi.cbs_interface_model(d, 4, np.ones(4))
     assert e.value.status == abi.CBS_ERR_SINGULAR
+
+
+def test_plan_create_validates_before_any_device_work():
+    # rejected descriptors never reach the device (no GPU needed)
+    from paper_2101_02286_gb300.solver import Plan
+    cases = [
+        (dict(shape=(0, 4, 64)), abi.CBS_ERR_INVALID_ARG),            # empty field
+        (dict(shape=(4, 4, 64), precision="fp32_refine", sweeps=3), abi.CBS_ERR_INVALID_ARG),
+        (dict(shape=(70000, 2, 64), direction=1), abi.CBS_ERR_UNSUPPORTED),  # y-line grid extent
+        (dict(shape=(4, 4, 64), h=0.0), abi.CBS_ERR_INVALID_ARG),     # stencil spacing
+        (dict(shape=(4, 4, 8), segments=5), abi.CBS_ERR_INVALID_ARG),  # n < 2 r p
+    ]
+    for kw, status in cases:
+        shape = kw.pop("shape")
+        direction = kw.pop("direction", 0)
+        h = kw.pop("h", 0.1)
+        with pytest.raises(abi.CbsError) as e:
+            Plan(shape, direction, lhs=(1 / 3,), rhs=(14 / 9, 1 / 9), h=h, **kw)
+        assert e.value.status == status, (shape, kw)
+    d = make_desc((4, 4, 64), 0, lhs=(1 / 3,))
+    d.precision = 7
+    with pytest.raises(abi.CbsError) as e:
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG
