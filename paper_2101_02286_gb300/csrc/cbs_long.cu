@@ -27,7 +27,7 @@
 #include <mutex>
 #include <string>
 
-#include "cbs_line.cuh"
+#include "cbs_line_launch.cuh"
 #include "cbs_long.cuh"
 #include "cbs_plan_struct.h"
 
@@ -151,12 +151,11 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 // bulk rows (acyclic, tables `tin`).  Segments seg0 + blockIdx.x.  FULL: every
 // inner partition has exactly M rows (whole-16-row layout): sizes are
 // compile-time and the refinement uses the paired residual.
+// One (segment, line) item, solved by the whole CTA.
 template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL>
-__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin, const int seg0) {
-  extern __shared__ __align__(16) unsigned long long xbuf[];  // kCtaXchgSlots * blockDim slots
+__device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables& tin, const int seg,
+                                         const int64_t line, CtaXchg& xch) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
-  const int seg = seg0 + blockIdx.x;
-  const int64_t line = blockIdx.y;
   const int i = threadIdx.x, P = tin.p;
   const bool lane_ok = i < P;
   int start = 0, size = FULL ? M : 2 * R;
@@ -167,7 +166,6 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
   TOut* x = (TOut*)a.out + row0 + R + start;
   const double* xt_here = a.xt + (line * a.p + seg) * R;
   const double* cc = a.cc + (line * a.p + seg) * 2 * R;  // [first R rows | last R rows]
-  CtaXchg xch{xbuf, 0};
   // Eq. 9 couplings to the known interface values, moved to the RHS; only the
   // first partition (bulk rows 0..R-1) and the last (rows size-R..size-1)
   double cF[R], cL[R];
@@ -260,6 +258,13 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
   if (threadIdx.x < R) ((TOut*)a.out)[row0 + threadIdx.x] = (TOut)xt_here[threadIdx.x];
 }
 
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL>
+__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin, const int seg0) {
+  extern __shared__ __align__(16) unsigned long long xbuf[];  // kCtaXchgSlots * blockDim slots
+  CtaXchg xch{xbuf, 0};
+  seg_item<R, M, MODE, TIn, TOut, FULL>(a, tin, seg0 + blockIdx.x, blockIdx.y, xch);
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
@@ -297,7 +302,7 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
     const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
 #define CBS_SEG(MO, RR, TI, TO)                                                                   \
   do {                                                                                            \
-    if (full) long_seg_kernel<RR, 16, MO, TI, TO, true><<<g, threads, smem, s>>>(a, tin, seg0);   \
+    if (full) long_seg_kernel<RR, 16, MO, TI, TO, true><<<g, threads, smem, s>>>(a, tin, seg0);    \
     else long_seg_kernel<RR, 16, MO, TI, TO, false><<<g, threads, smem, s>>>(a, tin, seg0);       \
   } while (0)
     if (mode == kModeRefine) {
@@ -314,7 +319,7 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
       else { if (in64) CBS_SEG(kModeF32, 2, double, float); else CBS_SEG(kModeF32, 2, float, float); }
     }
 #undef CBS_SEG
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*launches;
   }
