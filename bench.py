@@ -11,9 +11,9 @@ error against the FP64 oracle is <= 1e-12; the plain FP64 path is timed on
 the same field and reported beside it.  Inputs (1 GiB) exceed the 129 MB L2,
 so no flush is needed between steps.  The other workloads of the method
 (64^3 Fourier field, 32 long pentadiagonal lines, a ragged batch of 48 grids
-under a CUDA graph, the 256^3 variable-alpha forward and adjoint) are timed
-after it and reported under "other_workloads", each with its error against
-the FP64 oracle.
+under a CUDA graph, 256^3 acyclic systems, the 256^3 variable-alpha forward
+and adjoint) are timed after it and reported under "other_workloads", each
+with its error against the FP64 oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--size N] [--profile] [--no-configs] [--cpu-seconds S]
@@ -333,6 +333,26 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
                       problems=len(items), launches_per_step=abi.cbs_last_launch_count(), sampled_lines=4 * len(items)))
     b.close()
     del ins, outs, items, g
+
+    # acyclic (non-periodic) systems, right-hand side given: 256^3, y lines
+    dac = np.random.default_rng(19).standard_normal((256, 256, 256))
+    di = torch.from_numpy(dac).to(dev)
+    do = torch.empty_like(di)
+    for prec in ("fp32_refine", "fp64"):
+        pl = Plan(dac.shape, 1, lhs=W.LELE6_TRI["lhs"], rhs=None, precision=prec, cyclic=False)
+        ms = time_ms(lambda: pl.solve(di, do, stream), stream, steps)
+        err = None
+        if check:
+            ii = rng.integers(0, 256, size=(32, 2))
+            lines = np.stack([dac[i, :, j] for i, j in ii])
+            ref = oracle.solve_acyclic(oracle.toeplitz_bands(256, W.LELE6_TRI["lhs"]), lines)
+            got = do.cpu().numpy()
+            err = oracle.rel_err(np.stack([got[i, :, j] for i, j in ii]), ref)
+        res.append(_entry("256^3 acyclic tridiagonal (alpha=1/3, no wrap-around), y lines, right-hand side "
+                          "given, %s" % prec, 256 ** 3, ms, 16, hbm, err, segments=pl.info()["segments"],
+                          sampled_lines=32))
+        pl.close()
+    del di, do, dac
 
     # variable alpha: 256^3, forward and adjoint, FP64 and FP32 (x lines)
     f, al = W.variable_alpha_cube(256)

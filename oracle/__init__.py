@@ -16,7 +16,10 @@ What the oracle computes is the plain definition of the method's result:
                        The paper's solver is direct (abstract, Sec. 3), so its
                        exact result is this solution.
 * ``derivative``       x = A^{-1} S f, the compact first derivative (Eq. 1).
-* ``dense_matrix`` / ``dense_solve``  brute force for tiny n (partial pivoting).
+* ``solve_acyclic``    x = B^{-1} d for the non-periodic banded B (Sec. 3,
+                       acyclic case): banded LU without pivoting.
+* ``dense_matrix`` / ``acyclic_dense_matrix`` / ``dense_solve``  brute force
+                       for tiny n (partial pivoting).
 * ``adjoint_variable_tri``  gradients of L = <g, x> for x = A(alpha)^{-1} S f:
                        lambda = A^{-T} g, grad_f = S^T lambda,
                        grad_alpha_i = -lambda_i (x_{i-1} + x_{i+1}).  The paper
@@ -64,6 +67,8 @@ def _load():
         lib.orc_cyclic_tri.restype = ctypes.c_int
         lib.orc_cyclic_banded.argtypes = [dp, L, dp, dp, L, L, ctypes.c_int]
         lib.orc_cyclic_banded.restype = ctypes.c_int
+        lib.orc_acyclic_banded.argtypes = [dp, L, dp, dp, L, L, ctypes.c_int]
+        lib.orc_acyclic_banded.restype = ctypes.c_int
         lib.orc_banded_matvec.argtypes = [dp, L, dp, dp, L, L, ctypes.c_int]
         lib.orc_dense_solve.argtypes = [dp, dp, L]
         lib.orc_dense_solve.restype = ctypes.c_int
@@ -202,6 +207,39 @@ def solve_cyclic(bands, d, axis=-1, method="auto"):
     if rc:
         raise ArithmeticError("zero pivot in the oracle solve")
     return _unlines(x, shape, axis)
+
+
+def solve_acyclic(bands, d, axis=-1):
+    """x = B^{-1} d along `axis` for the acyclic (non-periodic) banded B: the
+    band set of ``toeplitz_bands`` (or per line) without the wrapped corner
+    entries.  Banded LU without pivoting (``cbs_oracle.c``)."""
+    d2, shape = _lines(d, axis)
+    lines, n = d2.shape
+    bands = np.asarray(bands, dtype=np.float64)
+    w = bands.shape[-2]
+    r = (w - 1) // 2
+    if bands.ndim == 2:
+        b2, stride = np.ascontiguousarray(bands), 0
+    else:
+        b2, stride = np.ascontiguousarray(bands.reshape(lines, w, n)), w * n
+    x = np.empty_like(d2)
+    if _load().orc_acyclic_banded(_ptr(b2), stride, _ptr(d2), _ptr(x), lines, n, r):
+        raise ArithmeticError("zero pivot in the oracle solve")
+    return _unlines(x, shape, axis)
+
+
+def acyclic_dense_matrix(bands):
+    """Dense n x n acyclic matrix of one band set (no wrapped corners)."""
+    bands = np.asarray(bands, dtype=np.float64)
+    w, n = bands.shape
+    r = (w - 1) // 2
+    A = np.zeros((n, n))
+    for i in range(n):
+        for k in range(w):
+            j = i + k - r
+            if 0 <= j < n:
+                A[i, j] = bands[k, i]
+    return A
 
 
 def matvec(bands, x, axis=-1):

@@ -345,6 +345,35 @@ int orc_cyclic_banded(const double *bands, long band_line_stride, const double *
 }
 
 /*
+ * Acyclic (non-periodic) banded solve x = B^{-1} d, B the banded matrix
+ * without the wrapped corner entries (Sec. 3, acyclic case): banded LU
+ * without pivoting (B diagonally dominant), forward and backward solve.
+ * Layout as orc_cyclic_banded; entries of `bands` that would wrap are ignored.
+ */
+int orc_acyclic_banded(const double *bands, long band_line_stride, const double *d,
+                       double *x, long lines, long n, int r) {
+    int bad = 0;
+    long l;
+    const long w = 2 * r + 1;
+#pragma omp parallel
+    {
+        double *F = (double *)malloc(sizeof(double) * w * n);
+#pragma omp for schedule(dynamic, 1)
+        for (l = 0; l < lines; l++) {
+            memcpy(F, bands + l * band_line_stride, sizeof(double) * w * n);
+            if (band_lu(F, n, r)) {
+#pragma omp atomic write
+                bad = 1;
+            } else {
+                band_lu_solve(F, n, r, d + l * n, x + l * n);
+            }
+        }
+        free(F);
+    }
+    return bad ? -1 : 0;
+}
+
+/*
  * out = A x for cyclic banded A (half-bandwidth r), used for residuals
  * ||A x - d|| and for building right-hand sides from known solutions.
  */

@@ -1397,11 +1397,14 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, xch);
     solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, t, xch);
     if (a.sweeps < 2) {
-      // x = x0 + delta: the FP64 pipe (idle otherwise on this path) takes the
-      // add and delta's conversion, x0 is converted with integer operations
+      // x = x0 + delta: one FP64 add (the FP64 pipe is idle otherwise on this
+      // path); x0 is widened with integer operations, delta too in the
+      // x-line layout, and by the FP64 pipe in the strided layout, whose
+      // integer work is heavier (measured: each choice is faster where used)
 #pragma unroll
       for (int k = 0; k < M; k++) {
-        const double xd = f32_to_f64_normal(xh[k]) + (double)v[k];
+        const double dv = DSTR ? (double)v[k] : f32_to_f64_normal(v[k]);
+        const double xd = f32_to_f64_normal(xh[k]) + dv;
         if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
         else xo[k] = (TOut)(xh[k] + v[k]);
       }

@@ -249,3 +249,27 @@ def test_full_512_cube_sampled(cuda):
             got = np.moveaxis(out.cpu().numpy(), ax, -1)[idx[:, 0], idx[:, 1]]
             assert oracle.rel_err(got, ref) < 1e-12, (precision, d)
             plan.close()
+
+
+@pytest.mark.parametrize("scheme", ["tri6", "penta10"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("direction,n,p", [(0, 64, 4), (0, 97, 7), (0, 512, 32), (1, 96, 11), (2, 128, 8),
+                                           (0, 250, 31), (1, 48, 3), (2, 16, 1)])
+def test_acyclic_solves(cuda, scheme, precision, tol, direction, n, p):
+    # the acyclic (non-periodic) system of Sec. 3: ceil(log2 p) PCR steps, no
+    # wrapped corners; right-hand side given
+    lhs = SCHEMES[scheme]["lhs"]
+    if n < 2 * len(lhs) * p:
+        pytest.skip("n < 2 r p")
+    shape = [5, 6, 7]
+    shape[2 - direction] = n
+    d = np.random.default_rng(n + p + direction).standard_normal(tuple(shape))
+    sweeps = 2 if (scheme == "penta10" and precision == "fp32_refine") else 1
+    plan = Plan(tuple(shape), direction, lhs=lhs, rhs=None, segments=p, precision=precision, sweeps=sweeps,
+                cyclic=False)
+    x = plan.solve(torch.from_numpy(d).cuda()).double().cpu().numpy()
+    info = plan.info()
+    plan.close()
+    assert info["segments"] == p and info["detach_steps"] == 0
+    ref = oracle.solve_acyclic(oracle.toeplitz_bands(n, lhs), d, axis=2 - direction)
+    assert oracle.rel_err(x, ref) < tol

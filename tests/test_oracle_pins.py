@@ -228,3 +228,38 @@ def test_adjoint_finite_differences():
         fd_a = (loss(f, alpha + e) - loss(f, alpha - e)) / (2 * eps)
         assert abs(fd_f - gf[l, i]) < 1e-7 * max(1.0, abs(gf[l, i]))
         assert abs(fd_a - ga[l, i]) < 1e-7 * max(1.0, abs(ga[l, i]))
+
+
+# ---------------------------------------------------------------- acyclic systems
+@pytest.mark.parametrize("lhs", [(1 / 3,), (0.5, 0.05)])
+@pytest.mark.parametrize("n", [9, 16, 41])
+def test_acyclic_solve_matches_dense_lapack(lhs, n):
+    # Sec. 3 acyclic case: no wrapped corners; brute force by LAPACK
+    rng = np.random.default_rng(n)
+    B = oracle.toeplitz_bands(n, lhs)
+    d = rng.standard_normal((3, n))
+    A = oracle.acyclic_dense_matrix(B)
+    ref = np.linalg.solve(A, d.T).T
+    assert oracle.rel_err(oracle.solve_acyclic(B, d), ref) < 1e-14
+
+
+def test_acyclic_matrix_is_cyclic_without_corners():
+    n = 12
+    for lhs in [(1 / 3,), (0.5, 0.05)]:
+        B = oracle.toeplitz_bands(n, lhs)
+        diff = oracle.dense_matrix(B) - oracle.acyclic_dense_matrix(B)
+        r = len(lhs)
+        nz = np.argwhere(diff != 0)
+        # only entries with |i - j| > n - 1 - r (the wrapped corners) differ
+        assert len(nz) == r * (r + 1)
+        assert all(abs(i - j) >= n - r for i, j in nz)
+
+
+def test_acyclic_solve_per_line_bands_recovers_known_solution():
+    rng = np.random.default_rng(3)
+    lines, n = 4, 30
+    al = rng.uniform(0.2, 0.4, size=(lines, n))
+    bands = oracle.variable_alpha_bands(al)
+    x = rng.standard_normal((lines, n))
+    d = np.stack([oracle.acyclic_dense_matrix(bands[l]) @ x[l] for l in range(lines)])
+    assert oracle.rel_err(oracle.solve_acyclic(bands, d), x) < 1e-13
