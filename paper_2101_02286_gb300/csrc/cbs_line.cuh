@@ -1403,7 +1403,9 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       // integer work is heavier (measured: each choice is faster where used)
 #pragma unroll
       for (int k = 0; k < M; k++) {
-        const double dv = DSTR ? (double)v[k] : f32_to_f64_normal(v[k]);
+        double dv;
+        if constexpr (DSTR) dv = (double)v[k];
+        else dv = f32_to_f64_normal(v[k]);
         const double xd = f32_to_f64_normal(xh[k]) + dv;
         if constexpr (sizeof(TOut) == 8) xo[k] = (TOut)xd;
         else xo[k] = (TOut)(xh[k] + v[k]);
