@@ -11,8 +11,8 @@ error against the FP64 oracle is <= 1e-12; the plain FP64 path is timed on
 the same field and reported beside it.  Inputs (1 GiB) exceed the 129 MB L2,
 so no flush is needed between steps.  The other workloads of the method
 (64^3 Fourier field, 32 long pentadiagonal lines, a ragged batch of 48 grids
-under a CUDA graph, 256^3 acyclic systems, the 256^3 variable-alpha forward
-and adjoint) are timed after it and reported under "other_workloads", each
+under a CUDA graph, 256^2 x-lines of 8192, 256^3 acyclic systems, the 256^3
+variable-alpha forward and adjoint) are timed after it and reported under "other_workloads", each
 with its error against the FP64 oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -333,6 +333,27 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
                       problems=len(items), launches_per_step=abi.cbs_last_launch_count(), sampled_lines=4 * len(items)))
     b.close()
     del ins, outs, items, g
+
+    # the paper's single-GPU workload along x: 256^2 lines of 8192, cyclic
+    # tridiagonal alpha = 1/3, right-hand side given, p = 8 and 7 (2^n - 1)
+    dpx = np.random.default_rng(20).standard_normal((256, 256, 8192))
+    di = torch.from_numpy(dpx).to(dev)
+    do = torch.empty_like(di)
+    for prec, p in (("fp32_refine", 8), ("fp32_refine", 7), ("fp64", 8)):
+        pl = Plan(dpx.shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=None, precision=prec, segments=p)
+        ms = time_ms(lambda: pl.solve(di, do, stream), stream, max(3, steps // 2))
+        err = None
+        if check:
+            ii = rng.integers(0, 256, size=(8, 2))
+            lines = np.stack([dpx[i, j] for i, j in ii])
+            ref = oracle.solve_cyclic(oracle.toeplitz_bands(8192, W.LELE6_TRI["lhs"]), lines)
+            got = do.cpu().numpy()
+            err = oracle.rel_err(np.stack([got[i, j] for i, j in ii]), ref)
+        res.append(_entry("256^2 x-lines of 8192 (the paper's single-GPU workload, x only), cyclic tridiagonal "
+                          "alpha=1/3, right-hand side given, %d segments per line, %s" % (p, prec),
+                          256 * 256 * 8192, ms, 16, hbm, err, segments=p, sampled_lines=8))
+        pl.close()
+    del di, do, dpx
 
     # acyclic (non-periodic) systems, right-hand side given: 256^3, y lines
     dac = np.random.default_rng(19).standard_normal((256, 256, 256))

@@ -142,10 +142,13 @@ typedef struct cbs_plan_info {
  * Lines of up to 32 partitions of at most 32 rows (16 for FP32 + refinement)
  * run one partition per thread of a warp (kernel 0); longer lines run one
  * segment per CTA (kernel 1: x-lines, cyclic Toeplitz bands, right-hand side
- * given, segments of at most 8192 rows).  Kernel 1 accepts p when p divides
- * n (equal segments), or when n - p r is a multiple of 16: the segments then
- * have 16 K + r or 16 (K - 1) + r rows (the larger ones first, as
- * cbs_plan_info reports in rows_big / rows_small / count_big).
+ * given, segments of at most 8192 rows).  Kernel 1 segments: when n - p r
+ * is a multiple of 16 they have 16 K + r or 16 (K - 1) + r rows (whole
+ * 16-row inner partitions); otherwise the first n mod p get ceil(n / p) rows
+ * and the rest floor(n / p) (larger ones first, as cbs_plan_info reports in
+ * rows_big / rows_small / count_big).  Two segment sizes need the truncated
+ * rows of D^-1 to agree (UNSUPPORTED for segments too short for the band's
+ * decay).
  * Errors: INVALID_ARG (n < 2 r p, bad enum, ...), UNSUPPORTED, SINGULAR (a
  * zero or non-finite pivot in D_i or an interface block), CUDA, NO_MEMORY. */
 cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* desc);

@@ -357,28 +357,44 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
       }
     }
   }
-  if (!full) {
-    if (p < 1 || n % p) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments must divide n");
-    sizes[0] = p;
-    sizes[1] = sizes[2] = n / p;
+  if (!full) {  // the first n mod p segments get ceil(n / p) rows, the rest floor
+    if (p < 1 || p > n) return fail(CBS_ERR_INVALID_ARG, "long lines: bad segment count");
+    sizes[0] = n % p ? n % p : p;
+    sizes[1] = (n + p - 1) / p;
+    sizes[2] = n / p;
   }
+  if (p > 65535) return fail(CBS_ERR_UNSUPPORTED, "long lines: at most 65535 segments per line");
   const int m = sizes[1], N = m - r;
   const int pin = full ? N / 16 : (N + 15) / 16;
+  const int Ns = sizes[2] - r, pin_s = full ? Ns / 16 : (Ns + 15) / 16;
   if (pin > 512) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments above 8192 rows (raise segments)");
-  if (N < 2 * r * pin || m < 4 * r) return fail(CBS_ERR_INVALID_ARG, "long lines: segments too short");
+  if (N < 2 * r * pin || Ns < 2 * r * pin_s || sizes[2] < 4 * r)
+    return fail(CBS_ERR_INVALID_ARG, "long lines: segments too short");
   if (!full) {
-    msg = build_line_tables(P->host, n, A, p, true, &singular, 1 << 30);
+    msg = build_line_tables(P->host, n, A, p, true, &singular, 1 << 30, sizes);
     if (msg.empty()) msg = build_line_tables(P->inner, N, A, pin, false, &singular, 1 << 30);
+    if (msg.empty() && sizes[0] < p) msg = build_line_tables(P->inner_small, Ns, A, pin_s, false, &singular, 1 << 30);
     if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
     K = truncated_inverse_rows(P->host, N, r, G);
+    if (sizes[0] < p) {  // the smaller segments must share the truncated rows
+      std::vector<double> G2;
+      const int K2 = truncated_inverse_rows(P->host, Ns, r, G2);
+      double tot = 0.0, diff = 0.0;
+      for (size_t k = 0; k < G.size(); k++) tot += std::fabs(G[k]);
+      bool same = K2 == K && K < Ns;
+      for (size_t k = 0; same && k < G.size(); k++) diff = std::fmax(diff, std::fabs(G[k] - G2[k]));
+      if (!same || diff > std::ldexp(tot, -60))
+        return fail(CBS_ERR_UNSUPPORTED, "long lines: segments too short for this band (choose p dividing n)");
+    }
   }
   cbs_status st = fill_dev_tables(P->dev, P->host, A, d, 0, &P->dbuf, false);
   if (st) return st;
   const int threads = ((pin + 31) / 32) * 32;
   st = fill_dev_tables(P->dev_inner, P->inner, A, d, threads, &P->lbuf, true);
   if (st) return st;
-  if (full && sizes[0] < p) {
-    st = fill_dev_tables(P->dev_inner_small, P->inner_small, A, d, threads, &P->lbuf_small, true);
+  if (sizes[0] < p) {
+    const int threads_s = ((P->inner_small.p + 31) / 32) * 32;
+    st = fill_dev_tables(P->dev_inner_small, P->inner_small, A, d, threads_s, &P->lbuf_small, true);
     if (st) return st;
   }
   P->inner_full = full;
@@ -695,7 +711,7 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     la.out = out;
     int launches = 0;
     cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->dev,
-                                P->dev_inner, (P->inner_full && la.cbig < la.p) ? &P->dev_inner_small : nullptr,
+                                P->dev_inner, la.cbig < la.p ? &P->dev_inner_small : nullptr,
                                 P->inner_full, (cudaStream_t)stream, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "long-line kernel launch");
     g_launches = launches;

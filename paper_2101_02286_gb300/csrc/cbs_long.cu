@@ -2,7 +2,7 @@
 // per segment (the paper's distributed level across thread blocks).
 //
 // A solve is three launches on one stream (four when the segments come in
-// two sizes, see create_long: the segment kernel then runs once per size):
+// two sizes: the segment kernel then runs once per size):
 //   1. ends:  for every segment only the first r and last r rows of
 //             y_i = D_i^{-1} b_i are needed (Sec. 4: only those rows cross
 //             partitions).  They are dot products of the segment's right-hand
@@ -45,8 +45,8 @@ __device__ __forceinline__ int seg_rows(const LongArgs& a, int s) { return s < a
 // ---------------------------------------------------------------- 1. ends
 template <typename TIn>
 __global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a) {
-  const int seg = blockIdx.x;
-  const int64_t line = blockIdx.y;
+  const int seg = blockIdx.y;           // grid (lines, segments): lines may exceed 65535
+  const int64_t line = blockIdx.x;
   const int r = a.r, N = seg_rows(a, seg) - r;
   const TIn* b = (const TIn*)a.in + line * a.n + seg_start(a, seg) + r;  // first bulk row
   double accF[kMaxR], accL[kMaxR];
@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 
 // ---------------------------------------------------------------- 3. segments
 // One CTA per (segment, line); thread i = inner partition i of the segment's
-// bulk rows (acyclic, tables `tin`).  Segments seg0 + blockIdx.x.  FULL: every
+// bulk rows (acyclic, tables `tin`).  Grid (lines, segments): line blockIdx.x,
+// segment seg0 + blockIdx.y.  FULL: every
 // inner partition has exactly M rows (whole-16-row layout): sizes are
 // compile-time and the refinement uses the paired residual.
 // One (segment, line) item, solved by the whole CTA.
@@ -262,7 +263,7 @@ template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL>
 __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin, const int seg0) {
   extern __shared__ __align__(16) unsigned long long xbuf[];  // kCtaXchgSlots * blockDim slots
   CtaXchg xch{xbuf, 0};
-  seg_item<R, M, MODE, TIn, TOut, FULL>(a, tin, seg0 + blockIdx.x, blockIdx.y, xch);
+  seg_item<R, M, MODE, TIn, TOut, FULL>(a, tin, seg0 + blockIdx.y, blockIdx.x, xch);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -270,7 +271,8 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
                         int* launches) {
   *launches = 0;
-  const dim3 gs((unsigned)a.p, (unsigned)a.lines);
+  if (a.p > 65535 || a.lines > 0x7fffffff) return cudaErrorInvalidValue;
+  const dim3 gs((unsigned)a.lines, (unsigned)a.p);
   if (in64) long_ends_kernel<double><<<gs, 128, 0, s>>>(a);
   else long_ends_kernel<float><<<gs, 128, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -291,13 +293,13 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
   if (e != cudaSuccess) return e;
   *launches = 2;
   // segment launches: the first cbig segments with `inner`, the rest with
-  // `inner_small` (whole-16-row layout with two sizes)
+  // `inner_small` (segments of two sizes)
   const int nbig = inner_small ? a.cbig : a.p;
   for (int part = 0; part < (inner_small ? 2 : 1); part++) {
     const DevLineTables& tin = part == 0 ? inner : *inner_small;
     const int seg0 = part == 0 ? 0 : nbig, nseg = part == 0 ? nbig : a.p - nbig;
     if (nseg <= 0) continue;
-    const dim3 g((unsigned)nseg, (unsigned)a.lines);
+    const dim3 g((unsigned)a.lines, (unsigned)nseg);
     const int threads = ((tin.p + 31) / 32) * 32;
     const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
 #define CBS_SEG(MO, RR, TI, TO)                                                                   \
@@ -405,7 +407,7 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
                                                     : kModeRefineI64;
   int launches = 0;
   cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->dev,
-                              P->dev_inner, (P->inner_full && a.cbig < a.p) ? &P->dev_inner_small : nullptr,
+                              P->dev_inner, a.cbig < a.p ? &P->dev_inner_small : nullptr,
                               P->inner_full, (cudaStream_t)stream, &launches);
   if (e != cudaSuccess) return set_error(CBS_ERR_CUDA, std::string("long-line kernel launch: ") + cudaGetErrorString(e));
   set_launch_count(launches);

@@ -92,3 +92,35 @@ def test_long_refine_fp64_interface(cuda):
     assert info["kernel"] == 1
     ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d.astype(np.float64))
     assert oracle.rel_err(x, ref) < 1e-12
+
+
+@pytest.mark.parametrize("p", [3, 7, 31, 63])
+@pytest.mark.parametrize("precision,sweeps", [("fp64", 1), ("fp32_refine", 1)])
+def test_long_lines_2n_minus_1_segments(cuda, p, precision, sweeps):
+    # the paper's 2^n - 1 partition counts on lines of 8192 (detach / reattach
+    # in the segment-level interface system); p does not divide n, so the
+    # segments have ceil(n / p) or floor(n / p) rows
+    n = 8192
+    d = np.random.default_rng(p).standard_normal((3, n))
+    x, info = _solve(d, W.LELE6_TRI["lhs"], p, precision=precision, sweeps=sweeps, in_dtype=torch.float64)
+    assert info["kernel"] == 1 and info["segments"] == p and info["detach_steps"] > 0
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.LELE6_TRI["lhs"]), d)
+    assert oracle.rel_err(x, ref) < 1e-12
+
+
+@pytest.mark.slow
+def test_long_more_lines_than_a_grid_dimension(cuda):
+    # 65540 lines (> 65535, the limit of a CUDA grid's y and z extents)
+    lines, n, p = 65540, 2048, 2
+    d = np.random.default_rng(8).standard_normal((lines, n)).astype(np.float32)
+    plan = Plan((1, lines, n), 0, lhs=W.LELE6_TRI["lhs"], rhs=None, segments=p, precision="fp32_refine",
+                in_dtype=torch.float32)
+    assert plan.info()["kernel"] == 1
+    x = plan.solve(torch.from_numpy(d.reshape(1, lines, n)).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    pick = np.random.default_rng(9).integers(0, lines, size=16)
+    pick[0], pick[1] = 0, lines - 1
+    got = x[0, pick].cpu().numpy()
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.LELE6_TRI["lhs"]), d[pick].astype(np.float64))
+    assert oracle.rel_err(got, ref) < 1e-12
