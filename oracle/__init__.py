@@ -16,6 +16,11 @@ What the oracle computes is the plain definition of the method's result:
                        The paper's solver is direct (abstract, Sec. 3), so its
                        exact result is this solution.
 * ``derivative``       x = A^{-1} S f, the compact first derivative (Eq. 1).
+* ``staggered_rhs`` / ``midpoint_rhs``  the right-hand sides of the staggered
+                       sixth-order derivative and of the compact midpoint
+                       interpolation (Eq. 2, App. A.2), between a grid and the
+                       grid shifted by half a spacing; ``staggered_derivative``
+                       / ``midpoint_interpolation`` solve with them.
 * ``solve_acyclic``    x = B^{-1} d for the non-periodic banded B (Sec. 3,
                        acyclic case): banded LU without pivoting.
 * ``dense_matrix`` / ``acyclic_dense_matrix`` / ``dense_solve``  brute force
@@ -63,6 +68,9 @@ def _load():
         L = ctypes.c_long
         lib.orc_central_rhs.argtypes = [dp, dp, L, L, dp, ctypes.c_int, ctypes.c_double]
         lib.orc_central_rhs_transpose.argtypes = [dp, dp, L, L, dp, ctypes.c_int, ctypes.c_double]
+        lib.orc_staggered_rhs.argtypes = [dp, dp, L, L, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int]
+        lib.orc_staggered_rhs_transpose.argtypes = lib.orc_staggered_rhs.argtypes
         lib.orc_cyclic_tri.argtypes = [dp, L, dp, dp, L, L]
         lib.orc_cyclic_tri.restype = ctypes.c_int
         lib.orc_cyclic_banded.argtypes = [dp, L, dp, dp, L, L, ctypes.c_int]
@@ -114,6 +122,42 @@ def central_rhs_transpose(g, coefs, h, axis=-1):
     out = np.empty_like(g2)
     _load().orc_central_rhs_transpose(_ptr(g2), _ptr(out), g2.shape[0], g2.shape[1], _ptr(c), len(c), float(h))
     return _unlines(out, shape, axis)
+
+
+def _staggered(f, coefs, h, shift, kind, transpose, axis):
+    if shift not in (0, 1):
+        raise ValueError("shift must be 0 or 1")
+    f2, shape = _lines(f, axis)
+    c = np.ascontiguousarray(coefs, dtype=np.float64)
+    out = np.empty_like(f2)
+    fn = _load().orc_staggered_rhs_transpose if transpose else _load().orc_staggered_rhs
+    fn(_ptr(f2), _ptr(out), f2.shape[0], f2.shape[1], _ptr(c), len(c), float(h), int(shift), int(kind))
+    return _unlines(out, shape, axis)
+
+
+def staggered_rhs(f, coefs, h, shift=0, axis=-1):
+    """Staggered derivative RHS (App. A.2, first scheme), periodic:
+    d_i = sum_k coefs[k-1] (f[i+k-1+shift] - f[i-k+shift]) / ((2k-1) h).
+    shift = 0: f[j] sits at x_{j+1/2}, d_i at x_i; shift = 1: f[j] at x_j,
+    d_i at x_{i+1/2}."""
+    return _staggered(f, coefs, h, shift, 0, False, axis)
+
+
+def midpoint_rhs(f, coefs, shift=0, axis=-1):
+    """Compact interpolation RHS (Eq. 2; App. A.2, second scheme), periodic:
+    d_i = sum_k coefs[k-1] (f[i+k-1+shift] + f[i-k+shift]) / 2 (points as in
+    staggered_rhs)."""
+    return _staggered(f, coefs, 1.0, shift, 1, False, axis)
+
+
+def staggered_rhs_transpose(g, coefs, h, shift=0, axis=-1):
+    """S^T g for the stencil of staggered_rhs (scatter form)."""
+    return _staggered(g, coefs, h, shift, 0, True, axis)
+
+
+def midpoint_rhs_transpose(g, coefs, shift=0, axis=-1):
+    """S^T g for the stencil of midpoint_rhs (scatter form)."""
+    return _staggered(g, coefs, 1.0, shift, 1, True, axis)
 
 
 # ---------------------------------------------------------------- matrices
@@ -262,6 +306,18 @@ def derivative(f, lhs, coefs, h, axis=-1):
     """Compact first derivative along `axis`: x = A^{-1} S f (Eq. 1)."""
     n = np.shape(f)[axis]
     return solve_cyclic(toeplitz_bands(n, lhs), central_rhs(f, coefs, h, axis), axis)
+
+
+def staggered_derivative(f, lhs, coefs, h, shift=0, axis=-1):
+    """Staggered compact first derivative: x = A^{-1} S f with S of staggered_rhs."""
+    n = np.shape(f)[axis]
+    return solve_cyclic(toeplitz_bands(n, lhs), staggered_rhs(f, coefs, h, shift, axis), axis)
+
+
+def midpoint_interpolation(f, lhs, coefs, shift=0, axis=-1):
+    """Compact interpolation to the half-shifted grid: x = A^{-1} S f with S of midpoint_rhs."""
+    n = np.shape(f)[axis]
+    return solve_cyclic(toeplitz_bands(n, lhs), midpoint_rhs(f, coefs, shift, axis), axis)
 
 
 def derivative_variable_tri(f, alpha, coefs, h, axis=-1):

@@ -109,6 +109,59 @@ void orc_central_rhs_transpose(const double *g, double *out, long lines, long n,
 }
 
 /*
+ * Right-hand sides of the staggered schemes (App. A.2): the sixth-order
+ * staggered first derivative (kind 0) and the compact midpoint interpolation
+ * of Eq. 2 (kind 1), both between a grid and the grid shifted by half a
+ * spacing.  Input element j holds the field at x_{j+1/2} when shift = 0
+ * (staggered -> nodes) and at x_j when shift = 1 (nodes -> staggered, output
+ * element i at x_{i+1/2}).  Term k couples the two input points at distance
+ * (k - 1/2) h on either side of the output point, i.e. elements
+ * i + k - 1 + shift and i - k + shift:
+ *
+ *   kind 0:  d_i = sum_k coef[k-1] (f_up - f_dn) / ((2k - 1) h)
+ *   kind 1:  d_i = sum_k coef[k-1] (f_up + f_dn) / 2
+ */
+void orc_staggered_rhs(const double *f, double *d, long lines, long n,
+                       const double *coef, int K, double h, int shift, int kind) {
+    long l;
+#pragma omp parallel for schedule(static)
+    for (l = 0; l < lines; l++) {
+        const double *fl = f + l * n;
+        double *dl = d + l * n;
+        for (long i = 0; i < n; i++) {
+            double s = 0.0;
+            for (int k = 1; k <= K; k++) {
+                double up = fl[wrap(i + k - 1 + shift, n)];
+                double dn = fl[wrap(i - k + shift, n)];
+                if (kind == 0) s += coef[k - 1] * (up - dn) / ((2.0 * k - 1.0) * h);
+                else s += coef[k - 1] * (up + dn) / 2.0;
+            }
+            dl[i] = s;
+        }
+    }
+}
+
+/* Transpose of orc_staggered_rhs as the scatter of each row into its columns. */
+void orc_staggered_rhs_transpose(const double *g, double *out, long lines, long n,
+                                 const double *coef, int K, double h, int shift, int kind) {
+    long l;
+#pragma omp parallel for schedule(static)
+    for (l = 0; l < lines; l++) {
+        const double *gl = g + l * n;
+        double *ol = out + l * n;
+        for (long j = 0; j < n; j++) ol[j] = 0.0;
+        for (long i = 0; i < n; i++) {
+            for (int k = 1; k <= K; k++) {
+                double w = (kind == 0) ? coef[k - 1] / ((2.0 * k - 1.0) * h) : coef[k - 1] / 2.0;
+                ol[wrap(i + k - 1 + shift, n)] += w * gl[i];
+                if (kind == 0) ol[wrap(i - k + shift, n)] -= w * gl[i];
+                else ol[wrap(i - k + shift, n)] += w * gl[i];
+            }
+        }
+    }
+}
+
+/*
  * Acyclic tridiagonal solve by Thomas elimination (no pivoting):
  *   a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = d[i],  a[0] and c[n-1] ignored.
  * Returns 0, or -1 on a zero pivot.  tmp holds n doubles.

@@ -13,6 +13,10 @@ Operators (inputs to both sides):
                    10th-order right-hand side a = 17/12, b = 101/150, c = 1/100.
   * CENTRAL4    -- explicit 4th-order central difference (alpha = 0):
                    a = 4/3, b = -1/3 in Lele's form.
+  * STAGGERED6  -- 6th-order staggered first derivative (App. A.2):
+                   alpha = 9/62, a = 63/62, b = 17/62.
+  * MIDPOINT6   -- 6th-order compact midpoint interpolation (Eq. 2, App. A.2):
+                   alpha = 3/10, a = 3/2, b = 1/10.
 """
 from __future__ import annotations
 
@@ -24,6 +28,8 @@ import numpy as np
 LELE6_TRI = {"lhs": (1.0 / 3.0,), "rhs": (14.0 / 9.0, 1.0 / 9.0)}
 PENTA10 = {"lhs": (1.0 / 2.0, 1.0 / 20.0), "rhs": (17.0 / 12.0, 101.0 / 150.0, 1.0 / 100.0)}
 CENTRAL4 = {"rhs": (4.0 / 3.0, -1.0 / 3.0)}
+STAGGERED6 = {"lhs": (9.0 / 62.0,), "rhs": (63.0 / 62.0, 17.0 / 62.0)}
+MIDPOINT6 = {"lhs": (3.0 / 10.0,), "rhs": (3.0 / 2.0, 1.0 / 10.0)}
 
 SEEDS = {"fourier64": 0, "cube512": 1, "penta_long": 2, "ragged_batch": 3, "variable_alpha": 4}
 

@@ -10,7 +10,10 @@ None of these compares the oracle with itself or with the GPU path:
     random cyclic banded systems;
   * FFT diagonalisation of circulant systems (any n);
   * the block-LU identity behind the interface system (Sec. 3, Fig. 4);
-  * finite differences and an explicit-inverse gradient for the adjoint.
+  * finite differences and an explicit-inverse gradient for the adjoint;
+  * the staggered schemes of Eq. 2 / App. A.2: exact Taylor matching, their
+    closed-form response to Fourier modes at half-shifted points, sixth-order
+    convergence, and the dense transpose of their stencils.
 """
 from fractions import Fraction as Fr
 
@@ -263,3 +266,115 @@ def test_acyclic_solve_per_line_bands_recovers_known_solution():
     x = rng.standard_normal((lines, n))
     d = np.stack([oracle.acyclic_dense_matrix(bands[l]) @ x[l] for l in range(lines)])
     assert oracle.rel_err(oracle.solve_acyclic(bands, d), x) < 1e-13
+
+
+# ---------------------------------------------------------------- staggered schemes (Eq. 2, App. A.2)
+def _staggered_order(alpha, coefs, interp, kmax=12):
+    """Largest P such that the staggered scheme (h = 1, output at t = 0, input
+    at the half points +-(q - 1/2)) is exact for every monomial x^k, k <= P:
+      derivative:    sum_t A_t f'(t) = sum_q c_q (f(q-1/2) - f(1/2-q)) / (2q-1)
+      interpolation: sum_t A_t f(t)  = sum_q c_q (f(q-1/2) + f(1/2-q)) / 2."""
+    A = {0: Fr(1), 1: Fr(alpha), -1: Fr(alpha)}
+    order = -1
+    for k in range(0, kmax + 1):
+        if interp:
+            lhs = sum(At * Fr(t) ** k for t, At in A.items())
+        else:
+            lhs = sum(At * (k * Fr(t) ** (k - 1) if k >= 1 else 0) for t, At in A.items())
+        rhs = Fr(0)
+        for q, c in enumerate(coefs, start=1):
+            u, d = Fr(2 * q - 1, 2), -Fr(2 * q - 1, 2)
+            rhs += Fr(c) * ((u ** k + d ** k) / 2 if interp else (u ** k - d ** k) / (2 * q - 1))
+        if lhs != rhs:
+            break
+        order = k
+    return order
+
+
+def test_staggered_scheme_coefficients_orders():
+    f = Fr
+    # App. A.2: both printed schemes are sixth order (the derivative is exact
+    # through x^6, the interpolation through x^5: error terms h^6 in both)
+    assert _staggered_order(f(9, 62), [f(63, 62), f(17, 62)], interp=False) == 6
+    assert _staggered_order(f(3, 10), [f(3, 2), f(1, 10)], interp=True) == 5
+    assert W.STAGGERED6 == {"lhs": (9 / 62,), "rhs": (63 / 62, 17 / 62)}
+    assert W.MIDPOINT6 == {"lhs": (3 / 10,), "rhs": (3 / 2, 1 / 10)}
+    # a perturbed coefficient loses the order
+    assert _staggered_order(f(9, 62), [f(63, 62), f(17, 63)], interp=False) < 6
+    assert _staggered_order(f(3, 10), [f(3, 2), f(1, 11)], interp=True) < 5
+
+
+def _staggered_modes(rng, lines, n, count=6):
+    ks = rng.integers(1, n // 3, size=(lines, count))
+    ph = rng.uniform(0, 2 * np.pi, size=(lines, count))
+    amp = rng.standard_normal((lines, count))
+    return ks, ph, amp
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("n", [16, 48, 97])
+def test_staggered_closed_form_fourier(shift, n):
+    # sum of plane waves sampled at the input points; the scheme's exact
+    # response at the output points (derived from the definitions):
+    #   derivative:    K'(k) = sum_q 2 c_q sin((2q-1) kh/2) / ((2q-1) h) / (1 + 2 alpha cos kh)
+    #   interpolation: T(k)  = sum_q c_q cos((2q-1) kh/2) / (1 + 2 alpha cos kh)
+    rng = np.random.default_rng(11 + n + shift)
+    lines = 5
+    h = W.grid_spacing(n)
+    ks, ph, amp = _staggered_modes(rng, lines, n)
+    j = np.arange(n)
+    x_in = (j + (0.5 if shift == 0 else 0.0)) * h
+    x_out = (j + (0.0 if shift == 0 else 0.5)) * h
+    f = np.zeros((lines, n))
+    want_d = np.zeros((lines, n))
+    want_i = np.zeros((lines, n))
+    (ad,), (cd1, cd2) = W.STAGGERED6["lhs"], W.STAGGERED6["rhs"]
+    (ai,), (ci1, ci2) = W.MIDPOINT6["lhs"], W.MIDPOINT6["rhs"]
+    for l in range(lines):
+        for k, p, a in zip(ks[l], ph[l], amp[l]):
+            th = k * h
+            f[l] += a * np.sin(k * x_in + p)
+            kp = (2 * cd1 * np.sin(th / 2) / h + 2 * cd2 * np.sin(3 * th / 2) / (3 * h)) / (1 + 2 * ad * np.cos(th))
+            tt = (ci1 * np.cos(th / 2) + ci2 * np.cos(3 * th / 2)) / (1 + 2 * ai * np.cos(th))
+            want_d[l] += a * kp * np.cos(k * x_out + p)
+            want_i[l] += a * tt * np.sin(k * x_out + p)
+    got_d = oracle.staggered_derivative(f, W.STAGGERED6["lhs"], W.STAGGERED6["rhs"], h, shift)
+    got_i = oracle.midpoint_interpolation(f, W.MIDPOINT6["lhs"], W.MIDPOINT6["rhs"], shift)
+    assert oracle.rel_err(got_d, want_d) < 1e-13
+    assert oracle.rel_err(got_i, want_i) < 1e-13
+    # the other shift puts the answer half a cell off: the pin tells them apart
+    other = oracle.staggered_derivative(f, W.STAGGERED6["lhs"], W.STAGGERED6["rhs"], h, 1 - shift)
+    assert oracle.rel_err(other, want_d) > 1e-3
+
+
+def test_staggered_sixth_order_convergence():
+    # f = exp(sin x) on [0, 2 pi): the error against the exact derivative /
+    # midpoint values falls by ~2^6 per doubling of n
+    errs_d, errs_i = [], []
+    for n in (16, 32, 64):
+        h = W.grid_spacing(n)
+        xs = (np.arange(n) + 0.5) * h  # staggered input, nodes out (shift 0)
+        xn = np.arange(n) * h
+        f = np.exp(np.sin(xs))[None, :]
+        d = oracle.staggered_derivative(f, W.STAGGERED6["lhs"], W.STAGGERED6["rhs"], h, 0)
+        it = oracle.midpoint_interpolation(f, W.MIDPOINT6["lhs"], W.MIDPOINT6["rhs"], 0)
+        errs_d.append(np.abs(d[0] - np.cos(xn) * np.exp(np.sin(xn))).max())
+        errs_i.append(np.abs(it[0] - np.exp(np.sin(xn))).max())
+    for e in (errs_d, errs_i):
+        assert e[0] / e[1] > 2 ** 5.5 and e[1] / e[2] > 2 ** 5.5
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_staggered_transpose_is_dense_transpose(shift):
+    n, coefs, h = 11, (63 / 62, 17 / 62), 0.3
+    I = np.eye(n)
+    for fwd, tr, neg in ((lambda v, s: oracle.staggered_rhs(v, coefs, h, s),
+                          lambda v, s: oracle.staggered_rhs_transpose(v, coefs, h, s), -1.0),
+                         (lambda v, s: oracle.midpoint_rhs(v, coefs, s),
+                          lambda v, s: oracle.midpoint_rhs_transpose(v, coefs, s), 1.0)):
+        S = np.stack([fwd(I[j], shift) for j in range(n)], axis=1)
+        ST = np.stack([tr(I[j], shift) for j in range(n)], axis=1)
+        assert np.allclose(ST, S.T, atol=1e-14)
+        # S^T is the other shift's stencil, negated for the derivative
+        S_other = np.stack([fwd(I[j], 1 - shift) for j in range(n)], axis=1)
+        assert np.allclose(ST, neg * S_other, atol=1e-14)
