@@ -252,8 +252,8 @@ def _entry(workload, unknowns, ms, bytes_per_unknown, hbm, err, **extra):
 
 
 def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
-    """The four other workloads of the method, each timed on `stream` and
-    checked against the FP64 oracle (whole output or sampled lines)."""
+    """The other workloads of the method, each timed on `stream` and checked
+    against the FP64 oracle (whole output or sampled lines)."""
     import numpy as np
     import torch
     from paper_2101_02286_gb300 import abi
@@ -374,6 +374,42 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
                           sampled_lines=32))
         pl.close()
     del di, do, dac
+
+    # staggered schemes of the paper's Taylor-Green runs (App. A.2): 256^3,
+    # sixth-order derivative from the nodes to the half points and compact
+    # interpolation from the half points to the nodes, along x, y and z
+    fs = np.random.default_rng(22).standard_normal((256, 256, 256))
+    fi = torch.from_numpy(fs).to(dev)
+    outs = [torch.empty_like(fi) for _ in range(3)]
+    hs = W.grid_spacing(256)
+    for kind, shift, sch in (("staggered", 1, W.STAGGERED6), ("midpoint", 0, W.MIDPOINT6)):
+        for prec in ("fp32_refine", "fp64"):
+            pls = [Plan(fs.shape, dd, lhs=sch["lhs"], rhs=sch["rhs"], h=hs, precision=prec, stencil=kind,
+                        shift=shift) for dd in range(3)]
+
+            def step():
+                for dd in range(3):
+                    pls[dd].solve(fi, outs[dd], stream)
+            ms = time_ms(step, stream, steps)
+            err = None
+            if check:
+                err = 0.0
+                for dd in range(3):
+                    ax = 2 - dd
+                    fl = np.moveaxis(fs, ax, -1)
+                    ii = rng.integers(0, 256, size=(8, 2))
+                    lines = np.stack([fl[i, j] for i, j in ii])
+                    ref = (oracle.staggered_derivative(lines, sch["lhs"], sch["rhs"], hs, shift) if kind == "staggered"
+                           else oracle.midpoint_interpolation(lines, sch["lhs"], sch["rhs"], shift))
+                    yl = np.moveaxis(outs[dd].cpu().numpy(), ax, -1)
+                    err = max(err, oracle.rel_err(np.stack([yl[i, j] for i, j in ii]), ref))
+            what = ("staggered 6th-order derivative (alpha=9/62), nodes -> half points" if kind == "staggered"
+                    else "compact 6th-order interpolation (alpha=3/10), half points -> nodes")
+            res.append(_entry("256^3 %s, x/y/z (3 launches), %s" % (what, prec), 3 * 256 ** 3, ms, 16, hbm, err,
+                              segments=pls[0].info()["segments"], sampled_lines=24))
+            for pl in pls:
+                pl.close()
+    del fi, outs, fs
 
     # variable alpha: 256^3, forward and adjoint, FP64 and FP32 (x lines)
     f, al = W.variable_alpha_cube(256)

@@ -82,10 +82,20 @@ enum {
                                 A[i,i-1] = A[i,i+1] = alpha_i, A[i,i] = 1            */
 };
 
-/* Right-hand side. */
+/* Right-hand side.  The staggered kinds (App. A.2; Eq. 2) map a field on one
+ * grid to the grid shifted by half a spacing, selected by cbs_desc.rhs_shift
+ * = s: with s = 0 input element j holds f at x_{j+1/2} and output element i
+ * is at x_i; with s = 1 input element j holds f at x_j and output element i
+ * is at x_{i+1/2}.  Term k couples input elements i+k-1+s and i-k+s. */
 enum {
     CBS_RHS_NONE = 0,        /* the input array already holds b                       */
-    CBS_RHS_CENTRAL = 1      /* b_i = sum_k c_k (f_{i+k} - f_{i-k}) / (2 k h), Eq. 1 */
+    CBS_RHS_CENTRAL = 1,     /* b_i = sum_k c_k (f_{i+k} - f_{i-k}) / (2 k h), Eq. 1 */
+    CBS_RHS_STAGGERED = 2,   /* b_i = sum_k c_k (f_{i+k-1+s} - f_{i-k+s}) / ((2k-1) h):
+                                the staggered first derivative (App. A.2: alpha =
+                                9/62, c = 63/62, 17/62)                              */
+    CBS_RHS_MIDPOINT = 3     /* b_i = sum_k c_k (f_{i+k-1+s} + f_{i-k+s}) / 2: the
+                                compact interpolation of Eq. 2 (App. A.2: alpha =
+                                3/10, c = 3/2, 1/10); h is not used                */
 };
 
 typedef struct cbs_desc {
@@ -102,7 +112,8 @@ typedef struct cbs_desc {
                                caller keeps it alive and may change its values)    */
     /* right-hand side */
     int32_t rhs_kind;       /* CBS_RHS_*                                            */
-    int32_t rhs_terms;      /* K = 1..3 stencil terms (CBS_RHS_CENTRAL)            */
+    int32_t rhs_terms;      /* K = 1..3 stencil terms (CBS_RHS_CENTRAL); 1..2 for
+                               the staggered kinds                                 */
     double  rhs_coef[3];    /* c_1..c_K (Lele's a, b, c)                           */
     double  h;              /* grid spacing (> 0)                                  */
     /* solver */
@@ -111,6 +122,10 @@ typedef struct cbs_desc {
     int32_t refine_sweeps;  /* refinement modes: 1 or 2                             */
     int32_t in_dtype;       /* CBS_DTYPE_* of the input (f or b)                   */
     int32_t out_dtype;      /* CBS_DTYPE_* of the output x (F64 for FP32_REFINE)   */
+    int32_t rhs_shift;      /* staggered kinds: s = 0 (half points -> nodes) or 1
+                               (nodes -> half points); ignored otherwise.  The
+                               staggered kinds need cyclic = 1, a Toeplitz LHS and
+                               on-chip lines (no batches)                          */
 } cbs_desc;
 
 typedef struct cbs_plan cbs_plan;

@@ -20,7 +20,7 @@ CBS_OK, CBS_ERR_INVALID_ARG, CBS_ERR_UNSUPPORTED, CBS_ERR_SINGULAR, CBS_ERR_TIME
 CBS_FP64, CBS_FP32, CBS_FP32_REFINE, CBS_FP32_REFINE_I64 = 0, 1, 2, 3
 CBS_DTYPE_F64, CBS_DTYPE_F32 = 0, 1
 CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE = 0, 1
-CBS_RHS_NONE, CBS_RHS_CENTRAL = 0, 1
+CBS_RHS_NONE, CBS_RHS_CENTRAL, CBS_RHS_STAGGERED, CBS_RHS_MIDPOINT = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA",
                 6: "NO_MEMORY"}
@@ -57,6 +57,7 @@ class cbs_desc(ctypes.Structure):
         ("refine_sweeps", ctypes.c_int32),
         ("in_dtype", ctypes.c_int32),
         ("out_dtype", ctypes.c_int32),
+        ("rhs_shift", ctypes.c_int32),
     ]
 
 

@@ -81,6 +81,8 @@ int mode_of(int precision) {
                                         : kModeRefineI64;
 }
 
+bool is_staggered(const cbs_desc* d) { return d->rhs_kind == CBS_RHS_STAGGERED || d->rhs_kind == CBS_RHS_MIDPOINT; }
+
 cbs_status validate(const cbs_desc* d) {
   if (!d) return fail(CBS_ERR_INVALID_ARG, "null descriptor");
   for (int k = 0; k < 3; k++)
@@ -90,11 +92,19 @@ cbs_status validate(const cbs_desc* d) {
   if (d->cyclic != 0 && d->cyclic != 1) return fail(CBS_ERR_INVALID_ARG, "cyclic must be 0 or 1");
   if (d->lhs_kind != CBS_LHS_TOEPLITZ && d->lhs_kind != CBS_LHS_VARIABLE)
     return fail(CBS_ERR_INVALID_ARG, "bad lhs_kind");
-  if (d->rhs_kind != CBS_RHS_NONE && d->rhs_kind != CBS_RHS_CENTRAL) return fail(CBS_ERR_INVALID_ARG, "bad rhs_kind");
+  if (d->rhs_kind < CBS_RHS_NONE || d->rhs_kind > CBS_RHS_MIDPOINT) return fail(CBS_ERR_INVALID_ARG, "bad rhs_kind");
   if (d->rhs_kind == CBS_RHS_CENTRAL) {
     if (d->rhs_terms < 1 || d->rhs_terms > 3) return fail(CBS_ERR_INVALID_ARG, "rhs_terms must be 1..3");
     if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(CBS_ERR_INVALID_ARG, "h must be positive");
     if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the central stencil is periodic: needs cyclic = 1");
+  }
+  if (is_staggered(d)) {
+    if (d->rhs_terms < 1 || d->rhs_terms > 2) return fail(CBS_ERR_INVALID_ARG, "staggered stencils: rhs_terms 1..2");
+    if (d->rhs_shift != 0 && d->rhs_shift != 1) return fail(CBS_ERR_INVALID_ARG, "rhs_shift must be 0 or 1");
+    if (d->rhs_kind == CBS_RHS_STAGGERED && (!(d->h > 0.0) || !std::isfinite(d->h)))
+      return fail(CBS_ERR_INVALID_ARG, "h must be positive");
+    if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the staggered stencils are periodic: needs cyclic = 1");
+    if (d->lhs_kind != CBS_LHS_TOEPLITZ) return fail(CBS_ERR_UNSUPPORTED, "staggered stencils: Toeplitz bands only");
   }
   if (d->precision < CBS_FP64 || d->precision > CBS_FP32_REFINE_I64) return fail(CBS_ERR_INVALID_ARG, "bad precision");
   if (is_refine(d->precision) && (d->refine_sweeps < 1 || d->refine_sweeps > 2))
@@ -584,7 +594,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   }
   P->M = M;
   P->ks = 0;
-  if (d->rhs_kind == CBS_RHS_CENTRAL) P->ks = d->rhs_terms <= 2 ? 2 : 3;
+  if (d->rhs_kind != CBS_RHS_NONE) P->ks = d->rhs_terms <= 2 ? 2 : 3;
 
   // ---- device tables ----
   st = fill_dev_tables(P->dev, T, A, d, 0, &P->dbuf);
@@ -607,10 +617,17 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   a.nz = d->dims[2];
   a.nlines = P->nlines;
   a.dir = d->direction;
-  a.K = (d->rhs_kind == CBS_RHS_CENTRAL) ? d->rhs_terms : 0;
+  a.K = (d->rhs_kind != CBS_RHS_NONE) ? d->rhs_terms : 0;
   a.sweeps = d->refine_sweeps;
+  a.stag_shift = is_staggered(d) ? d->rhs_shift : 0;
+  a.stag_sum = d->rhs_kind == CBS_RHS_MIDPOINT;
   for (int q = 0; q < kMaxRhsTerms; q++) {
-    const double w = (q < a.K) ? d->rhs_coef[q] / (2.0 * (q + 1) * d->h) : 0.0;
+    // term weights: c_q / (2 q h) (Eq. 1), c_q / ((2q - 1) h) (staggered
+    // derivative), c_q / 2 (midpoint interpolation)
+    const double den = d->rhs_kind == CBS_RHS_CENTRAL     ? 2.0 * (q + 1) * d->h
+                       : d->rhs_kind == CBS_RHS_STAGGERED ? (2.0 * q + 1.0) * d->h
+                                                          : 2.0;
+    const double w = (q < a.K) ? d->rhs_coef[q] / den : 0.0;
     a.w[q] = w;
     a.wHi[q] = (float)w;
     a.wLo[q] = (float)(w - (double)a.wHi[q]);
@@ -723,7 +740,7 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaErrorInvalidValue;
   const int R = P->r;
-#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, P->ks, d.in_dtype, d.out_dtype, a, P->dev, s)
+#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, P->ks, is_staggered(&d), d.in_dtype, d.out_dtype, a, P->dev, s)
   if (mode == kModeF64) e = (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
   else if (mode == kModeF32) e = (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
   else if (mode == kModeRefine) e = (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
@@ -756,9 +773,9 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
     return CBS_OK;
   }
   if (P->kind != 0) return fail(CBS_ERR_UNSUPPORTED, "transpose solve of long-line plans");
-  // Toeplitz: A is symmetric, and on a periodic grid A^{-1} and the central
-  // stencil S are both circulant, so S^T A^{-T} g = A^{-1} (S^T g) = A^{-1} (-S g):
-  // the same line kernel with negated stencil weights.
+  // Toeplitz: A is symmetric, and on a periodic grid A^{-1} and the stencil S
+  // are both circulant, so S^T A^{-T} g = A^{-1} (S^T g), with S^T = -S for the
+  // central stencil: the same line kernel with transposed stencil weights.
   if (d.in_dtype != d.out_dtype) return fail(CBS_ERR_UNSUPPORTED, "transpose needs in_dtype == out_dtype");
   if (!d.cyclic) return fail(CBS_ERR_UNSUPPORTED, "transpose of acyclic plans");
   if (grad_bands) return fail(CBS_ERR_INVALID_ARG, "Toeplitz plans have no band field");
@@ -766,7 +783,7 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
   const int R = P->r;
   int launches = 0;
   auto run = [&](const LineArgs& a, int ks) -> cudaError_t {
-#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, d.out_dtype, d.in_dtype, a, P->dev, s)
+#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, ks > 0 && is_staggered(&d), d.out_dtype, d.in_dtype, a, P->dev, s)
     if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
     if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
     if (mode == kModeRefine) return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
@@ -786,10 +803,15 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
     LineArgs a = P->args;
     a.in = g;
     a.out = grad_in;
-    for (int q = 0; q < kMaxRhsTerms; q++) {
-      a.w[q] = -a.w[q];
-      a.wHi[q] = -a.wHi[q];
-      a.wLo[q] = -a.wLo[q];
+    // staggered stencils: S^T is the stencil of the other shift (the input
+    // and output grids swap), negated for the derivative, as is the central one
+    if (is_staggered(&d)) a.stag_shift = 1 - a.stag_shift;
+    if (d.rhs_kind != CBS_RHS_MIDPOINT) {
+      for (int q = 0; q < kMaxRhsTerms; q++) {
+        a.w[q] = -a.w[q];
+        a.wHi[q] = -a.wHi[q];
+        a.wLo[q] = -a.wLo[q];
+      }
     }
     pack_weights(a);
     cudaError_t e = run(a, P->ks);
@@ -837,9 +859,10 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   for (int k = 0; k < count; k++) {
     const cbs_desc& d = descs[k];
     if (d.lhs_kind != CBS_LHS_TOEPLITZ || d.in_dtype != CBS_DTYPE_F64 || d.out_dtype != CBS_DTYPE_F64 ||
-        (d.precision != CBS_FP64 && d.precision != CBS_FP32_REFINE)) {
+        (d.precision != CBS_FP64 && d.precision != CBS_FP32_REFINE) || is_staggered(&d)) {
       cbs_batch_destroy(B);
-      return fail(CBS_ERR_UNSUPPORTED, "batch problems: Toeplitz, FP64 in/out, FP64 or FP32_REFINE");
+      return fail(CBS_ERR_UNSUPPORTED,
+                  "batch problems: Toeplitz, FP64 in/out, FP64 or FP32_REFINE, no staggered stencil");
     }
     cbs_plan* P = nullptr;
     cbs_status st = cbs_plan_create(&P, &d);

@@ -42,6 +42,11 @@ struct LineArgs {
   int dir;
   int K;                 // stencil terms actually used (<= template KS)
   int sweeps;            // refinement sweeps (refinement modes)
+  // staggered stencils (kernels compiled with ST = 1): stag_shift = s moves the
+  // window up by s rows; stag_sum = 1 adds the two points of a term
+  // (interpolation), 0 subtracts them (derivative).  Two shorts fill the
+  // alignment gap before w, so the argument block keeps its layout.
+  short stag_shift, stag_sum;
   double w[kMaxRhsTerms];              // c_q / (2 q h)
   float wHi[kMaxRhsTerms], wLo[kMaxRhsTerms];
   // the same split weights as pairs for the two-rows-per-instruction
@@ -908,11 +913,124 @@ __device__ __forceinline__ TW window_up(const TW (&w)[M + KS], const TW (&hh)[KA
   return pick<TW, KA, FULL>(hh, k + q - size);
 }
 
+// Staggered stencils (App. A.2; Eq. 2): when s is set, move the window up by
+// one row, so that window row r holds partition row r + 1 for r in
+// [-KS, M + KS - 2] (the top halo row is then never read).  Ascending order
+// reads every source before it is overwritten.
+template <typename X, int M, int KS, int KA, bool FULL>
+__device__ __forceinline__ void shift_window(X (&w)[M + KS], X (&hh)[KA], int size, bool s) {
+  if (!s) return;
+#pragma unroll
+  for (int j = 0; j < KS; j++) w[j] = w[j + 1];
+#pragma unroll
+  for (int k = 0; k < M; k++) w[KS + k] = window_up<X, M, KS, KA, FULL>(w, hh, k, 1, size);
+#pragma unroll
+  for (int q = 0; q + 1 < KA; q++) hh[q] = hh[q + 1];
+}
+
+// a1 with a staggered stencil on the (shifted) window:
+// b_k = sum_q w_q (f_{k+q-1} + SG f_{k-q}), SG = +1 interpolation, -1 derivative.
+template <int SG, typename T, typename TW, int M, int KS, int KA, bool FULL>
+__device__ __forceinline__ void staggered_rhs(const double* wq, const TW (&w)[M + KS], const TW (&hh)[KA], int size,
+                                              T (&v)[M]) {
+#pragma unroll
+  for (int k = 0; k < M; k++) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 1; q <= KS; q++) {
+      const T up = conv<T>(window_up<TW, M, KS, KA, FULL>(w, hh, k, q - 1, size));
+      const T dn = conv<T>(w[KS + k - q]);
+      s += (T)wq[q - 1] * (SG > 0 ? up + dn : up - dn);
+    }
+    v[k] = s;
+  }
+}
+
 // Split of an input element into an unevaluated FP32 pair.
 template <typename X>
 __device__ __forceinline__ f2 split_in(X x) {
   if constexpr (sizeof(X) == 8) return split_f64((double)x);
   else return f2{(float)x, 0.f};
+}
+
+// a1 in double-float on the refinement path: b_k = sum_q w_q (f_{k+q+DU} +
+// SG f_{k-q}) from the split window (fh, fl; upper halo hhh, hhl), as an
+// unevaluated pair (bh carries the leading bits, bl the rest).  DU = 0, SG =
+// -1: the central stencil of Eq. 1; DU = -1: the staggered stencils of App.
+// A.2 / Eq. 2 on a shifted window.  Whole-size partitions with M even take
+// rows k and k + M/2 in one instruction (same results as the scalar form).
+template <int DU, int SG, int M, int KS, int KA, bool FULL>
+__device__ __forceinline__ void rhs_df(const LineArgs& a, const float (&fh)[M + KS], const float (&fl)[M + KS],
+                                       const float (&hhh)[KA], const float (&hhl)[KA], int size, float (&bh)[M],
+                                       float (&bl)[M]) {
+  if constexpr (FULL && (M % 2) == 0) {
+    constexpr int H = M / 2;
+#pragma unroll
+    for (int k = 0; k < H; k++) {
+      f32x2 dh = 0ull, dl = 0ull;
+#pragma unroll
+      for (int q = 1; q <= KS; q++) {
+        const f32x2 uh = pk(win_row<M, KS, KA>(fh, hhh, k + q + DU), win_row<M, KS, KA>(fh, hhh, k + H + q + DU));
+        const f32x2 ul = pk(win_row<M, KS, KA>(fl, hhl, k + q + DU), win_row<M, KS, KA>(fl, hhl, k + H + q + DU));
+        f32x2 ds, de, dlo;
+        if constexpr (SG > 0) {
+          two_sum2(uh, pk(fh[KS + k - q], fh[KS + k + H - q]), ds, de);
+          dlo = add2(de, add2(ul, pk(fl[KS + k - q], fl[KS + k + H - q])));
+        } else {
+          two_diff2(uh, pk(fh[KS + k - q], fh[KS + k + H - q]), ds, de);
+          dlo = add2(de, sub2(ul, pk(fl[KS + k - q], fl[KS + k + H - q])));
+        }
+        const f32x2 W = a.wP[q - 1][0], NW = a.wP[q - 1][1], WL = a.wP[q - 1][2];
+        const f32x2 pr = mul2(W, ds);
+        const f32x2 pen = fma2(NW, ds, pr);  // -(error of pr)
+        const f32x2 plo = sub2(fma2(W, dlo, mul2(WL, ds)), pen);
+        if (q == 1) {
+          dh = pr;
+          dl = plo;
+        } else {
+          f32x2 sh, se;
+          two_sum2(dh, pr, sh, se);
+          dh = sh;
+          dl = add2(dl, add2(se, plo));
+        }
+      }
+      unpk(dh, bh[k], bh[k + H]);
+      unpk(dl, bl[k], bl[k + H]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      float dh = 0.f, dl = 0.f;
+#pragma unroll
+      for (int q = 1; q <= KS; q++) {
+        const int u = k + q + DU;  // row of the upper point
+        const int kq = (u < M) ? u : M - 1;
+        float uh, ul;
+        if (u < M) {
+          uh = sel2<FULL>(u < size, fh[KS + kq], pick<float, KA, FULL>(hhh, u - size));
+          ul = sel2<FULL>(u < size, fl[KS + kq], pick<float, KA, FULL>(hhl, u - size));
+        } else {
+          uh = pick<float, KA, FULL>(hhh, u - size);
+          ul = pick<float, KA, FULL>(hhl, u - size);
+        }
+        const float dnh = fh[KS + k - q], dnl = fl[KS + k - q];
+        const f2 df = two_sum(uh, SG > 0 ? dnh : -dnh);
+        const float dlo = df.lo + (SG > 0 ? ul + dnl : ul - dnl);
+        const f2 pr = two_prod(a.wHi[q - 1], df.hi);
+        const float plo = pr.lo + __fmaf_rn(a.wHi[q - 1], dlo, a.wLo[q - 1] * df.hi);
+        if (q == 1) {
+          dh = pr.hi;
+          dl = plo;
+        } else {
+          const f2 sm = two_sum(dh, pr.hi);
+          dh = sm.hi;
+          dl += sm.lo + plo;
+        }
+      }
+      bh[k] = dh;
+      bl[k] = dl;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- async copies
@@ -1033,7 +1151,7 @@ __device__ __forceinline__ void prefetch_rows(TIn* slot0, const TIn* gline, int6
 // per-plan kernel (one tile per CTA) and by the persistent batch kernel (many
 // tiles per CTA).
 template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged,
-          bool PIPE = false>
+          bool PIPE = false, int ST = 0>
 __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables& t, const void* in_ptr,
                                           void* out_ptr, const int tx, const int to, unsigned char* smem_raw,
                                           const TIn* pslots = nullptr) {
@@ -1138,17 +1256,24 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;  // interface of the FP32 solves
   if constexpr (!refine_mode(MODE)) {
     T v[M];
+    if constexpr (KS > 0 && ST != 0) {
+      shift_window<TW, M, KS, KA, FULL>(w, hh, size, a.stag_shift != 0);
+      if (a.stag_sum) staggered_rhs<1, T, TW, M, KS, KA, FULL>(a.w, w, hh, size, v);
+      else staggered_rhs<-1, T, TW, M, KS, KA, FULL>(a.w, w, hh, size, v);
+    } else {
 #pragma unroll
-    for (int k = 0; k < M; k++) {
-      if (KS == 0) {
-        v[k] = conv<T>(w[KS + k]);
-      } else {
-        // a1: b_k = sum_q w_q (f_{k+q} - f_{k-q})
-        T s = T(0);
+      for (int k = 0; k < M; k++) {
+        if (KS == 0) {
+          v[k] = conv<T>(w[KS + k]);
+        } else {
+          // a1: b_k = sum_q w_q (f_{k+q} - f_{k-q})
+          T s = T(0);
 #pragma unroll
-        for (int q = 1; q <= KS; q++)
-          s += (T)a.w[q - 1] * (conv<T>(window_up<TW, M, KS, KA, FULL>(w, hh, k, q, size)) - conv<T>(w[KS + k - q]));
-        v[k] = s;
+          for (int q = 1; q <= KS; q++)
+            s += (T)a.w[q - 1] *
+                 (conv<T>(window_up<TW, M, KS, KA, FULL>(w, hh, k, q, size)) - conv<T>(w[KS + k - q]));
+          v[k] = s;
+        }
       }
     }
     solve_partition<T, R, M, T, FULL>(v, size, i, lane_ok, t, xch);
@@ -1320,69 +1445,14 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         bh[k] = fh[KS + k];
         bl[k] = fl[KS + k];
       }
-    } else if constexpr (FULL && (M % 2) == 0) {
-      // a1 in double-float, rows k and k + M/2 in one instruction (same
-      // results as the scalar form below)
-      constexpr int H = M / 2;
-#pragma unroll
-      for (int k = 0; k < H; k++) {
-        f32x2 dh = 0ull, dl = 0ull;
-#pragma unroll
-        for (int q = 1; q <= KS; q++) {
-          const f32x2 uh = pk(win_row<M, KS, KA>(fh, hhh, k + q), win_row<M, KS, KA>(fh, hhh, k + H + q));
-          const f32x2 ul = pk(win_row<M, KS, KA>(fl, hhl, k + q), win_row<M, KS, KA>(fl, hhl, k + H + q));
-          f32x2 ds, de;
-          two_diff2(uh, pk(fh[KS + k - q], fh[KS + k + H - q]), ds, de);
-          const f32x2 dlo = add2(de, sub2(ul, pk(fl[KS + k - q], fl[KS + k + H - q])));
-          const f32x2 W = a.wP[q - 1][0], NW = a.wP[q - 1][1], WL = a.wP[q - 1][2];
-          const f32x2 pr = mul2(W, ds);
-          const f32x2 pen = fma2(NW, ds, pr);  // -(error of pr)
-          const f32x2 plo = sub2(fma2(W, dlo, mul2(WL, ds)), pen);
-          if (q == 1) {
-            dh = pr;
-            dl = plo;
-          } else {
-            f32x2 sh, se;
-            two_sum2(dh, pr, sh, se);
-            dh = sh;
-            dl = add2(dl, add2(se, plo));
-          }
-        }
-        unpk(dh, bh[k], bh[k + H]);  // unnormalised pair, as below
-        unpk(dl, bl[k], bl[k + H]);
-      }
+    } else if constexpr (ST != 0) {
+      shift_window<float, M, KS, KA, FULL>(fh, hhh, size, a.stag_shift != 0);
+      shift_window<float, M, KS, KA, FULL>(fl, hhl, size, a.stag_shift != 0);
+      if (a.stag_sum) rhs_df<-1, 1, M, KS, KA, FULL>(a, fh, fl, hhh, hhl, size, bh, bl);
+      else rhs_df<-1, -1, M, KS, KA, FULL>(a, fh, fl, hhh, hhl, size, bh, bl);
     } else {
-      // a1 in double-float: b = sum_q w_q (f_{k+q} - f_{k-q})
-#pragma unroll
-      for (int k = 0; k < M; k++) {
-        float dh = 0.f, dl = 0.f;
-#pragma unroll
-        for (int q = 1; q <= KS; q++) {
-          const int kq = (k + q < M) ? k + q : M - 1;
-          float uh, ul;
-          if (k + q < M) {
-            uh = sel2<FULL>(k + q < size, fh[KS + kq], pick<float, KA, FULL>(hhh, k + q - size));
-            ul = sel2<FULL>(k + q < size, fl[KS + kq], pick<float, KA, FULL>(hhl, k + q - size));
-          } else {
-            uh = pick<float, KA, FULL>(hhh, k + q - size);
-            ul = pick<float, KA, FULL>(hhl, k + q - size);
-          }
-          const f2 df = two_sum(uh, -fh[KS + k - q]);
-          const float dlo = df.lo + (ul - fl[KS + k - q]);
-          const f2 pr = two_prod(a.wHi[q - 1], df.hi);
-          const float plo = pr.lo + __fmaf_rn(a.wHi[q - 1], dlo, a.wLo[q - 1] * df.hi);
-          if (q == 1) {
-            dh = pr.hi;
-            dl = plo;
-          } else {
-            const f2 sm = two_sum(dh, pr.hi);
-            dh = sm.hi;
-            dl += sm.lo + plo;
-          }
-        }
-        bh[k] = dh;  // unnormalised pair: bh carries the leading bits, bl the rest
-        bl[k] = dl;
-      }
+      // a1: b = sum_q w_q (f_{k+q} - f_{k-q}) in double-float
+      rhs_df<0, -1, M, KS, KA, FULL>(a, fh, fl, hhh, hhl, size, bh, bl);
     }
     // sweep 0: x0 = A^{-1} bh
     float xh[M], v[M];
@@ -1468,10 +1538,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   }
 }
 
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL, int LAYOUT>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL, int LAYOUT, int ST = 0>
 __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3) line_kernel(const LineArgs a, const DevLineTables t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  line_tile<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
+  line_tile<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT, false, ST>(a, t, a.in, a.out, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Issue (and commit) the copies of this thread's rows of tile `tile` into
@@ -1500,7 +1570,7 @@ __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTa
 // overlaps the arithmetic.  Shared memory: the message buffer (strided
 // layout only, kCtaXchgSlots 64-bit slots per thread) followed by 2 x
 // (M + 2 KS) slots of TIn per thread.
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT, int ST = 0>
 __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
     line_kernel_pipe(const LineArgs a, const DevLineTables t, const int gx, const int ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1520,8 +1590,8 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
       cp_async_wait<0>();
     }
     const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
-    line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true>(a, t, a.in, a.out, tx, to, smem_raw,
-                                                           slots + (size_t)buf * NS * bd);
+    line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true, ST>(a, t, a.in, a.out, tx, to, smem_raw,
+                                                               slots + (size_t)buf * NS * bd);
   }
 }
 

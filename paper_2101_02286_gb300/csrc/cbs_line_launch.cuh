@@ -28,7 +28,8 @@ inline dim3 tile_grid(int64_t nx, int64_t ny, int64_t nz, int64_t nlines, int di
   return dim3((unsigned)((nx + lines_per_cta - 1) / lines_per_cta), (unsigned)(dir == 1 ? nz : ny), 1);
 }
 
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL = false, int LAYOUT = kStaged,
+          int ST = 0>
 cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
   if (a.nlines <= 0) return cudaSuccess;
@@ -47,19 +48,19 @@ cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s
                       : LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0;
   static size_t configured = 0;  // per instantiation
   if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT>,
+    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT><<<grid, threads, smem, s>>>(a, t);
+  line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT, ST><<<grid, threads, smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
 // Persistent pipelined launch (whole-size partitions, direct layouts): one
 // CTA per resident slot (occupancy x SMs), each walking tiles with the next
 // tile's rows in flight while it computes the current one.
-template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT>
+template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT, int ST = 0>
 cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if (a.nlines <= 0) return cudaSuccess;
   constexpr int NS = M + 2 * KS;
@@ -69,7 +70,7 @@ cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t 
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
   const size_t smem = (LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0) +
                       2 * (size_t)NS * threads * sizeof(TIn);
-  auto kern = line_kernel_pipe<R, M, MODE, KS, TIn, TOut, LAYOUT>;
+  auto kern = line_kernel_pipe<R, M, MODE, KS, TIn, TOut, LAYOUT, ST>;
   // per instantiation: the largest dynamic shared memory configured so far
   // and the occupancy of the last (threads, smem) launched (both depend on
   // the plan's lanes per line, not only on the instantiation)
@@ -106,7 +107,7 @@ cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t 
 // for FP64 input and output only.
 inline bool tile_full(const DevLineTables& t, int M) { return t.count_big == t.p && t.rows_big == M; }
 
-template <int R, int M, int MODE, int KSV, typename TIn, typename TOut>
+template <int R, int M, int MODE, int KSV, typename TIn, typename TOut, int ST = 0>
 cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if constexpr (sizeof(TIn) == 8 && sizeof(TOut) == 8) {
     if (tile_full(t, M)) {
@@ -114,19 +115,22 @@ cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream
       // hide HBM latency without the pipelined prefetch; the FP64 / FP32
       // kernels keep 3 CTAs per SM and load directly
       if constexpr (refine_mode(MODE)) {
-        if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectX>(a, t, s);
-        return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectStrided>(a, t, s);
+        if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectX, ST>(a, t, s);
+        return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectStrided, ST>(a, t, s);
       } else {
-        if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectX>(a, t, s);
-        return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectStrided>(a, t, s);
+        if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectX, ST>(a, t, s);
+        return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectStrided, ST>(a, t, s);
       }
     }
   }
-  return launch_one<R, M, MODE, KSV, TIn, TOut, false, kStaged>(a, t, s);
+  return launch_one<R, M, MODE, KSV, TIn, TOut, false, kStaged, ST>(a, t, s);
 }
 
+// KS: stencil terms compiled in; the staggered stencils (LineArgs::stag_*
+// in use, a.K <= 2) have their own kernels with two terms.
 template <int R, int M, int MODE, typename TIn, typename TOut>
-cudaError_t launch_ks(int KS, const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
+cudaError_t launch_ks(int KS, bool staggered, const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
+  if (staggered) return KS == 2 ? launch_variant<R, M, MODE, 2, TIn, TOut, 1>(a, t, s) : cudaErrorNotSupported;
   switch (KS) {
     case 0: return launch_variant<R, M, MODE, 0, TIn, TOut>(a, t, s);
     case 2: return launch_variant<R, M, MODE, 2, TIn, TOut>(a, t, s);
@@ -137,34 +141,35 @@ cudaError_t launch_ks(int KS, const LineArgs& a, const DevLineTables& t, cudaStr
 
 // Defined once per (MODE, R, M) in its own translation unit (parallel build).
 template <int MODE, int R, int M>
-cudaError_t launch_line_mrm(int KS, int tin, int tout, const LineArgs& a, const DevLineTables& t, cudaStream_t s);
+cudaError_t launch_line_mrm(int KS, bool staggered, int tin, int tout, const LineArgs& a, const DevLineTables& t,
+                            cudaStream_t s);
 
 // Supported element types: FP64 -> FP64 for every mode; FP32 -> FP32 for the
 // FP32 mode; FP32 input -> FP64 output without a stencil for the FP64 and
 // refinement modes.
 #define CBS_DEFINE_LINE_LAUNCH(MODE, R, M)                                                        \
   template <>                                                                                     \
-  cudaError_t launch_line_mrm<MODE, R, M>(int KS, int tin, int tout, const LineArgs& a,           \
+  cudaError_t launch_line_mrm<MODE, R, M>(int KS, bool stag, int tin, int tout, const LineArgs& a, \
                                           const DevLineTables& t, cudaStream_t s) {               \
     const bool i64 = tin == CBS_DTYPE_F64, o64 = tout == CBS_DTYPE_F64;                          \
-    if (i64 && o64) return launch_ks<R, M, MODE, double, double>(KS, a, t, s);                    \
+    if (i64 && o64) return launch_ks<R, M, MODE, double, double>(KS, stag, a, t, s);              \
     if constexpr (MODE == kModeF32) {                                                             \
-      if (!i64 && !o64) return launch_ks<R, M, MODE, float, float>(KS, a, t, s);                  \
+      if (!i64 && !o64) return launch_ks<R, M, MODE, float, float>(KS, stag, a, t, s);            \
     } else {                                                                                      \
-      if (!i64 && o64 && KS == 0) return launch_one<R, M, MODE, 0, float, double>(a, t, s);       \
+      if (!i64 && o64 && KS == 0 && !stag) return launch_one<R, M, MODE, 0, float, double>(a, t, s); \
     }                                                                                             \
     return cudaErrorNotSupported;                                                                 \
   }
 
 // Dispatch over M (declared specialisations live in the per-M units).
 template <int MODE, int R>
-inline cudaError_t launch_line_mode_r(int M, int KS, int tin, int tout, const LineArgs& a, const DevLineTables& t,
-                                      cudaStream_t s) {
+inline cudaError_t launch_line_mode_r(int M, int KS, bool stag, int tin, int tout, const LineArgs& a,
+                                      const DevLineTables& t, cudaStream_t s) {
   switch (M) {
-    case 8: return launch_line_mrm<MODE, R, 8>(KS, tin, tout, a, t, s);
-    case 16: return launch_line_mrm<MODE, R, 16>(KS, tin, tout, a, t, s);
+    case 8: return launch_line_mrm<MODE, R, 8>(KS, stag, tin, tout, a, t, s);
+    case 16: return launch_line_mrm<MODE, R, 16>(KS, stag, tin, tout, a, t, s);
     case 32:
-      if constexpr (!refine_mode(MODE)) return launch_line_mrm<MODE, R, 32>(KS, tin, tout, a, t, s);
+      if constexpr (!refine_mode(MODE)) return launch_line_mrm<MODE, R, 32>(KS, stag, tin, tout, a, t, s);
       break;
   }
   return cudaErrorNotSupported;

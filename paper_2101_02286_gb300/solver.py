@@ -14,15 +14,22 @@ _PREC = {"fp64": abi.CBS_FP64, "fp32": abi.CBS_FP32, "fp32_refine": abi.CBS_FP32
 _DT = {torch.float64: abi.CBS_DTYPE_F64, torch.float32: abi.CBS_DTYPE_F32}
 
 
+_STENCIL = {"central": abi.CBS_RHS_CENTRAL, "staggered": abi.CBS_RHS_STAGGERED, "midpoint": abi.CBS_RHS_MIDPOINT}
+
+
 def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 1.0, segments: int = 0,
               precision: str = "fp64", sweeps: int = 1, in_dtype=torch.float64, out_dtype=None,
-              cyclic: bool = True, bands_ptr: int | None = None) -> abi.cbs_desc:
+              cyclic: bool = True, bands_ptr: int | None = None, stencil: str = "central",
+              shift: int = 0) -> abi.cbs_desc:
     """Descriptor for lines along `direction` of a (nz, ny, nx) field.
 
     lhs: (alpha,) tridiagonal or (alpha, beta) pentadiagonal Toeplitz bands
     (diagonal 1), or "variable" with bands_ptr pointing at a per-point alpha
-    field.  rhs: None (input is b) or Lele coefficients (c_1, .., c_K) of the
-    periodic central stencil with spacing h.
+    field.  rhs: None (input is b) or the coefficients (c_1, .., c_K) of the
+    periodic stencil named by `stencil`: "central" (Eq. 1, spacing h),
+    "staggered" (staggered first derivative, App. A.2) or "midpoint" (compact
+    interpolation, Eq. 2); the two staggered kinds map half points to nodes
+    (shift 0) or nodes to half points (shift 1).
     """
     nz, ny, nx = (int(s) for s in shape_zyx)
     d = abi.cbs_desc()
@@ -43,7 +50,8 @@ def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 
         d.rhs_kind = abi.CBS_RHS_NONE
         d.rhs_terms = 0
     else:
-        d.rhs_kind = abi.CBS_RHS_CENTRAL
+        d.rhs_kind = _STENCIL[stencil]
+        d.rhs_shift = int(shift)
         d.rhs_terms = len(rhs)
         for q, c in enumerate(rhs):
             d.rhs_coef[q] = float(c)

@@ -142,3 +142,28 @@ def test_plan_create_validates_before_any_device_work():
     with pytest.raises(abi.CbsError) as e:
         abi.cbs_plan_create(d)
     assert e.value.status == abi.CBS_ERR_INVALID_ARG
+
+
+def test_staggered_descriptors_validated_before_device_work():
+    from paper_2101_02286_gb300 import workloads as W
+    from paper_2101_02286_gb300.solver import Plan
+    sch = W.STAGGERED6
+    cases = [
+        (dict(stencil="staggered", shift=2), abi.CBS_ERR_INVALID_ARG),               # shift is 0 or 1
+        (dict(stencil="midpoint", rhs=(1.5, 0.1, 0.01)), abi.CBS_ERR_INVALID_ARG),   # 1..2 terms
+        (dict(stencil="staggered", h=0.0), abi.CBS_ERR_INVALID_ARG),                 # derivative spacing
+        (dict(stencil="staggered", cyclic=False), abi.CBS_ERR_UNSUPPORTED),          # periodic only
+        (dict(stencil="midpoint", lhs="variable", bands_ptr=4096), abi.CBS_ERR_UNSUPPORTED),
+    ]
+    for kw, status in cases:
+        kw.setdefault("lhs", sch["lhs"])
+        kw.setdefault("rhs", sch["rhs"])
+        kw.setdefault("h", 0.1)
+        with pytest.raises(abi.CbsError) as e:
+            Plan((4, 4, 64), 0, **kw)
+        assert e.value.status == status, kw
+    d = make_desc((4, 4, 64), 0, lhs=sch["lhs"], rhs=sch["rhs"], h=0.1)
+    d.rhs_kind = 4
+    with pytest.raises(abi.CbsError) as e:
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG
