@@ -334,23 +334,29 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     b.close()
     del ins, outs, items, g
 
-    # the paper's single-GPU workload along x: 256^2 lines of 8192, cyclic
-    # tridiagonal alpha = 1/3, right-hand side given, p = 8 and 7 (2^n - 1)
-    dpx = np.random.default_rng(20).standard_normal((256, 256, 8192))
+    # the paper's single-GPU workload: 256^2 lines of 8192 along x, y and z
+    # (fields 8192 x 256 x 256, 256 x 8192 x 256, 256 x 256 x 8192), cyclic
+    # tridiagonal alpha = 1/3, right-hand side given, p = 8 and 7 (2^n - 1);
+    # the three fields share one buffer of random values
+    dpx = np.random.default_rng(20).standard_normal(256 * 256 * 8192)
     di = torch.from_numpy(dpx).to(dev)
     do = torch.empty_like(di)
-    for prec, p in (("fp32_refine", 8), ("fp32_refine", 7), ("fp64", 8)):
-        pl = Plan(dpx.shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=None, precision=prec, segments=p)
-        ms = time_ms(lambda: pl.solve(di, do, stream), stream, max(3, steps // 2))
+    for direction, prec, p in ((0, "fp32_refine", 8), (0, "fp32_refine", 7), (0, "fp64", 8),
+                               (1, "fp32_refine", 8), (1, "fp64", 8), (2, "fp32_refine", 8), (2, "fp64", 8)):
+        shape = [(256, 256, 8192), (256, 8192, 256), (8192, 256, 256)][direction]  # (nz, ny, nx)
+        pl = Plan(shape, direction, lhs=W.LELE6_TRI["lhs"], rhs=None, precision=prec, segments=p)
+        dv, ov = di.view(shape), do.view(shape)
+        ms = time_ms(lambda: pl.solve(dv, ov, stream), stream, max(3, steps // 2))
         err = None
         if check:
             ii = rng.integers(0, 256, size=(8, 2))
-            lines = np.stack([dpx[i, j] for i, j in ii])
+            src = np.moveaxis(dpx.reshape(shape), 2 - direction, -1)
+            got = np.moveaxis(do.cpu().numpy().reshape(shape), 2 - direction, -1)
+            lines = np.stack([src[i, j] for i, j in ii])
             ref = oracle.solve_cyclic(oracle.toeplitz_bands(8192, W.LELE6_TRI["lhs"]), lines)
-            got = do.cpu().numpy()
             err = oracle.rel_err(np.stack([got[i, j] for i, j in ii]), ref)
-        res.append(_entry("256^2 x-lines of 8192 (the paper's single-GPU workload, x only), cyclic tridiagonal "
-                          "alpha=1/3, right-hand side given, %d segments per line, %s" % (p, prec),
+        res.append(_entry("256^2 %s-lines of 8192 (the paper's single-GPU workload), cyclic tridiagonal "
+                          "alpha=1/3, right-hand side given, %d segments per line, %s" % ("xyz"[direction], p, prec),
                           256 * 256 * 8192, ms, 16, hbm, err, segments=p, sampled_lines=8))
         pl.close()
     del di, do, dpx

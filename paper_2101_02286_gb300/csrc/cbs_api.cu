@@ -317,12 +317,17 @@ static int truncated_inverse_rows(const LineTables& T, int N, int r, std::vector
 // them to 2^-60.  Otherwise p must divide n and the segments are equal, with
 // ragged inner partitions.
 cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
-  if (d->direction != 0 || d->rhs_kind != CBS_RHS_NONE || !d->cyclic || d->lhs_kind != CBS_LHS_TOEPLITZ)
-    return fail(CBS_ERR_UNSUPPORTED, "long lines: x-lines, right-hand side given, cyclic Toeplitz bands");
+  if (d->rhs_kind != CBS_RHS_NONE || !d->cyclic || d->lhs_kind != CBS_LHS_TOEPLITZ)
+    return fail(CBS_ERR_UNSUPPORTED, "long lines: right-hand side given, cyclic Toeplitz bands");
   const int n = P->n, r = P->r;
+  // y/z lines run a tile of adjacent lines per CTA (kLongLines, or half as
+  // many above 512 / kLongLines inner partitions): at most 1024 / kLongLines
+  // inner partitions (segments of about 2048 rows)
+  const bool tiled = d->direction != 0;
+  const int max_inner = tiled ? 1024 / kLongLines : 512;
   int p = d->segments;
-  if (!p) {  // segments of about 4096 rows
-    p = (n + 4095) / 4096;
+  if (!p) {  // segments of about 4096 rows (x), 1024 (y/z)
+    p = tiled ? (n + 1023) / 1024 : (n + 4095) / 4096;
     if ((n - (int64_t)p * r) % 16 != 0)
       while (p < n && n % p) p++;
   }
@@ -343,7 +348,7 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
     const int64_t T16 = (n - (int64_t)p * r) / 16;        // 16-row blocks of all bulks
     const int64_t K16 = (T16 + p - 1) / p;                 // blocks of a big segment
     const int64_t cbig = T16 - (int64_t)p * (K16 - 1);     // in [1, p]
-    if (K16 <= 512 && K16 - 1 >= 2 * r) {
+    if (K16 <= max_inner && K16 - 1 >= 2 * r) {
       sizes[0] = (int)cbig;
       sizes[1] = (int)(16 * K16 + r);
       sizes[2] = (int)(16 * (K16 - 1) + r);
@@ -377,7 +382,9 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   const int m = sizes[1], N = m - r;
   const int pin = full ? N / 16 : (N + 15) / 16;
   const int Ns = sizes[2] - r, pin_s = full ? Ns / 16 : (Ns + 15) / 16;
-  if (pin > 512) return fail(CBS_ERR_UNSUPPORTED, "long lines: segments above 8192 rows (raise segments)");
+  if (pin > max_inner)
+    return fail(CBS_ERR_UNSUPPORTED, tiled ? "long y/z lines: segments above 2048 rows (raise segments)"
+                                           : "long lines: segments above 8192 rows (raise segments)");
   if (N < 2 * r * pin || Ns < 2 * r * pin_s || sizes[2] < 4 * r)
     return fail(CBS_ERR_INVALID_ARG, "long lines: segments too short");
   if (!full) {
@@ -434,6 +441,11 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   a.msmall = sizes[2];
   a.sweeps = d->refine_sweeps;
   for (int k = 0; k < 2 * kMaxR + 1; k++) a.band[k] = A.v[k];
+  LongGeom& gm = P->lgeom;
+  gm.nx = d->dims[0];
+  gm.ny = d->dims[1];
+  gm.dir = d->direction;
+  gm.es = d->direction == 0 ? 1 : d->direction == 1 ? d->dims[0] : d->dims[0] * d->dims[1];
   P->kind = 1;
   P->M = 16;
   P->inner_threads = threads;
@@ -727,7 +739,8 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     la.in = in;
     la.out = out;
     int launches = 0;
-    cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->dev,
+    cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->lgeom,
+                                P->dev,
                                 P->dev_inner, la.cbig < la.p ? &P->dev_inner_small : nullptr,
                                 P->inner_full, (cudaStream_t)stream, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "long-line kernel launch");

@@ -42,18 +42,35 @@ __device__ __forceinline__ int64_t seg_start(const LongArgs& a, int s) {
 }
 __device__ __forceinline__ int seg_rows(const LongArgs& a, int s) { return s < a.cbig ? a.m : a.msmall; }
 
+// Element offset of row 0 of a line (row k at + k * es); line < 2^31.
+__device__ __forceinline__ int64_t long_base(const LongArgs& a, const LongGeom& gm, int64_t line) {
+  if (gm.dir == 0) return line * a.n;
+  if (gm.dir == 1) {
+    const unsigned L = (unsigned)line, NX = (unsigned)gm.nx;
+    return (int64_t)(L % NX) + gm.nx * gm.ny * (int64_t)(L / NX);
+  }
+  return line;
+}
+
 // ---------------------------------------------------------------- 1. ends
-template <typename TIn>
-__global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a) {
-  const int seg = blockIdx.y;           // grid (lines, segments): lines may exceed 65535
-  const int64_t line = blockIdx.x;
+// One CTA per (segment, LG lines): x-lines LG = 1; y/z lines LG = kLongLines
+// adjacent lines, thread = (j, line) with the line fastest, so each row of
+// the tile is read as one contiguous run.
+template <typename TIn, int LG>
+__global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a, const LongGeom gm) {
+  constexpr int J = 128 / LG;           // threads per line
+  const int seg = blockIdx.y;           // grid (line tiles, segments): lines may exceed 65535
+  const int g = LG == 1 ? 0 : threadIdx.x % LG, jj = LG == 1 ? threadIdx.x : threadIdx.x / LG;
+  const int64_t line = (int64_t)blockIdx.x * LG + g;
+  const bool line_ok = LG == 1 || line < a.lines;
   const int r = a.r, N = seg_rows(a, seg) - r;
-  const TIn* b = (const TIn*)a.in + line * a.n + seg_start(a, seg) + r;  // first bulk row
+  const int64_t es = LG == 1 ? 1 : gm.es;
+  const TIn* b = (const TIn*)a.in + (LG == 1 ? line * a.n : long_base(a, gm, line)) + (seg_start(a, seg) + r) * es;
   double accF[kMaxR], accL[kMaxR];
 #pragma unroll
   for (int q = 0; q < kMaxR; q++) accF[q] = accL[q] = 0.0;
-  for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-    const double bf = (double)__ldg(b + j), bl = (double)__ldg(b + N - 1 - j);
+  for (int j = jj; line_ok && j < a.K; j += J) {
+    const double bf = (double)__ldg(b + j * es), bl = (double)__ldg(b + (N - 1 - j) * es);
 #pragma unroll
     for (int q = 0; q < kMaxR; q++)
       if (q < r) {
@@ -61,40 +78,44 @@ __global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a) {
         accL[q] += __ldg(a.G + (r - 1 - q) * a.K + j) * bl;  // persymmetry of D^{-1}
       }
   }
-  __shared__ double red[2 * kMaxR][4];
+  __shared__ double red[2 * kMaxR][4][LG];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 2 * kMaxR; q++) {
     double v = (q < kMaxR) ? accF[q] : accL[q - kMaxR];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    if (lane == 0) red[q][wid] = v;
+    for (int o = 16; o >= LG; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane < LG) red[q][wid][lane] = v;  // lane = the line for lane < LG
   }
   __syncthreads();
-  if (threadIdx.x < 2 * r) {
-    const int q = threadIdx.x;  // 0..r-1 first rows, r..2r-1 last rows
-    const int slot = (q < r) ? q : kMaxR + (q - r);
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[slot][w];
-    a.yb[(line * a.p + seg) * 2 * r + q] = v;
+  if (threadIdx.x < 2 * r * LG) {
+    const int q = threadIdx.x / LG, gg = threadIdx.x % LG;  // q: 0..r-1 first rows, r..2r-1 last rows
+    const int64_t ln = (int64_t)blockIdx.x * LG + gg;
+    if (LG == 1 || ln < a.lines) {
+      const int slot = (q < r) ? q : kMaxR + (q - r);
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[slot][w][gg];
+      a.yb[(ln * a.p + seg) * 2 * r + q] = v;
+    }
   }
 }
 
 // ---------------------------------------------------------------- 2. interface
-template <typename TIn>
-__global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, const DevLineTables t) {
+template <typename TIn, bool STR>
+__global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, const DevLineTables t, const LongGeom gm) {
   extern __shared__ __align__(16) double xs[];  // 2 buffers of p*r
   const int64_t line = blockIdx.x;
   const int p = a.p, r = a.r, rr = r * r;
   const double* yb = a.yb + line * p * 2 * r;
-  const TIn* bl = (const TIn*)a.in + line * a.n;
+  const TIn* bl = (const TIn*)a.in + (STR ? long_base(a, gm, line) : line * a.n);
+  const int64_t es = STR ? gm.es : 1;
   double* X0 = xs;
   double* X1 = xs + p * r;
   // b-hat_i = b~_i - L~ y_{i-1}[last] - U~ y_i[first]   (Eq. 21)
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
     const int im = (i == 0) ? p - 1 : i - 1;
     for (int q = 0; q < r; q++) {
-      double v = (double)__ldg(bl + seg_start(a, i) + q);
+      double v = STR ? (double)__ldg(bl + (seg_start(a, i) + q) * es) : (double)__ldg(bl + seg_start(a, i) + q);
       for (int e = 0; e < r; e++) {
         v -= t.Lt[q][e] * yb[im * 2 * r + r + e];
         v -= t.Ut[q][e] * yb[i * 2 * r + e];
@@ -153,18 +174,24 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 // inner partition has exactly M rows (whole-16-row layout): sizes are
 // compile-time and the refinement uses the paired residual.
 // One (segment, line) item, solved by the whole CTA.
-template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL>
-__device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables& tin, const int seg,
-                                         const int64_t line, CtaXchg& xch) {
+// LG: lines per CTA (1: x-lines, thread i = inner partition i; kLongLines or
+// kLongLines / 2: y/z lines, thread = (inner partition i, line g) with g
+// fastest).
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG, typename X>
+__device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables& tin, const LongGeom& gm,
+                                         const int seg, const int64_t line, X& xch) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
-  const int i = threadIdx.x, P = tin.p;
-  const bool lane_ok = i < P;
+  const int i = LG == 1 ? threadIdx.x : threadIdx.x / LG, P = tin.p;
+  const bool line_ok = LG == 1 || line < a.lines;
+  const bool lane_ok = i < P && line_ok;
   int start = 0, size = FULL ? M : 2 * R;
   if (FULL) start = i * M;
   else if (lane_ok) partition_of(tin, i, start, size);
-  const int64_t row0 = line * a.n + seg_start(a, seg);  // segment's first row
-  const TIn* b = (const TIn*)a.in + row0 + R + start;   // this partition's bulk rows
-  TOut* x = (TOut*)a.out + row0 + R + start;
+  const int64_t es = LG == 1 ? 1 : gm.es;
+  // the segment's first row, then this partition's first bulk row
+  const int64_t row0 = LG == 1 ? line * a.n + seg_start(a, seg) : long_base(a, gm, line) + seg_start(a, seg) * es;
+  const TIn* b = LG == 1 ? (const TIn*)a.in + row0 + R + start : (const TIn*)a.in + row0 + (R + start) * es;
+  TOut* x = LG == 1 ? (TOut*)a.out + row0 + R + start : (TOut*)a.out + row0 + (R + start) * es;
   const double* xt_here = a.xt + (line * a.p + seg) * R;
   const double* cc = a.cc + (line * a.p + seg) * 2 * R;  // [first R rows | last R rows]
   // Eq. 9 couplings to the known interface values, moved to the RHS; only the
@@ -180,7 +207,7 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
     T v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-      T val = (lane_ok && (FULL || k < size)) ? conv<T>(__ldg(b + k)) : T(0);
+      T val = (lane_ok && (FULL || k < size)) ? conv<T>(__ldg(b + k * es)) : T(0);
       if (k < R) val -= conv<T>(cF[k]);
 #pragma unroll
       for (int e = 0; e < R; e++) {
@@ -196,7 +223,7 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
     if (lane_ok) {
 #pragma unroll
       for (int k = 0; k < M; k++)
-        if (FULL || k < size) x[k] = conv<TOut>(v[k]);
+        if (FULL || k < size) x[k * es] = conv<TOut>(v[k]);
     }
   } else {
     float bh[M], bl[M], xh[M], xl[M], v[M];
@@ -209,7 +236,7 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
 #pragma unroll
     for (int k = 0; k < M; k++) {
       f2 s = {0.f, 0.f};
-      if (lane_ok && (FULL || k < size)) s = split_in(__ldg(b + k));
+      if (lane_ok && (FULL || k < size)) s = split_in(__ldg(b + k * es));
       // subtract the correction (zero on all but the edge rows) exactly
       f2 c = {0.f, 0.f};
       if (k < R) c = sF[k];
@@ -252,43 +279,69 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
     if (lane_ok) {
 #pragma unroll
       for (int k = 0; k < M; k++)
-        if (FULL || k < size) x[k] = (TOut)(f32_to_f64(xh[k]) + f32_to_f64(xl[k]));
+        if (FULL || k < size) x[k * es] = (TOut)(f32_to_f64(xh[k]) + f32_to_f64(xl[k]));
     }
   }
   // the segment's interface rows
-  if (threadIdx.x < R) ((TOut*)a.out)[row0 + threadIdx.x] = (TOut)xt_here[threadIdx.x];
+  if (LG == 1) {
+    if (threadIdx.x < R) ((TOut*)a.out)[row0 + threadIdx.x] = (TOut)xt_here[threadIdx.x];
+  } else if (i < R && line_ok) {
+    ((TOut*)a.out)[row0 + i * es] = (TOut)xt_here[i];
+  }
 }
 
-template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL>
-__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin, const int seg0) {
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG>
+__global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, const DevLineTables tin, const int seg0,
+                                                         const LongGeom gm) {
   extern __shared__ __align__(16) unsigned long long xbuf[];  // kCtaXchgSlots * blockDim slots
-  CtaXchg xch{xbuf, 0};
-  seg_item<R, M, MODE, TIn, TOut, FULL>(a, tin, seg0 + blockIdx.y, blockIdx.x, xch);
+  const int g = LG == 1 ? 0 : threadIdx.x % LG;
+  CtaXchgT<LG == 1 ? 0 : LG> xch{xbuf, 0, 1, g};
+  seg_item<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, seg0 + blockIdx.y, (int64_t)blockIdx.x * LG + g, xch);
 }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
+cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const LongGeom& gm,
+                        const DevLineTables& outer,
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
                         int* launches) {
   *launches = 0;
   if (a.p > 65535 || a.lines > 0x7fffffff) return cudaErrorInvalidValue;
-  const dim3 gs((unsigned)a.lines, (unsigned)a.p);
-  if (in64) long_ends_kernel<double><<<gs, 128, 0, s>>>(a);
-  else long_ends_kernel<float><<<gs, 128, 0, s>>>(a);
+  const bool tiled = gm.dir != 0;  // y/z lines: kLongLines adjacent lines per CTA
+  const int LG = tiled ? kLongLines : 1;
+  const unsigned tiles = (unsigned)((a.lines + LG - 1) / LG);
+  const dim3 gs(tiles, (unsigned)a.p);
+  if (tiled) {
+    if (in64) long_ends_kernel<double, kLongLines><<<gs, 128, 0, s>>>(a, gm);
+    else long_ends_kernel<float, kLongLines><<<gs, 128, 0, s>>>(a, gm);
+  } else {
+    if (in64) long_ends_kernel<double, 1><<<gs, 128, 0, s>>>(a, gm);
+    else long_ends_kernel<float, 1><<<gs, 128, 0, s>>>(a, gm);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ithreads = a.p < 1024 ? ((a.p + 31) / 32) * 32 : 1024;
   const size_t ismem = 2 * (size_t)a.p * a.r * sizeof(double);
+  static std::mutex imu;
   static size_t iconf = 0;
-  if (ismem > 48 * 1024 && ismem > iconf) {
-    e = cudaFuncSetAttribute(long_iface_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(long_iface_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-    if (e != cudaSuccess) return e;
-    iconf = ismem;
+  if (ismem > 48 * 1024) {
+    std::lock_guard<std::mutex> lock(imu);
+    if (ismem > iconf) {
+      const void* ks[4] = {(const void*)long_iface_kernel<double, false>, (const void*)long_iface_kernel<float, false>,
+                           (const void*)long_iface_kernel<double, true>, (const void*)long_iface_kernel<float, true>};
+      for (int k = 0; k < 4 && e == cudaSuccess; k++)
+        e = cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+      if (e != cudaSuccess) return e;
+      iconf = ismem;
+    }
   }
-  if (in64) long_iface_kernel<double><<<(unsigned)a.lines, ithreads, ismem, s>>>(a, outer);
-  else long_iface_kernel<float><<<(unsigned)a.lines, ithreads, ismem, s>>>(a, outer);
+  const unsigned nl = (unsigned)a.lines;
+  if (tiled) {
+    if (in64) long_iface_kernel<double, true><<<nl, ithreads, ismem, s>>>(a, outer, gm);
+    else long_iface_kernel<float, true><<<nl, ithreads, ismem, s>>>(a, outer, gm);
+  } else {
+    if (in64) long_iface_kernel<double, false><<<nl, ithreads, ismem, s>>>(a, outer, gm);
+    else long_iface_kernel<float, false><<<nl, ithreads, ismem, s>>>(a, outer, gm);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *launches = 2;
@@ -299,13 +352,27 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
     const DevLineTables& tin = part == 0 ? inner : *inner_small;
     const int seg0 = part == 0 ? 0 : nbig, nseg = part == 0 ? nbig : a.p - nbig;
     if (nseg <= 0) continue;
-    const dim3 g((unsigned)a.lines, (unsigned)nseg);
-    const int threads = ((tin.p + 31) / 32) * 32;
+    // x: one warp-multiple of inner partitions; y/z: a tile of lg lines x
+    // (inner partitions rounded up), a multiple of 32 threads as well: lg =
+    // kLongLines up to 64 inner partitions, half as many lines up to 128
+    const int lg = !tiled ? 1 : tin.p <= 512 / kLongLines ? kLongLines : kLongLines / 2;
+    const int rnd = 32 / lg;
+    const int threads = tiled ? lg * (((tin.p + rnd - 1) / rnd) * rnd) : ((tin.p + 31) / 32) * 32;
+    if (threads > 512) return cudaErrorInvalidConfiguration;
+    const dim3 g((unsigned)((a.lines + lg - 1) / lg), (unsigned)nseg);
     const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
-#define CBS_SEG(MO, RR, TI, TO)                                                                   \
-  do {                                                                                            \
-    if (full) long_seg_kernel<RR, 16, MO, TI, TO, true><<<g, threads, smem, s>>>(a, tin, seg0);    \
-    else long_seg_kernel<RR, 16, MO, TI, TO, false><<<g, threads, smem, s>>>(a, tin, seg0);       \
+#define CBS_SEG(MO, RR, TI, TO)                                                                              \
+  do {                                                                                                       \
+    if (lg == kLongLines) {                                                                                  \
+      if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, kLongLines><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
+      else long_seg_kernel<RR, 16, MO, TI, TO, false, kLongLines><<<g, threads, smem, s>>>(a, tin, seg0, gm);     \
+    } else if (lg > 1) {                                                                                     \
+      if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, kLongLines / 2><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
+      else long_seg_kernel<RR, 16, MO, TI, TO, false, kLongLines / 2><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
+    } else {                                                                                                 \
+      if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, 1><<<g, threads, smem, s>>>(a, tin, seg0, gm);          \
+      else long_seg_kernel<RR, 16, MO, TI, TO, false, 1><<<g, threads, smem, s>>>(a, tin, seg0, gm);             \
+    }                                                                                                        \
   } while (0)
     if (mode == kModeRefine) {
       if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }
@@ -406,7 +473,8 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
                    : d.precision == CBS_FP32_REFINE ? kModeRefine
                                                     : kModeRefineI64;
   int launches = 0;
-  cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->dev,
+  cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->lgeom,
+                              P->dev,
                               P->dev_inner, a.cbig < a.p ? &P->dev_inner_small : nullptr,
                               P->inner_full, (cudaStream_t)stream, &launches);
   if (e != cudaSuccess) return set_error(CBS_ERR_CUDA, std::string("long-line kernel launch: ") + cudaGetErrorString(e));

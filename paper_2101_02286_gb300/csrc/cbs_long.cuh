@@ -6,8 +6,12 @@
 
 namespace cbs {
 
+// Lines per CTA of the ends and segment kernels for y/z lines: a tile of
+// adjacent lines, so that every row of the tile is one contiguous run.
+constexpr int kLongLines = 8;
+
 struct LongArgs {
-  const void* in;     // b, lines x n (line-contiguous)
+  const void* in;     // b: the field (x-lines: lines x n, line-contiguous; see LongGeom)
   void* out;          // x, same layout, FP64 (or FP32 for FP32 mode)
   double* yb;         // [line][seg][2r]: y_i first r, then last r rows
   double* xt;         // [line][seg][r]: interface solution x~
@@ -19,6 +23,15 @@ struct LongArgs {
   int cbig, msmall;   // segments cbig.. have msmall rows
   int sweeps;
   double band[2 * kMaxR + 1];
+};
+
+// Geometry of the lines, passed to the kernels after their other arguments:
+// lines along dir (0 = x, 1 = y, 2 = z) of an (nx, ny, nz) field; es = row
+// stride in elements (1, nx or nx ny).  y-lines are numbered x + nx z and
+// z-lines x + nx y, so consecutive lines are adjacent in x.
+struct LongGeom {
+  int64_t nx, ny, es;
+  int dir;
 };
 
 }  // namespace cbs

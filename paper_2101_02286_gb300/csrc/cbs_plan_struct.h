@@ -13,6 +13,7 @@ using cbs::DevLineTables;
 using cbs::LineArgs;
 using cbs::LineTables;
 using cbs::LongArgs;
+using cbs::LongGeom;
 using cbs::VarArgs;
 
 struct cbs_batch {
@@ -40,6 +41,7 @@ struct cbs_plan {
   DevLineTables dev_inner, dev_inner_small;
   bool inner_full = false;            // every segment's bulk is a whole number of 16-row partitions
   LongArgs largs;
+  LongGeom lgeom;
   void* lbuf = nullptr;
   void* lbuf_small = nullptr;
   void* sbuf = nullptr;
@@ -53,7 +55,8 @@ cbs_status set_error(cbs_status s, const std::string& msg);
 void set_launch_count(int n);
 // inner_small: tables of the msmall-row segments (whole-16-row layout), or
 // null when every segment uses `inner`.
-cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& outer,
+cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const LongGeom& gm,
+                        const DevLineTables& outer,
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
                         int* launches);
 }  // namespace cbs

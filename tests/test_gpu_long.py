@@ -124,3 +124,97 @@ def test_long_more_lines_than_a_grid_dimension(cuda):
     got = x[0, pick].cpu().numpy()
     ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.LELE6_TRI["lhs"]), d[pick].astype(np.float64))
     assert oracle.rel_err(got, ref) < 1e-12
+
+
+# ---------------------------------------------------------------- y / z lines
+def _solve_dir(f, direction, lhs, segments, precision, sweeps=1, in_dtype=torch.float64):
+    plan = Plan(f.shape, direction, lhs=lhs, rhs=None, segments=segments, precision=precision, sweeps=sweeps,
+                in_dtype=in_dtype)
+    x = plan.solve(torch.from_numpy(np.ascontiguousarray(f)).to("cuda", in_dtype))
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert plan.status() == 0
+    plan.close()
+    return x.double().cpu().numpy(), info
+
+
+@pytest.mark.parametrize("direction", [1, 2])
+@pytest.mark.parametrize("precision,tol,sweeps", [("fp64", 1e-12, 1), ("fp32", 2e-5, 1), ("fp32_refine", 1e-12, 1),
+                                                  ("fp32_refine", 1e-12, 2), ("fp32_refine_i64", 1e-12, 1)])
+@pytest.mark.parametrize("lhs,n,p", [(W.LELE6_TRI["lhs"], 2048, 2), (W.LELE6_TRI["lhs"], 2050, 2),
+                                     (W.LELE6_TRI["lhs"], 3000, 3), (W.LELE6_TRI["lhs"], 4096, 7),
+                                     (W.PENTA10["lhs"], 2048, 2), (W.PENTA10["lhs"], 2052, 2),
+                                     (W.PENTA10["lhs"], 3000, 3), (W.PENTA10["lhs"], 1536, 2),
+                                     (W.LELE6_TRI["lhs"], 4096, 2), (W.PENTA10["lhs"], 3000, 2)])
+def test_long_y_z_lines(cuda, direction, precision, tol, sweeps, lhs, n, p):
+    # strided lines, a tile of 8 adjacent lines per CTA; line counts that
+    # are not a multiple of the tile (12 x 5 and 12 x 3 lines); whole
+    # 16-row inner partitions when n - p r is a multiple of 16 (2050 tri,
+    # 2052 penta), ragged ones otherwise; tiles of 8 lines up to 64 inner
+    # partitions (2048 / 2), of 4 lines above (4096 / 2, 3000 / 2)
+    if precision == "fp32_refine" and sweeps == 1 and lhs == W.PENTA10["lhs"]:
+        sweeps = 2  # the pentadiagonal system needs the second sweep for 1e-12
+    shape = (5, n, 12) if direction == 1 else (n, 3, 12)
+    rng = np.random.default_rng(n + 10 * p + direction)
+    f = rng.standard_normal(shape)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    x, info = _solve_dir(f, direction, lhs, p, precision, sweeps, dt)
+    assert info["kernel"] == 1 and info["segments"] == p
+    assert info["lines"] == (60 if direction == 1 else 36)
+    src = f.astype(np.float32).astype(np.float64) if dt == torch.float32 else f
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, lhs), src, axis=2 - direction)
+    assert oracle.rel_err(x, ref) < tol
+
+
+@pytest.mark.parametrize("direction", [1, 2])
+def test_long_y_z_fp32_input(cuda, direction):
+    # FP32 right-hand side, FP64 solution (the long-line precision workload's
+    # element types) along y and z
+    n = 4096
+    shape = (3, n, 16) if direction == 1 else (n, 2, 16)
+    f = np.random.default_rng(40 + direction).standard_normal(shape).astype(np.float32)
+    x, _ = _solve_dir(f, direction, W.PENTA10["lhs"], 4, "fp32_refine", 2, torch.float32)
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), f.astype(np.float64), axis=2 - direction)
+    assert oracle.rel_err(x, ref) < 1e-12
+
+
+def test_long_y_z_segment_limit(cuda):
+    # y/z segments hold at most 128 inner partitions of 16 rows: one segment
+    # of 4096 rows is refused, the default segment count fits
+    from paper_2101_02286_gb300 import abi
+    f = np.zeros((2, 4096, 8))
+    with pytest.raises(abi.CbsError) as e:
+        Plan(f.shape, 1, lhs=W.LELE6_TRI["lhs"], rhs=None, segments=1, precision="fp64")
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+    plan = Plan(f.shape, 1, lhs=W.LELE6_TRI["lhs"], rhs=None, precision="fp64")
+    assert plan.info()["kernel"] == 1 and plan.info()["segments"] == 4
+    plan.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("direction", [1, 2])
+def test_paper_workload_y_z_sampled(cuda, direction):
+    # the paper's workload along y and z: 256^2 lines of 8192, tridiagonal
+    # alpha = 1/3, p = 8 and p = 7, checked on sampled lines
+    shape = (256, 8192, 256) if direction == 1 else (8192, 256, 256)
+    rng = np.random.default_rng(50 + direction)
+    f = rng.standard_normal(shape)
+    fi = torch.from_numpy(f).cuda()
+    lhs = W.LELE6_TRI["lhs"]
+    for p in (8, 7):
+        plan = Plan(shape, direction, lhs=lhs, rhs=None, segments=p, precision="fp32_refine")
+        x = plan.solve(fi)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        plan.close()
+        xs = x.cpu().numpy()
+        del x
+        ii = rng.integers(0, 256, size=(8, 2))
+        if direction == 1:
+            lines = np.stack([f[i, :, j] for i, j in ii])
+            got = np.stack([xs[i, :, j] for i, j in ii])
+        else:
+            lines = np.stack([f[:, i, j] for i, j in ii])
+            got = np.stack([xs[:, i, j] for i, j in ii])
+        ref = oracle.solve_cyclic(oracle.toeplitz_bands(8192, lhs), lines)
+        assert oracle.rel_err(got, ref) < 1e-12, p
