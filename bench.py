@@ -336,13 +336,14 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
 
     # the paper's single-GPU workload: 256^2 lines of 8192 along x, y and z
     # (fields 8192 x 256 x 256, 256 x 8192 x 256, 256 x 256 x 8192), cyclic
-    # tridiagonal alpha = 1/3, right-hand side given, p = 8 and 7 (2^n - 1);
+    # tridiagonal alpha = 1/3, right-hand side given; x: p = 8 and 7 (2^n - 1),
+    # y/z: p = 16 (the default: 512-row segments, tiles of 8 strided lines);
     # the three fields share one buffer of random values
     dpx = np.random.default_rng(20).standard_normal(256 * 256 * 8192)
     di = torch.from_numpy(dpx).to(dev)
     do = torch.empty_like(di)
     for direction, prec, p in ((0, "fp32_refine", 8), (0, "fp32_refine", 7), (0, "fp64", 8),
-                               (1, "fp32_refine", 8), (1, "fp64", 8), (2, "fp32_refine", 8), (2, "fp64", 8)):
+                               (1, "fp32_refine", 16), (1, "fp64", 16), (2, "fp32_refine", 16), (2, "fp64", 16)):
         shape = [(256, 256, 8192), (256, 8192, 256), (8192, 256, 256)][direction]  # (nz, ny, nx)
         pl = Plan(shape, direction, lhs=W.LELE6_TRI["lhs"], rhs=None, precision=prec, segments=p)
         dv, ov = di.view(shape), do.view(shape)

@@ -1154,7 +1154,7 @@ template <int R, int M, int MODE, int KS, typename TIn, typename TOut, bool FULL
           bool PIPE = false, int ST = 0>
 __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables& t, const void* in_ptr,
                                           void* out_ptr, const int tx, const int to, unsigned char* smem_raw,
-                                          const TIn* pslots = nullptr) {
+                                          const TIn* pslots = nullptr, int* xflip = nullptr) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
   constexpr bool DIRECT = LAYOUT == kDirectX, DSTR = LAYOUT == kDirectStrided;
@@ -1253,6 +1253,12 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
 
   TOut xo[M];
   auto xch = make_xchg<DSTR>(pw, smem_raw, g);
+  // a CTA walking several tiles continues the exchange buffers' alternation
+  // across tiles: the first round of a tile then never writes the buffer the
+  // previous tile's last round is still being read from
+  if constexpr (DSTR) {
+    if (xflip) xch.flip = *xflip;
+  }
   using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;  // interface of the FP32 solves
   if constexpr (!refine_mode(MODE)) {
     T v[M];
@@ -1502,6 +1508,9 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     }
   }
 
+  if constexpr (DSTR) {
+    if (xflip) *xflip = xch.flip;
+  }
   // ---- write back
   if constexpr (DSTR) {
     if (ok) {
@@ -1579,7 +1588,7 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
   const size_t xbytes = LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * bd * sizeof(unsigned long long) : 0;
   TIn* slots = reinterpret_cast<TIn*>(smem_raw + xbytes);
   const ThreadPart tp = thread_part<M, true, LAYOUT>(t);
-  int tile = blockIdx.x, buf = 0;
+  int tile = blockIdx.x, buf = 0, xflip = 0;
   if (tile < ntiles) prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, tile, slots, 0);
   for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
     const int next = tile + gridDim.x;
@@ -1591,7 +1600,7 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
     }
     const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
     line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true, ST>(a, t, a.in, a.out, tx, to, smem_raw,
-                                                               slots + (size_t)buf * NS * bd);
+                                                               slots + (size_t)buf * NS * bd, &xflip);
   }
 }
 

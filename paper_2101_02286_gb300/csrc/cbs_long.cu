@@ -174,12 +174,13 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 // inner partition has exactly M rows (whole-16-row layout): sizes are
 // compile-time and the refinement uses the paired residual.
 // One (segment, line) item, solved by the whole CTA.
-// LG: lines per CTA (1: x-lines, thread i = inner partition i; kLongLines or
-// kLongLines / 2: y/z lines, thread = (inner partition i, line g) with g
-// fastest).
-template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG, typename X>
+// LG: lines per CTA (1: x-lines, thread i = inner partition i; 2, 4 or 8:
+// y/z lines, thread = (inner partition i, line g) with g fastest).
+// PIPE: the bulk rows were copied ahead into this thread's shared-memory
+// slots (row k at pslot[k * blockDim.x]) by the persistent kernel below.
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG, typename X, bool PIPE = false>
 __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables& tin, const LongGeom& gm,
-                                         const int seg, const int64_t line, X& xch) {
+                                         const int seg, const int64_t line, X& xch, const TIn* pslot = nullptr) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   const int i = LG == 1 ? threadIdx.x : threadIdx.x / LG, P = tin.p;
   const bool line_ok = LG == 1 || line < a.lines;
@@ -207,7 +208,8 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
     T v[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-      T val = (lane_ok && (FULL || k < size)) ? conv<T>(__ldg(b + k * es)) : T(0);
+      T val = T(0);
+      if (lane_ok && (FULL || k < size)) val = conv<T>(PIPE ? pslot[k * blockDim.x] : __ldg(b + k * es));
       if (k < R) val -= conv<T>(cF[k]);
 #pragma unroll
       for (int e = 0; e < R; e++) {
@@ -236,7 +238,7 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
 #pragma unroll
     for (int k = 0; k < M; k++) {
       f2 s = {0.f, 0.f};
-      if (lane_ok && (FULL || k < size)) s = split_in(__ldg(b + k * es));
+      if (lane_ok && (FULL || k < size)) s = split_in(PIPE ? pslot[k * blockDim.x] : __ldg(b + k * es));
       // subtract the correction (zero on all but the edge rows) exactly
       f2 c = {0.f, 0.f};
       if (k < R) c = sF[k];
@@ -299,7 +301,112 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
   seg_item<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, seg0 + blockIdx.y, (int64_t)blockIdx.x * LG + g, xch);
 }
 
+// Persistent, software-pipelined segment kernel for y/z tiles: each CTA
+// walks the items (tile, segment) = it % tiles, seg0 + it / tiles for it =
+// blockIdx.x, + gridDim.x, ..., and issues the asynchronous copies of the next
+// item's bulk rows into the other half of a double buffer of thread-private
+// shared-memory slots before solving the current one, so that the strided
+// HBM reads overlap the arithmetic (the plain kernel is bound by load
+// latency: 16 warps per SM at 128 registers).  Shared memory: the message
+// buffer (kCtaXchgSlots slots per thread), then 2 x M slots of TIn per thread.
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG>
+__device__ __forceinline__ void seg_prefetch(const LongArgs& a, const DevLineTables& tin, const LongGeom& gm,
+                                             const int it, const int tiles, const int seg0, TIn* slot0) {
+  const int i = threadIdx.x / LG, g = threadIdx.x % LG;
+  const int seg = seg0 + it / tiles;
+  const int64_t line = (int64_t)(it % tiles) * LG + g;
+  if (i < tin.p && line < a.lines) {
+    int start = i * M, size = M;
+    if (!FULL) partition_of(tin, i, start, size);
+    const int64_t es = gm.es;
+    const TIn* b = (const TIn*)a.in + long_base(a, gm, line) + (seg_start(a, seg) + R + start) * es;
+#pragma unroll
+    for (int k = 0; k < M; k++)
+      if (FULL || k < size) cp_async<sizeof(TIn)>(slot0 + k * blockDim.x, b + k * es);
+  }
+  cp_async_commit();
+}
+
+template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG>
+__global__ void __launch_bounds__(256, 2) long_seg_pipe_kernel(const LongArgs a, const DevLineTables tin,
+                                                               const int seg0, const LongGeom gm, const int tiles,
+                                                               const int items) {
+  extern __shared__ __align__(16) unsigned long long xbuf[];
+  const int bd = blockDim.x, g = threadIdx.x % LG;
+  TIn* slots = reinterpret_cast<TIn*>(xbuf + (size_t)kCtaXchgSlots * bd);
+  CtaXchgT<LG> xch{xbuf, 0, 1, g};  // one exchanger for every item: the buffers keep alternating
+  int it = blockIdx.x, buf = 0;
+  if (it < items) seg_prefetch<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, it, tiles, seg0, slots + threadIdx.x);
+  for (; it < items; it += gridDim.x, buf ^= 1) {
+    const int next = it + gridDim.x;
+    if (next < items) {
+      seg_prefetch<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, next, tiles, seg0,
+                                                    slots + (size_t)(buf ^ 1) * M * bd + threadIdx.x);
+      cp_async_wait<1>();  // this item's copies are done, the next item's stay in flight
+    } else {
+      cp_async_wait<0>();
+    }
+    seg_item<R, M, MODE, TIn, TOut, FULL, LG, CtaXchgT<LG>, true>(
+        a, tin, gm, seg0 + it / tiles, (int64_t)(it % tiles) * LG + g, xch, slots + (size_t)buf * M * bd + threadIdx.x);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
+// Persistent launch of long_seg_pipe_kernel: one CTA per resident slot
+// (occupancy x SMs) over the tiles x nseg items of segments seg0..
+template <int R, int MODE, typename TIn, typename TOut, bool FULL, int LG>
+cudaError_t launch_seg_pipe(const LongArgs& a, const DevLineTables& tin, int seg0, int nseg, const LongGeom& gm,
+                            int threads, cudaStream_t s) {
+  constexpr int M = 16;
+  const int64_t tiles = (a.lines + LG - 1) / LG, items = tiles * nseg;
+  if (items > 0x7fffffff || threads > 256) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) + 2 * (size_t)M * threads * sizeof(TIn);
+  auto kern = long_seg_pipe_kernel<R, M, MODE, TIn, TOut, FULL, LG>;
+  // per instantiation: largest dynamic shared memory configured, and the
+  // occupancy of the last (threads, smem) launched
+  static std::mutex mu;
+  static size_t attr_smem = 0, occ_smem = 0;
+  static int occ_threads = 0, per_sm = 0;
+  int blocks_per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cudaError_t e;
+    if (smem > 48 * 1024 && smem > attr_smem) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_smem = smem;
+    }
+    if (occ_smem != smem || occ_threads != threads) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+      if (e != cudaSuccess) return e;
+      occ_smem = smem;
+      occ_threads = threads;
+    }
+    blocks_per_sm = per_sm;
+  }
+  if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t want = (int64_t)blocks_per_sm * sm_count();
+  const unsigned blocks = (unsigned)(items < want ? items : want);
+  kern<<<blocks, threads, smem, s>>>(a, tin, seg0, gm, (int)tiles, (int)items);
+  return cudaGetLastError();
+}
+
+// y/z tiles: the pipelined kernel for the FP32 modes (load-latency bound
+// otherwise); FP64 is bound by its FP64 pipe and runs the plain kernel (the
+// pipelined one measured a few per cent slower there).
+template <int R, int MODE, typename TIn, typename TOut, bool FULL, int LG>
+cudaError_t launch_seg_tiled(const LongArgs& a, const DevLineTables& tin, int seg0, int nseg, const LongGeom& gm,
+                             int threads, cudaStream_t s) {
+  if constexpr (MODE == kModeF64) {
+    const dim3 g((unsigned)((a.lines + LG - 1) / LG), (unsigned)nseg);
+    const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
+    long_seg_kernel<R, 16, MODE, TIn, TOut, FULL, LG><<<g, threads, smem, s>>>(a, tin, seg0, gm);
+    return cudaGetLastError();
+  } else {
+    return launch_seg_pipe<R, MODE, TIn, TOut, FULL, LG>(a, tin, seg0, nseg, gm, threads, s);
+  }
+}
+
 cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const LongGeom& gm,
                         const DevLineTables& outer,
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,
@@ -353,26 +460,29 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
     const int seg0 = part == 0 ? 0 : nbig, nseg = part == 0 ? nbig : a.p - nbig;
     if (nseg <= 0) continue;
     // x: one warp-multiple of inner partitions; y/z: a tile of lg lines x
-    // (inner partitions rounded up), a multiple of 32 threads as well: lg =
-    // kLongLines up to 64 inner partitions, half as many lines up to 128
-    const int lg = !tiled ? 1 : tin.p <= 512 / kLongLines ? kLongLines : kLongLines / 2;
+    // (inner partitions rounded up), a multiple of 32 threads as well, with
+    // lg the widest of 8, 4, 2 lines that keeps the CTA at <= 256 threads
+    // (two CTAs per SM at 128 registers: one loads while the other computes)
+    int lg = 1;
+    if (tiled) {
+      lg = kLongLines;
+      while (lg > 2 && lg * (((tin.p + 32 / lg - 1) / (32 / lg)) * (32 / lg)) > 256) lg /= 2;
+    }
     const int rnd = 32 / lg;
     const int threads = tiled ? lg * (((tin.p + rnd - 1) / rnd) * rnd) : ((tin.p + 31) / 32) * 32;
     if (threads > 512) return cudaErrorInvalidConfiguration;
     const dim3 g((unsigned)((a.lines + lg - 1) / lg), (unsigned)nseg);
     const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
-#define CBS_SEG(MO, RR, TI, TO)                                                                              \
-  do {                                                                                                       \
-    if (lg == kLongLines) {                                                                                  \
-      if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, kLongLines><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
-      else long_seg_kernel<RR, 16, MO, TI, TO, false, kLongLines><<<g, threads, smem, s>>>(a, tin, seg0, gm);     \
-    } else if (lg > 1) {                                                                                     \
-      if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, kLongLines / 2><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
-      else long_seg_kernel<RR, 16, MO, TI, TO, false, kLongLines / 2><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
-    } else {                                                                                                 \
-      if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, 1><<<g, threads, smem, s>>>(a, tin, seg0, gm);          \
-      else long_seg_kernel<RR, 16, MO, TI, TO, false, 1><<<g, threads, smem, s>>>(a, tin, seg0, gm);             \
-    }                                                                                                        \
+#define CBS_SEGP(MO, RR, TI, TO, LGV)                                                                  \
+  (full ? launch_seg_tiled<RR, MO, TI, TO, true, LGV>(a, tin, seg0, nseg, gm, threads, s)              \
+        : launch_seg_tiled<RR, MO, TI, TO, false, LGV>(a, tin, seg0, nseg, gm, threads, s))
+#define CBS_SEG(MO, RR, TI, TO)                                                                        \
+  do {                                                                                                 \
+    if (lg == 8) e = CBS_SEGP(MO, RR, TI, TO, 8);                                                      \
+    else if (lg == 4) e = CBS_SEGP(MO, RR, TI, TO, 4);                                                 \
+    else if (lg == 2) e = CBS_SEGP(MO, RR, TI, TO, 2);                                                 \
+    else if (full) long_seg_kernel<RR, 16, MO, TI, TO, true, 1><<<g, threads, smem, s>>>(a, tin, seg0, gm); \
+    else long_seg_kernel<RR, 16, MO, TI, TO, false, 1><<<g, threads, smem, s>>>(a, tin, seg0, gm);        \
   } while (0)
     if (mode == kModeRefine) {
       if (R == 1) { if (in64) CBS_SEG(kModeRefine, 1, double, double); else CBS_SEG(kModeRefine, 1, float, double); }
@@ -388,6 +498,7 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
       else { if (in64) CBS_SEG(kModeF32, 2, double, float); else CBS_SEG(kModeF32, 2, float, float); }
     }
 #undef CBS_SEG
+#undef CBS_SEGP
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*launches;

@@ -145,13 +145,16 @@ def _solve_dir(f, direction, lhs, segments, precision, sweeps=1, in_dtype=torch.
                                      (W.LELE6_TRI["lhs"], 3000, 3), (W.LELE6_TRI["lhs"], 4096, 7),
                                      (W.PENTA10["lhs"], 2048, 2), (W.PENTA10["lhs"], 2052, 2),
                                      (W.PENTA10["lhs"], 3000, 3), (W.PENTA10["lhs"], 1536, 2),
-                                     (W.LELE6_TRI["lhs"], 4096, 2), (W.PENTA10["lhs"], 3000, 2)])
+                                     (W.LELE6_TRI["lhs"], 4096, 2), (W.PENTA10["lhs"], 3000, 2),
+                                     (W.LELE6_TRI["lhs"], 2048, 4), (W.LELE6_TRI["lhs"], 2052, 4),
+                                     (W.PENTA10["lhs"], 2052, 4)])
 def test_long_y_z_lines(cuda, direction, precision, tol, sweeps, lhs, n, p):
     # strided lines, a tile of 8 adjacent lines per CTA; line counts that
     # are not a multiple of the tile (12 x 5 and 12 x 3 lines); whole
     # 16-row inner partitions when n - p r is a multiple of 16 (2050 tri,
-    # 2052 penta), ragged ones otherwise; tiles of 8 lines up to 64 inner
-    # partitions (2048 / 2), of 4 lines above (4096 / 2, 3000 / 2)
+    # 2052 penta, 2052 / 4 tri), ragged ones otherwise; tiles of 8 lines up
+    # to 32 inner partitions (2048 / 4), of 4 up to 64 (2048 / 2), of 2 up to
+    # 128 (4096 / 2, 3000 / 2)
     if precision == "fp32_refine" and sweeps == 1 and lhs == W.PENTA10["lhs"]:
         sweeps = 2  # the pentadiagonal system needs the second sweep for 1e-12
     shape = (5, n, 12) if direction == 1 else (n, 3, 12)
@@ -187,7 +190,7 @@ def test_long_y_z_segment_limit(cuda):
         Plan(f.shape, 1, lhs=W.LELE6_TRI["lhs"], rhs=None, segments=1, precision="fp64")
     assert e.value.status == abi.CBS_ERR_UNSUPPORTED
     plan = Plan(f.shape, 1, lhs=W.LELE6_TRI["lhs"], rhs=None, precision="fp64")
-    assert plan.info()["kernel"] == 1 and plan.info()["segments"] == 4
+    assert plan.info()["kernel"] == 1 and plan.info()["segments"] == 8
     plan.close()
 
 
