@@ -326,8 +326,9 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   const bool tiled = d->direction != 0;
   const int max_inner = tiled ? 1024 / kLongLines : 512;
   int p = d->segments;
-  if (!p) {  // segments of about 4096 rows (x), 512 (y/z: tiles of 8 lines x 32 inner partitions)
-    p = tiled ? (n + 511) / 512 : (n + 4095) / 4096;
+  if (!p) {  // segments of about 512 rows (y/z: tiles of 8 lines x 32 inner partitions), 1024 (x, n <= 2^16),
+             // 4096 (longer x-lines)
+    p = tiled ? (n + 511) / 512 : n <= 65536 ? (n + 1023) / 1024 : (n + 4095) / 4096;
     if ((n - (int64_t)p * r) % 16 != 0)
       while (p < n && n % p) p++;
   }

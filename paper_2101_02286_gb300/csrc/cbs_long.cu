@@ -100,6 +100,48 @@ __global__ void __launch_bounds__(128) long_ends_kernel(const LongArgs a, const 
   }
 }
 
+// x-lines: one warp per (line, segment) item, 8 items per CTA; lane j reads
+// rows j, j + 32, ... of both ends (contiguous) and the sums are reduced with
+// shuffles.  A CTA per item spent more time launching and reducing than
+// reading (K ~ 50 rows per end).
+template <typename TIn>
+__global__ void __launch_bounds__(256) long_ends_warp_kernel(const LongArgs a, const int64_t items) {
+  const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (item >= items) return;  // whole warps: no barrier below
+  const int lane = threadIdx.x & 31;
+  const int64_t line = item / a.p;
+  const int seg = (int)(item - line * a.p);
+  const int r = a.r, N = seg_rows(a, seg) - r;
+  const TIn* b = (const TIn*)a.in + line * a.n + seg_start(a, seg) + r;  // first bulk row
+  double accF[kMaxR], accL[kMaxR];
+#pragma unroll
+  for (int q = 0; q < kMaxR; q++) accF[q] = accL[q] = 0.0;
+  for (int j = lane; j < a.K; j += 32) {
+    const double bf = (double)__ldg(b + j), bl = (double)__ldg(b + N - 1 - j);
+#pragma unroll
+    for (int q = 0; q < kMaxR; q++)
+      if (q < r) {
+        accF[q] += __ldg(a.G + q * a.K + j) * bf;
+        accL[q] += __ldg(a.G + (r - 1 - q) * a.K + j) * bl;  // persymmetry of D^{-1}
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < kMaxR; q++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      accF[q] += __shfl_xor_sync(kFull, accF[q], o);
+      accL[q] += __shfl_xor_sync(kFull, accL[q], o);
+    }
+  }
+  double* yb = a.yb + item * 2 * r;  // item = line * p + seg
+#pragma unroll
+  for (int q = 0; q < kMaxR; q++)
+    if (q < r && lane == 0) {
+      yb[q] = accF[q];
+      yb[r + q] = accL[q];
+    }
+}
+
 // ---------------------------------------------------------------- 2. interface
 template <typename TIn, bool STR>
 __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, const DevLineTables t, const LongGeom gm) {
@@ -176,11 +218,12 @@ __global__ void __launch_bounds__(1024) long_iface_kernel(const LongArgs a, cons
 // One (segment, line) item, solved by the whole CTA.
 // LG: lines per CTA (1: x-lines, thread i = inner partition i; 2, 4 or 8:
 // y/z lines, thread = (inner partition i, line g) with g fastest).
-// PIPE: the bulk rows were copied ahead into this thread's shared-memory
-// slots (row k at pslot[k * blockDim.x]) by the persistent kernel below.
+// PIPE: the bulk rows were copied ahead into shared-memory slots (this
+// thread's row k at pslot[k * pstride]) by the persistent kernel below.
 template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG, typename X, bool PIPE = false>
 __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables& tin, const LongGeom& gm,
-                                         const int seg, const int64_t line, X& xch, const TIn* pslot = nullptr) {
+                                         const int seg, const int64_t line, X& xch, const TIn* pslot = nullptr,
+                                         const int pstride = 0) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   const int i = LG == 1 ? threadIdx.x : threadIdx.x / LG, P = tin.p;
   const bool line_ok = LG == 1 || line < a.lines;
@@ -209,7 +252,7 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
 #pragma unroll
     for (int k = 0; k < M; k++) {
       T val = T(0);
-      if (lane_ok && (FULL || k < size)) val = conv<T>(PIPE ? pslot[k * blockDim.x] : __ldg(b + k * es));
+      if (lane_ok && (FULL || k < size)) val = conv<T>(PIPE ? pslot[k * pstride] : __ldg(b + k * es));
       if (k < R) val -= conv<T>(cF[k]);
 #pragma unroll
       for (int e = 0; e < R; e++) {
@@ -238,7 +281,7 @@ __device__ __forceinline__ void seg_item(const LongArgs& a, const DevLineTables&
 #pragma unroll
     for (int k = 0; k < M; k++) {
       f2 s = {0.f, 0.f};
-      if (lane_ok && (FULL || k < size)) s = split_in(PIPE ? pslot[k * blockDim.x] : __ldg(b + k * es));
+      if (lane_ok && (FULL || k < size)) s = split_in(PIPE ? pslot[k * pstride] : __ldg(b + k * es));
       // subtract the correction (zero on all but the edge rows) exactly
       f2 c = {0.f, 0.f};
       if (k < R) c = sF[k];
@@ -309,11 +352,13 @@ __global__ void __launch_bounds__(512, 1) long_seg_kernel(const LongArgs a, cons
 // HBM reads overlap the arithmetic (the plain kernel is bound by load
 // latency: 16 warps per SM at 128 registers).  Shared memory: the message
 // buffer (kCtaXchgSlots slots per thread), then 2 x M slots of TIn per thread.
+// Slots of one buffer: thread t's row k at sbuf[k * blockDim + t]; each thread
+// copies its own rows (a tile row is one contiguous run of LG elements).
 template <int R, int M, int MODE, typename TIn, typename TOut, bool FULL, int LG>
 __device__ __forceinline__ void seg_prefetch(const LongArgs& a, const DevLineTables& tin, const LongGeom& gm,
-                                             const int it, const int tiles, const int seg0, TIn* slot0) {
-  const int i = threadIdx.x / LG, g = threadIdx.x % LG;
+                                             const int it, const int tiles, const int seg0, TIn* sbuf) {
   const int seg = seg0 + it / tiles;
+  const int i = threadIdx.x / LG, g = threadIdx.x % LG;
   const int64_t line = (int64_t)(it % tiles) * LG + g;
   if (i < tin.p && line < a.lines) {
     int start = i * M, size = M;
@@ -322,7 +367,7 @@ __device__ __forceinline__ void seg_prefetch(const LongArgs& a, const DevLineTab
     const TIn* b = (const TIn*)a.in + long_base(a, gm, line) + (seg_start(a, seg) + R + start) * es;
 #pragma unroll
     for (int k = 0; k < M; k++)
-      if (FULL || k < size) cp_async<sizeof(TIn)>(slot0 + k * blockDim.x, b + k * es);
+      if (FULL || k < size) cp_async<sizeof(TIn)>(sbuf + k * blockDim.x + threadIdx.x, b + k * es);
   }
   cp_async_commit();
 }
@@ -336,18 +381,18 @@ __global__ void __launch_bounds__(256, 2) long_seg_pipe_kernel(const LongArgs a,
   TIn* slots = reinterpret_cast<TIn*>(xbuf + (size_t)kCtaXchgSlots * bd);
   CtaXchgT<LG> xch{xbuf, 0, 1, g};  // one exchanger for every item: the buffers keep alternating
   int it = blockIdx.x, buf = 0;
-  if (it < items) seg_prefetch<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, it, tiles, seg0, slots + threadIdx.x);
+  if (it < items) seg_prefetch<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, it, tiles, seg0, slots);
   for (; it < items; it += gridDim.x, buf ^= 1) {
     const int next = it + gridDim.x;
     if (next < items) {
-      seg_prefetch<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, next, tiles, seg0,
-                                                    slots + (size_t)(buf ^ 1) * M * bd + threadIdx.x);
+      seg_prefetch<R, M, MODE, TIn, TOut, FULL, LG>(a, tin, gm, next, tiles, seg0, slots + (size_t)(buf ^ 1) * M * bd);
       cp_async_wait<1>();  // this item's copies are done, the next item's stay in flight
     } else {
       cp_async_wait<0>();
     }
-    seg_item<R, M, MODE, TIn, TOut, FULL, LG, CtaXchgT<LG>, true>(
-        a, tin, gm, seg0 + it / tiles, (int64_t)(it % tiles) * LG + g, xch, slots + (size_t)buf * M * bd + threadIdx.x);
+    seg_item<R, M, MODE, TIn, TOut, FULL, LG, CtaXchgT<LG>, true>(a, tin, gm, seg0 + it / tiles,
+                                                                  (int64_t)(it % tiles) * LG + g, xch,
+                                                                  slots + (size_t)buf * M * bd + threadIdx.x, bd);
   }
 }
 
@@ -421,8 +466,11 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
     if (in64) long_ends_kernel<double, kLongLines><<<gs, 128, 0, s>>>(a, gm);
     else long_ends_kernel<float, kLongLines><<<gs, 128, 0, s>>>(a, gm);
   } else {
-    if (in64) long_ends_kernel<double, 1><<<gs, 128, 0, s>>>(a, gm);
-    else long_ends_kernel<float, 1><<<gs, 128, 0, s>>>(a, gm);
+    const int64_t items = a.lines * a.p;
+    if ((items + 7) / 8 > 0x7fffffff) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((items + 7) / 8);
+    if (in64) long_ends_warp_kernel<double><<<blocks, 256, 0, s>>>(a, items);
+    else long_ends_warp_kernel<float><<<blocks, 256, 0, s>>>(a, items);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -469,7 +517,7 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
       while (lg > 2 && lg * (((tin.p + 32 / lg - 1) / (32 / lg)) * (32 / lg)) > 256) lg /= 2;
     }
     const int rnd = 32 / lg;
-    const int threads = tiled ? lg * (((tin.p + rnd - 1) / rnd) * rnd) : ((tin.p + 31) / 32) * 32;
+    const int threads = lg > 1 ? lg * (((tin.p + rnd - 1) / rnd) * rnd) : ((tin.p + 31) / 32) * 32;
     if (threads > 512) return cudaErrorInvalidConfiguration;
     const dim3 g((unsigned)((a.lines + lg - 1) / lg), (unsigned)nseg);
     const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long);
