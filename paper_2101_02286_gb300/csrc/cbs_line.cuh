@@ -1057,8 +1057,27 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //    positions of 32 / kStridedLines partitions (full 32-byte sectors, no
 //    staging); the interface messages between partitions then cross warps
 //    through shared memory.  The CTA has kStridedLines x pw threads.
-constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2;
+//  kStridedWarp: y/z lines of 32 partitions in the pipelined kernel.  The
+//    rows are copied with the line-fastest mapping of kDirectStrided (same
+//    global access pattern) but into the shared-memory slots of the thread
+//    that solves them, where a warp holds one line (lane = partition), so the
+//    interface messages are warp shuffles as for x-lines; the results go back
+//    through the same slots and leave with the line-fastest mapping.
+constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2, kStridedWarp = 3;
 constexpr int kStridedLines = 8;
+__host__ __device__ constexpr bool strided_layout(int layout) {
+  return layout == kDirectStrided || layout == kStridedWarp;
+}
+
+// Column of solving thread c in the pipelined kernel's slot rows.  In
+// kStridedWarp (32 lanes per line, c = 32 g + i) the lanes of line g are
+// permuted (i ^ 2g): the copies of one warp (8 lines x 4 partitions) and the
+// reads of one line then fall on distinct banks in each half-warp.
+template <int LAYOUT>
+__device__ __forceinline__ int slot_col(int c) {
+  if constexpr (LAYOUT == kStridedWarp) return c ^ (((c >> 5) & 7) << 1);
+  else return c;
+}
 
 // Exchanger of the interface messages for a layout: warp shuffles when a
 // warp holds a whole line, shared memory otherwise (strided layout: partition
@@ -1072,20 +1091,20 @@ __device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int offse
 // This thread's own rows from the prefetch slots (layout of prefetch_rows;
 // VEC: 16-byte units read back with 16-byte shared loads).
 template <int M, typename TIn, bool VEC>
-__device__ __forceinline__ void pipe_rows(const TIn* slots, TIn (&v)[M]) {
+__device__ __forceinline__ void pipe_rows(const TIn* slots, TIn (&v)[M], const int col) {
   const int bd = blockDim.x;
   if constexpr (VEC && (M % (16 / sizeof(TIn))) == 0) {
     constexpr int V = 16 / sizeof(TIn);
 #pragma unroll
     for (int u = 0; u < M / V; u++) {
-      const float4 q = *reinterpret_cast<const float4*>(slots + ((size_t)u * bd + threadIdx.x) * V);
+      const float4 q = *reinterpret_cast<const float4*>(slots + ((size_t)u * bd + col) * V);
       const TIn* e = reinterpret_cast<const TIn*>(&q);
 #pragma unroll
       for (int j = 0; j < V; j++) v[u * V + j] = e[j];
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < M; k++) v[k] = slots[(size_t)k * bd + threadIdx.x];
+    for (int k = 0; k < M; k++) v[k] = slots[(size_t)k * bd + col];
   }
 }
 
@@ -1157,12 +1176,13 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
                                           const TIn* pslots = nullptr, int* xflip = nullptr) {
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
-  constexpr bool DIRECT = LAYOUT == kDirectX, DSTR = LAYOUT == kDirectStrided;
-  using TW = typename std::conditional<DIRECT || DSTR, TIn, TT>::type;  // element type of the gathered window
+  constexpr bool DIRECT = LAYOUT == kDirectX, DSTR = LAYOUT == kDirectStrided, SWARP = LAYOUT == kStridedWarp;
+  static_assert(!SWARP || (PIPE && FULL), "kStridedWarp: pipelined whole-size partitions only");
+  using TW = typename std::conditional<DIRECT || DSTR || SWARP, TIn, TT>::type;  // element type of the gathered window
   constexpr int KA = KS > 0 ? KS : 1;  // halo array size (KS = 0 compiles no stencil)
   TT* S = reinterpret_cast<TT*>(smem_raw);
   const int pw = t.pw;
-  const int TL = DSTR ? kStridedLines : blockDim.x / pw;
+  const int TL = strided_layout(LAYOUT) ? kStridedLines : blockDim.x / pw;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
   const int nl = tr.nl;
   const ThreadPart tp = thread_part<M, FULL, LAYOUT>(t);
@@ -1172,9 +1192,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   const int n = t.n;
   TT* SL = S + g * t.lsz;
   // direct layouts: row 0 of this thread's line; row r at gin[r * es]
-  const int64_t es = DSTR ? tr.es : 1;
-  const TIn* gin = (const TIn*)in_ptr + tr.base + (DSTR ? (int64_t)g : (int64_t)g * n);
-  TOut* gout = (TOut*)out_ptr + tr.base + (DSTR ? (int64_t)g : (int64_t)g * n);
+  const int64_t es = strided_layout(LAYOUT) ? tr.es : 1;
+  const TIn* gin = (const TIn*)in_ptr + tr.base + (strided_layout(LAYOUT) ? (int64_t)g : (int64_t)g * n);
+  TOut* gout = (TOut*)out_ptr + tr.base + (strided_layout(LAYOUT) ? (int64_t)g : (int64_t)g * n);
+  const int col = slot_col<LAYOUT>(threadIdx.x);  // this thread's column of the prefetch slots
 
   // ---- gather: w[KS + k] = row start + k, w[q] = row start - KS + q, hh[q] = row start + size + q
   // (the refinement mode gathers straight into FP32 pairs below)
@@ -1185,10 +1206,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       __syncthreads();
     }
   } else if constexpr (PIPE) {
-    const TIn* s0 = pslots + threadIdx.x;
+    const TIn* s0 = pslots + col;
     const int bd = blockDim.x;
     TIn own[M];
-    pipe_rows<M, TIn, DIRECT>(pslots, own);
+    pipe_rows<M, TIn, DIRECT>(pslots, own, col);
 #pragma unroll
     for (int k = 0; k < M; k++) w[KS + k] = (ok && (FULL || k < size)) ? own[k] : TIn(0);
 #pragma unroll
@@ -1292,10 +1313,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     float fh[M + KS], fl[M + KS], hhh[KA], hhl[KA];
     if constexpr (PIPE && sizeof(TIn) == 8) {
       // whole-size partitions only (PIPE implies FULL)
-      const TIn* s0 = pslots + threadIdx.x;
+      const TIn* s0 = pslots + col;
       const int bd = blockDim.x;
       TIn own[M], lo_h[KA], hi_h[KA];
-      pipe_rows<M, TIn, DIRECT>(pslots, own);
+      pipe_rows<M, TIn, DIRECT>(pslots, own, col);
 #pragma unroll
       for (int q = 0; q < KS; q++) {
         lo_h[q] = s0[(M + q) * bd];
@@ -1322,7 +1343,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         if (bad) {  // a zero or a value outside [2^-103, 2^128) in this thread's rows:
                     // split them again (re-read from the slots) the general way
           TIn again[M];
-          pipe_rows<M, TIn, DIRECT>(pslots, again);
+          pipe_rows<M, TIn, DIRECT>(pslots, again, col);
 #pragma unroll
           for (int k = 0; k < M; k++) {
             sv = split_f64((double)again[k]);
@@ -1346,10 +1367,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         for (int q = 0; q < KA; q++) hhh[q] = hhl[q] = 0.f;
       }
     } else if constexpr (PIPE) {
-      const TIn* s0 = pslots + threadIdx.x;
+      const TIn* s0 = pslots + col;
       const int bd = blockDim.x;
       TIn own[M];
-      pipe_rows<M, TIn, DIRECT>(pslots, own);
+      pipe_rows<M, TIn, DIRECT>(pslots, own, col);
 #pragma unroll
       for (int k = 0; k < M; k++) {
         const f2 sv = split_in((ok && (FULL || k < size)) ? own[k] : TIn(0));
@@ -1512,7 +1533,24 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     if (xflip) *xflip = xch.flip;
   }
   // ---- write back
-  if constexpr (DSTR) {
+  if constexpr (SWARP) {
+    // into this thread's own slots (its rows are consumed), then out with
+    // the line-fastest mapping of the copies: one warp-wide store covers
+    // kStridedLines consecutive x positions of 32 / kStridedLines rows
+    static_assert(sizeof(TOut) == sizeof(TIn), "kStridedWarp: the slots hold the results");
+    TOut* so = reinterpret_cast<TOut*>(const_cast<TIn*>(pslots));
+    const int bd = blockDim.x;
+#pragma unroll
+    for (int k = 0; k < M; k++) so[(size_t)k * bd + col] = xo[k];
+    __syncthreads();
+    const int gp = threadIdx.x % kStridedLines, ip = threadIdx.x / kStridedLines;
+    if (gp < nl && ip < t.p) {
+      const int cs = slot_col<LAYOUT>(gp * pw + ip);
+      TOut* go = (TOut*)out_ptr + tr.base + gp + (int64_t)ip * M * tr.es;
+#pragma unroll
+      for (int k = 0; k < M; k++) go[(int64_t)k * tr.es] = so[(size_t)k * bd + cs];
+    }
+  } else if constexpr (DSTR) {
     if (ok) {
 #pragma unroll
       for (int k = 0; k < M; k++)
@@ -1559,10 +1597,20 @@ template <int M, int KS, typename TIn, int LAYOUT>
 __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTables& t, const ThreadPart& tp,
                                               const int gx, const int tile, TIn* slots, const int buf) {
   constexpr int NS = M + 2 * KS;
-  const int bd = blockDim.x, TL = LAYOUT == kDirectStrided ? kStridedLines : bd / t.pw;
-  const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
+  constexpr bool STR = strided_layout(LAYOUT);
+  const int bd = blockDim.x, TL = STR ? kStridedLines : bd / t.pw;
+  const int tx = STR ? tile % gx : tile, to = STR ? tile / gx : 0;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
-  if (tp.lane_ok && tp.g < tr.nl) {
+  if constexpr (LAYOUT == kStridedWarp) {
+    // line-fastest copy mapping (line gp, partition ip) into the slots of
+    // the thread gp * pw + ip that solves that partition
+    const int gp = threadIdx.x % kStridedLines, ip = threadIdx.x / kStridedLines;
+    if (gp < tr.nl && ip < t.p) {
+      const TIn* gline = (const TIn*)a.in + tr.base + gp;
+      prefetch_rows<M, KS, true, TIn, false>(slots + (size_t)buf * NS * bd + slot_col<LAYOUT>(gp * t.pw + ip), gline,
+                                             tr.es, ip * M, M, t.n);
+    }
+  } else if (tp.lane_ok && tp.g < tr.nl) {
     const TIn* gline = (const TIn*)a.in + tr.base + (LAYOUT == kDirectStrided ? (int64_t)tp.g : (int64_t)tp.g * t.n);
     constexpr bool VEC = LAYOUT == kDirectX && (M % (16 / sizeof(TIn))) == 0;
     prefetch_rows<M, KS, true, TIn, VEC>(slots + (size_t)buf * NS * bd + threadIdx.x, gline,
@@ -1590,6 +1638,20 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
   const ThreadPart tp = thread_part<M, true, LAYOUT>(t);
   int tile = blockIdx.x, buf = 0, xflip = 0;
   if (tile < ntiles) prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, tile, slots, 0);
+  if constexpr (LAYOUT == kStridedWarp) {
+    // the copies land in other threads' slots: wait for this tile's, then a
+    // barrier, which also shows that every thread has written out the
+    // previous tile from the other half before the next copies go there
+    for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+      cp_async_wait<0>();
+      __syncthreads();
+      const int next = tile + gridDim.x;
+      if (next < ntiles) prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, next, slots, buf ^ 1);
+      line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true, ST>(a, t, a.in, a.out, tile % gx, tile / gx, smem_raw,
+                                                                 slots + (size_t)buf * NS * bd);
+    }
+    return;
+  }
   for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
     const int next = tile + gridDim.x;
     if (next < ntiles) {

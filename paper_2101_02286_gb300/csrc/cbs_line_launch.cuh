@@ -64,7 +64,7 @@ template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOU
 cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if (a.nlines <= 0) return cudaSuccess;
   constexpr int NS = M + 2 * KS;
-  const int threads = LAYOUT == kDirectStrided ? kStridedLines * t.pw : kLineThreads;
+  const int threads = strided_layout(LAYOUT) ? kStridedLines * t.pw : kLineThreads;
   const dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, threads / t.pw);
   const int64_t ntiles = (int64_t)grid.x * grid.y;
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
@@ -115,7 +115,10 @@ cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream
       // hide HBM latency without the pipelined prefetch; the FP64 / FP32
       // kernels keep 3 CTAs per SM and load directly
       if constexpr (refine_mode(MODE)) {
+        // y/z lines: with 32 partitions per line a warp can hold a line
+        // (messages by shuffles, rows and results through the slots)
         if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectX, ST>(a, t, s);
+        if (t.pw == 32) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kStridedWarp, ST>(a, t, s);
         return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectStrided, ST>(a, t, s);
       } else {
         if (a.dir == 0) return launch_one<R, M, MODE, KSV, TIn, TOut, true, kDirectX, ST>(a, t, s);

@@ -209,6 +209,26 @@ def test_pipelined_plans_of_different_widths_in_sequence(cuda):
         assert oracle.rel_err(got, oracle_derivative(f, 1, "tri6")) < 1e-12
 
 
+@pytest.mark.parametrize("direction", [1, 2])
+@pytest.mark.parametrize("scheme,n,p,precision,sweeps", [
+    ("tri6", 512, 32, "fp32_refine", 1), ("tri6", 256, 32, "fp32_refine", 2), ("penta10", 512, 32, "fp32_refine", 2),
+    ("tri6", 384, 24, "fp32_refine", 1), ("penta10", 256, 32, "fp32_refine_i64", 2)])
+def test_refine_yz_lines_warp_per_line(cuda, direction, scheme, n, p, precision, sweeps):
+    # y/z lines in 32 lanes (n = p x M, p <= 32): rows are copied line-fastest
+    # into the slots of the threads that solve them (a warp per line, shuffled
+    # messages) and the results leave through the same slots.  13 lines along
+    # x leave the second tile of each row ragged, and 2 x 400 tiles are more
+    # than the resident CTAs, so CTAs walk several tiles through both halves
+    # of their double buffer.
+    rng = np.random.default_rng(71 + direction + n)
+    shape = [400, 13, 13] if direction == 1 else [13, 400, 13]
+    shape[2 - direction] = n
+    f = rng.uniform(-1, 1, size=tuple(shape))
+    got, info = gpu_derivative(f, direction, scheme, precision=precision, segments=p, sweeps=sweeps)
+    assert info["segments"] == p and info["rows_big"] * p == n
+    assert oracle.rel_err(got, oracle_derivative(f, direction, scheme)) < 1e-12
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 def test_identity_lhs_gives_explicit_stencil(cuda, precision):
     # alpha = 0: A = I, every coupling block vanishes and x = S f exactly the

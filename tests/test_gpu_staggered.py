@@ -65,6 +65,20 @@ def test_whole_partitions(cuda, kind, shift, direction, precision):
     assert err < TOL[precision]
 
 
+@pytest.mark.parametrize("direction", [1, 2])
+@pytest.mark.parametrize("n", [256, 512])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("kind", ["staggered", "midpoint"])
+def test_refine_yz_32_partitions(cuda, kind, shift, n, direction):
+    # 32 partitions of 8 or 16 rows along y or z: the refinement kernel that
+    # holds a line per warp (rows and results through shared memory)
+    rng = np.random.default_rng(300 + n + 10 * direction + shift)
+    f = rng.uniform(-1, 1, size=_shape(direction, n, others=(20, 11)))
+    err, info = run(f, direction, kind, shift, "fp32_refine", segments=32)
+    assert info["segments"] == 32 and info["rows_big"] == n // 32
+    assert err < 1e-12
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_refine"])
 @pytest.mark.parametrize("n,p", [(50, 4), (61, 5), (200, 13), (97, 7), (16, 1), (8, 2)])
 @pytest.mark.parametrize("shift", [0, 1])
