@@ -191,7 +191,10 @@ cbs_status cbs_plan_destroy(cbs_plan* plan);
 
 /* x = A^{-1} b along every line, with b = S f when the plan has a stencil.
  * in: device, in_dtype, the field f (or b); out: device, out_dtype, same dims.
- * `out` must not alias `in`.  Asynchronous on `stream`. */
+ * `out` must not alias `in`.  Asynchronous on `stream`.  Arrays need only
+ * element alignment: x-line plans with whole-size partitions move rows in
+ * 16-byte units when both arrays start on a 16-byte boundary and otherwise
+ * run a staged kernel (same results, slower). */
 cbs_status cbs_solve(cbs_plan* plan, const void* in, void* out, void* stream);
 
 /* Adjoint of cbs_solve (Sec. 3 operators transposed):

@@ -1043,6 +1043,10 @@ template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(B) : "memory");
 }
+// 16-byte copy that bypasses L1 (streamed tiles)
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -1063,7 +1067,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //    that solves them, where a warp holds one line (lane = partition), so the
 //    interface messages are warp shuffles as for x-lines; the results go back
 //    through the same slots and leave with the line-fastest mapping.
-constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2, kStridedWarp = 3;
+//  kTileX: x-lines in the pipelined kernel.  A warp holds one line (lane =
+//    partition; or 32 / pw lines), which is contiguous in HBM: the warp copies
+//    it with 16-byte copies of consecutive pieces (coalesced) into shared
+//    memory, one chunk of M rows per partition, each chunk padded by 16 bytes
+//    so that the lanes' reads of their own chunks fall on distinct banks; the
+//    stencil halo comes from the neighbouring chunks.
+constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2, kStridedWarp = 3, kTileX = 4;
 constexpr int kStridedLines = 8;
 __host__ __device__ constexpr bool strided_layout(int layout) {
   return layout == kDirectStrided || layout == kStridedWarp;
@@ -1073,6 +1083,14 @@ __host__ __device__ constexpr bool strided_layout(int layout) {
 // kStridedWarp (32 lanes per line, c = 32 g + i) the lanes of line g are
 // permuted (i ^ 2g): the copies of one warp (8 lines x 4 partitions) and the
 // reads of one line then fall on distinct banks in each half-warp.
+// Elements of one half of the pipelined kernel's double buffer: kTileX holds
+// (bd / pw) lines of p padded chunks, the others NS = M + 2 KS slot rows of
+// bd threads.
+template <int M, int KS, typename TIn, int LAYOUT>
+__host__ __device__ constexpr int pipe_buf_elems(int bd, int pw, int p) {
+  return LAYOUT == kTileX ? (bd / pw) * p * (M + 16 / (int)sizeof(TIn)) : (M + 2 * KS) * bd;
+}
+
 template <int LAYOUT>
 __device__ __forceinline__ int slot_col(int c) {
   if constexpr (LAYOUT == kStridedWarp) return c ^ (((c >> 5) & 7) << 1);
@@ -1162,6 +1180,33 @@ __device__ __forceinline__ void prefetch_rows(TIn* slot0, const TIn* gline, int6
   }
 }
 
+// kTileX: rows of this lane's chunk (chunk g p + i of the half-buffer
+// `buf`, M rows padded to CS = M + 16 / sizeof(TIn) elements) and the KS
+// halo rows on each side from the neighbouring chunks of the same line
+// (periodic).  Lanes without a partition read chunk g p (values unused).
+template <int M, int KS, int KA, typename TIn>
+__device__ __forceinline__ void tilex_rows(const TIn* buf, const DevLineTables& t, const int g, const int i,
+                                           const bool lane_ok, TIn (&own)[M], TIn (&lo_h)[KA], TIn (&hi_h)[KA]) {
+  constexpr int CS = M + 16 / (int)sizeof(TIn);
+  const int c0 = g * t.p, c = c0 + (lane_ok ? i : 0);
+  const TIn* chunk = buf + (size_t)c * CS;
+  const TIn* cprev = buf + (size_t)(i == 0 || !lane_ok ? c0 + t.p - 1 : c - 1) * CS;
+  const TIn* cnext = buf + (size_t)(i >= t.p - 1 || !lane_ok ? c0 : c + 1) * CS;
+  static_assert((M * sizeof(TIn)) % 16 == 0, "whole 16-byte units per chunk");
+#pragma unroll
+  for (int u = 0; u < (int)(M * sizeof(TIn) / 16); u++) {
+    const float4 q = *reinterpret_cast<const float4*>(chunk + u * (16 / sizeof(TIn)));
+    const TIn* e = reinterpret_cast<const TIn*>(&q);
+#pragma unroll
+    for (int j = 0; j < (int)(16 / sizeof(TIn)); j++) own[u * (16 / sizeof(TIn)) + j] = e[j];
+  }
+#pragma unroll
+  for (int q = 0; q < KS; q++) {
+    lo_h[q] = cprev[M - KS + q];
+    hi_h[q] = cnext[q];
+  }
+}
+
 // One tile = blockDim / pw consecutive lines, processed by the whole CTA:
 // gather the rows (+ stencil halo) of every partition, stencil + solve per
 // thread, write back.  KS: stencil terms compiled in (0 = the input already
@@ -1177,8 +1222,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
   using T = typename std::conditional<MODE == kModeF64, double, float>::type;
   using TT = typename std::conditional<(sizeof(TIn) == 8 || sizeof(TOut) == 8), double, float>::type;
   constexpr bool DIRECT = LAYOUT == kDirectX, DSTR = LAYOUT == kDirectStrided, SWARP = LAYOUT == kStridedWarp;
-  static_assert(!SWARP || (PIPE && FULL), "kStridedWarp: pipelined whole-size partitions only");
-  using TW = typename std::conditional<DIRECT || DSTR || SWARP, TIn, TT>::type;  // element type of the gathered window
+  constexpr bool TILEX = LAYOUT == kTileX;
+  static_assert(!(SWARP || TILEX) || (PIPE && FULL), "pipelined whole-size partitions only");
+  static_assert(!TILEX || (sizeof(TIn) == 8 && refine_mode(MODE)), "kTileX: FP64 input, refinement");
+  using TW = typename std::conditional<DIRECT || DSTR || SWARP || TILEX, TIn, TT>::type;  // element type of the gathered window
   constexpr int KA = KS > 0 ? KS : 1;  // halo array size (KS = 0 compiles no stencil)
   TT* S = reinterpret_cast<TT*>(smem_raw);
   const int pw = t.pw;
@@ -1316,11 +1363,15 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       const TIn* s0 = pslots + col;
       const int bd = blockDim.x;
       TIn own[M], lo_h[KA], hi_h[KA];
-      pipe_rows<M, TIn, DIRECT>(pslots, own, col);
+      if constexpr (TILEX) {
+        tilex_rows<M, KS, KA>(pslots, t, g, i, lane_ok, own, lo_h, hi_h);
+      } else {
+        pipe_rows<M, TIn, DIRECT>(pslots, own, col);
 #pragma unroll
-      for (int q = 0; q < KS; q++) {
-        lo_h[q] = s0[(M + q) * bd];
-        hi_h[q] = s0[(M + KS + q) * bd];
+        for (int q = 0; q < KS; q++) {
+          lo_h[q] = s0[(M + q) * bd];
+          hi_h[q] = s0[(M + KS + q) * bd];
+        }
       }
       if (ok) {
         unsigned bad = 0u;
@@ -1342,22 +1393,42 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         }
         if (bad) {  // a zero or a value outside [2^-103, 2^128) in this thread's rows:
                     // split them again (re-read from the slots) the general way
-          TIn again[M];
-          pipe_rows<M, TIn, DIRECT>(pslots, again, col);
+          if constexpr (TILEX) {
+            TIn again[M], lo_a[KA], hi_a[KA];
+            tilex_rows<M, KS, KA>(pslots, t, g, i, lane_ok, again, lo_a, hi_a);
 #pragma unroll
-          for (int k = 0; k < M; k++) {
-            sv = split_f64((double)again[k]);
-            fh[KS + k] = sv.hi;
-            fl[KS + k] = sv.lo;
-          }
+            for (int k = 0; k < M; k++) {
+              sv = split_f64((double)again[k]);
+              fh[KS + k] = sv.hi;
+              fl[KS + k] = sv.lo;
+            }
 #pragma unroll
-          for (int q = 0; q < KS; q++) {
-            sv = split_f64((double)s0[(M + q) * bd]);
-            fh[q] = sv.hi;
-            fl[q] = sv.lo;
-            sv = split_f64((double)s0[(M + KS + q) * bd]);
-            hhh[q] = sv.hi;
-            hhl[q] = sv.lo;
+            for (int q = 0; q < KS; q++) {
+              sv = split_f64((double)lo_a[q]);
+              fh[q] = sv.hi;
+              fl[q] = sv.lo;
+              sv = split_f64((double)hi_a[q]);
+              hhh[q] = sv.hi;
+              hhl[q] = sv.lo;
+            }
+          } else {
+            TIn again[M];
+            pipe_rows<M, TIn, DIRECT>(pslots, again, col);
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+              sv = split_f64((double)again[k]);
+              fh[KS + k] = sv.hi;
+              fl[KS + k] = sv.lo;
+            }
+#pragma unroll
+            for (int q = 0; q < KS; q++) {
+              sv = split_f64((double)s0[(M + q) * bd]);
+              fh[q] = sv.hi;
+              fl[q] = sv.lo;
+              sv = split_f64((double)s0[(M + KS + q) * bd]);
+              hhh[q] = sv.hi;
+              hhl[q] = sv.lo;
+            }
           }
         }
       } else {
@@ -1556,7 +1627,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       for (int k = 0; k < M; k++)
         if (FULL || k < size) gout[(start + k) * es] = xo[k];
     }
-  } else if constexpr (DIRECT) {
+  } else if constexpr (DIRECT || TILEX) {
     constexpr int V = 16 / sizeof(TOut);
     if (ok) {
       if (FULL && (M % V) == 0) {
@@ -1601,7 +1672,26 @@ __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTa
   const int bd = blockDim.x, TL = STR ? kStridedLines : bd / t.pw;
   const int tx = STR ? tile % gx : tile, to = STR ? tile / gx : 0;
   const TileRef tr = tile_of(a, t.n, TL, tx, to);
-  if constexpr (LAYOUT == kStridedWarp) {
+  if constexpr (LAYOUT == kTileX) {
+    // each warp copies its own 32 / pw lines, nl' n consecutive elements, in
+    // 16-byte pieces taken in order (512 contiguous bytes per warp-wide copy);
+    // element e (from the warp's first line l0) goes to chunk l0 p + e / M
+    // (a chunk holds M rows, M % V == 0)
+    constexpr int V = 16 / sizeof(TIn), CS = M + V;
+    static_assert(M % V == 0, "kTileX: whole 16-byte pieces per chunk");
+    const int lpw = 32 / t.pw, l0 = (threadIdx.x >> 5) * lpw;
+    const int lines = tr.nl - l0 < lpw ? tr.nl - l0 : lpw;
+    if (lines > 0) {
+      TIn* dst = slots + (size_t)buf * pipe_buf_elems<M, KS, TIn, LAYOUT>(bd, t.pw, t.p) + (size_t)l0 * t.p * CS;
+      const TIn* gsrc = (const TIn*)a.in + tr.base + (int64_t)l0 * t.n;
+      const int pieces = lines * t.n / V;
+      for (int j = threadIdx.x & 31; j < pieces; j += 32) {
+        const int e = j * V;
+        cp_async_cg16(dst + (e / M) * CS + (e % M), gsrc + e);
+      }
+    }
+    (void)NS;
+  } else if constexpr (LAYOUT == kStridedWarp) {
     // line-fastest copy mapping (line gp, partition ip) into the slots of
     // the thread gp * pw + ip that solves that partition
     const int gp = threadIdx.x % kStridedLines, ip = threadIdx.x / kStridedLines;
@@ -1640,8 +1730,8 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
   if (tile < ntiles) prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, tile, slots, 0);
   if constexpr (LAYOUT == kStridedWarp) {
     // the copies land in other threads' slots: wait for this tile's, then a
-    // barrier, which also shows that every thread has written out the
-    // previous tile from the other half before the next copies go there
+    // barrier, which also shows that every thread is done with the previous
+    // tile in the other half before the next copies go there
     for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
       cp_async_wait<0>();
       __syncthreads();
@@ -1652,17 +1742,22 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
     }
     return;
   }
+  // kTileX: a warp reads only the lines it copied, so warp barriers order
+  // its lanes' copies and reads
   for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
     const int next = tile + gridDim.x;
     if (next < ntiles) {
+      if constexpr (LAYOUT == kTileX) __syncwarp();  // the warp is done reading the other half
       prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, next, slots, buf ^ 1);
       cp_async_wait<1>();  // this tile's copies are done, the next tile's stay in flight
     } else {
       cp_async_wait<0>();
     }
+    if constexpr (LAYOUT == kTileX) __syncwarp();  // every lane's copies of this tile have landed
     const int tx = LAYOUT == kDirectStrided ? tile % gx : tile, to = LAYOUT == kDirectStrided ? tile / gx : 0;
-    line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true, ST>(a, t, a.in, a.out, tx, to, smem_raw,
-                                                               slots + (size_t)buf * NS * bd, &xflip);
+    line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true, ST>(
+        a, t, a.in, a.out, tx, to, smem_raw,
+        slots + (size_t)buf * pipe_buf_elems<M, KS, TIn, LAYOUT>(bd, t.pw, t.p), &xflip);
   }
 }
 

@@ -69,7 +69,8 @@ cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t 
   const int64_t ntiles = (int64_t)grid.x * grid.y;
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
   const size_t smem = (LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0) +
-                      2 * (size_t)NS * threads * sizeof(TIn);
+                      2 * (size_t)pipe_buf_elems<M, KS, TIn, LAYOUT>(threads, t.pw, t.p) * sizeof(TIn);
+  (void)NS;
   auto kern = line_kernel_pipe<R, M, MODE, KS, TIn, TOut, LAYOUT, ST>;
   // per instantiation: the largest dynamic shared memory configured so far
   // and the occupancy of the last (threads, smem) launched (both depend on
@@ -102,22 +103,25 @@ cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t 
   return cudaGetLastError();
 }
 
-// Whole-size partitions (n = p M): sizes are compile-time constants and
-// neither x-lines nor y/z lines are staged through shared memory.  Compiled
-// for FP64 input and output only.
+// Whole-size partitions (n = p M): sizes are compile-time constants and the
+// direct and pipelined layouts apply.  Compiled for FP64 input and output
+// only; x-lines whose arrays are not 16-byte aligned take the staged path.
 inline bool tile_full(const DevLineTables& t, int M) { return t.count_big == t.p && t.rows_big == M; }
+// The x-line layouts move rows in 16-byte units: both arrays must start on a
+// 16-byte boundary (rows of a line then do too, n being a multiple of M).
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 template <int R, int M, int MODE, int KSV, typename TIn, typename TOut, int ST = 0>
 cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if constexpr (sizeof(TIn) == 8 && sizeof(TOut) == 8) {
-    if (tile_full(t, M)) {
+    if (tile_full(t, M) && (a.dir != 0 || (aligned16(a.in) && aligned16(a.out)))) {
       // the refinement kernel holds 2 CTAs per SM (registers), too few to
       // hide HBM latency without the pipelined prefetch; the FP64 / FP32
       // kernels keep 3 CTAs per SM and load directly
       if constexpr (refine_mode(MODE)) {
         // y/z lines: with 32 partitions per line a warp can hold a line
         // (messages by shuffles, rows and results through the slots)
-        if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectX, ST>(a, t, s);
+        if (a.dir == 0) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kTileX, ST>(a, t, s);
         if (t.pw == 32) return launch_pipe<R, M, MODE, KSV, TIn, TOut, kStridedWarp, ST>(a, t, s);
         return launch_pipe<R, M, MODE, KSV, TIn, TOut, kDirectStrided, ST>(a, t, s);
       } else {

@@ -95,6 +95,10 @@ class Plan:
                              % (self.shape, self.in_dtype))
         if out is None:
             out = torch.empty(self.shape, dtype=self.out_dtype, device=inp.device)
+        elif out.shape != self.shape or out.dtype != self.out_dtype or not out.is_contiguous() \
+                or out.device != inp.device:
+            raise ValueError("out must be a contiguous tensor of shape %s and dtype %s on the input's device"
+                             % (self.shape, self.out_dtype))
         s = stream if stream is not None else torch.cuda.current_stream(inp.device)
         abi.cbs_solve(self.handle, inp.data_ptr(), out.data_ptr(), s.cuda_stream)
         return out

@@ -229,6 +229,33 @@ def test_refine_yz_lines_warp_per_line(cuda, direction, scheme, n, p, precision,
     assert oracle.rel_err(got, oracle_derivative(f, direction, scheme)) < 1e-12
 
 
+@pytest.mark.parametrize("precision,p", [("fp64", 16), ("fp32_refine", 32), ("fp32", 16)])
+def test_x_lines_arrays_off_16_byte_boundary(cuda, precision, p):
+    # x-lines of whole-size partitions move rows in 16-byte units when both
+    # arrays are 16-byte aligned; views that start one element (8 bytes) into
+    # their buffers take the staged kernel and give the same results
+    rng = np.random.default_rng(81)
+    shape = (3, 21, 512)
+    f = rng.uniform(-1, 1, size=shape)
+    count = int(np.prod(shape))
+    h = W.grid_spacing(512)
+    plan = Plan(shape, 0, lhs=W.LELE6_TRI["lhs"], rhs=W.LELE6_TRI["rhs"], h=h, segments=p, precision=precision)
+    fb = torch.empty(count + 1, dtype=torch.float64, device="cuda")
+    ob = torch.full((count + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    x, y = fb[1:].view(shape), ob[1:].view(shape)
+    assert x.data_ptr() % 16 == 8 and y.data_ptr() % 16 == 8
+    x.copy_(torch.from_numpy(f))
+    plan.solve(x, y)
+    aligned = plan.solve(torch.from_numpy(f).cuda())
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    plan.close()
+    got = y.cpu().numpy()
+    assert np.isnan(ob[0].item())  # nothing written before the view
+    assert oracle.rel_err(got, aligned.cpu().numpy()) < TOL[precision]
+    assert oracle.rel_err(got, oracle_derivative(f, 0, "tri6")) < TOL[precision]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 def test_identity_lhs_gives_explicit_stencil(cuda, precision):
     # alpha = 0: A = I, every coupling block vanishes and x = S f exactly the
