@@ -716,11 +716,11 @@ def main():
             "ms_per_direction": dir_ref,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": hbm_src,
-                         "kernel": "line_kernel_pipe refine, strided direct layout (y and z lines)",
+                         "kernel": "line_kernel_pipe refine, y and z lines (warp per line, rows and results through shared memory)",
                          "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_yz,
                          "slowest_direction": "xyz"[kdir]},
             "roofline_x": {"bound": "hbm", "achieved": achieved_x, "peak": hbm, "unit": "GB/s",
-                           "frac": achieved_x / hbm, "kernel": "line_kernel_pipe refine, 16-byte prefetch (x lines)",
+                           "frac": achieved_x / hbm, "kernel": "line_kernel_pipe refine, x lines (per-warp contiguous tile copy)",
                            "ms_per_launch": dir_ref[0]},
             "refine_fp64_interface": {"value": job_throughput(units, world, ms_i64), "unit": "Gunknowns/s",
                                       "ms_per_step": ms_i64, "ms_per_direction": dir_i64,
