@@ -1075,6 +1075,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //    stencil halo comes from the neighbouring chunks.
 constexpr int kStaged = 0, kDirectX = 1, kDirectStrided = 2, kStridedWarp = 3, kTileX = 4;
 constexpr int kStridedLines = 8;
+constexpr int kStridedWarpThreads = kStridedLines * 32;  // kStridedWarp: 8 lines of 32 lanes
 __host__ __device__ constexpr bool strided_layout(int layout) {
   return layout == kDirectStrided || layout == kStridedWarp;
 }
@@ -1084,11 +1085,13 @@ __host__ __device__ constexpr bool strided_layout(int layout) {
 // permuted (i ^ 2g): the copies of one warp (8 lines x 4 partitions) and the
 // reads of one line then fall on distinct banks in each half-warp.
 // Elements of one half of the pipelined kernel's double buffer: kTileX holds
-// (bd / pw) lines of p padded chunks, the others NS = M + 2 KS slot rows of
-// bd threads.
+// (bd / pw) lines of p padded chunks, kStridedWarp M slot rows of bd threads
+// (the halo rows are read from the neighbouring lanes' slots), the others
+// NS = M + 2 KS slot rows of bd threads.
 template <int M, int KS, typename TIn, int LAYOUT>
 __host__ __device__ constexpr int pipe_buf_elems(int bd, int pw, int p) {
-  return LAYOUT == kTileX ? (bd / pw) * p * (M + 16 / (int)sizeof(TIn)) : (M + 2 * KS) * bd;
+  return LAYOUT == kTileX ? (bd / pw) * p * (M + 16 / (int)sizeof(TIn))
+         : LAYOUT == kStridedWarp ? M * bd : (M + 2 * KS) * bd;
 }
 
 template <int LAYOUT>
@@ -1108,9 +1111,9 @@ __device__ __forceinline__ auto make_xchg(int pw, unsigned char* smem, int offse
 
 // This thread's own rows from the prefetch slots (layout of prefetch_rows;
 // VEC: 16-byte units read back with 16-byte shared loads).
-template <int M, typename TIn, bool VEC>
+template <int M, typename TIn, bool VEC, int BD = 0>
 __device__ __forceinline__ void pipe_rows(const TIn* slots, TIn (&v)[M], const int col) {
-  const int bd = blockDim.x;
+  const int bd = BD ? BD : blockDim.x;  // BD: block size known at compile time
   if constexpr (VEC && (M % (16 / sizeof(TIn))) == 0) {
     constexpr int V = 16 / sizeof(TIn);
 #pragma unroll
@@ -1155,10 +1158,10 @@ __device__ __forceinline__ ThreadPart thread_part(const DevLineTables& t) {
 // VEC (contiguous rows, M a multiple of the 16-byte vector width V): own
 // rows are copied in 16-byte units, unit u of thread tid at element offset
 // (u * bd + tid) * V, conflict-free for 16-byte shared loads.
-template <int M, int KS, bool FULL, typename TIn, bool VEC = false>
+template <int M, int KS, bool FULL, typename TIn, bool VEC = false, int BD = 0>
 __device__ __forceinline__ void prefetch_rows(TIn* slot0, const TIn* gline, int64_t es, int start, int size,
                                               int n) {
-  const int bd = blockDim.x;
+  const int bd = BD ? BD : blockDim.x;  // BD: block size known at compile time
   if constexpr (VEC) {
     constexpr int V = 16 / sizeof(TIn);
     TIn* base = slot0 - threadIdx.x;  // thread 0's slot 0
@@ -1204,6 +1207,26 @@ __device__ __forceinline__ void tilex_rows(const TIn* buf, const DevLineTables& 
   for (int q = 0; q < KS; q++) {
     lo_h[q] = cprev[M - KS + q];
     hi_h[q] = cnext[q];
+  }
+}
+
+// kStridedWarp: rows of lane i of line g (slot column slot_col(32 g + i) of
+// the half-buffer `buf`, M slot rows of kStridedWarpThreads) and the KS halo
+// rows on each side from the slots of lanes i - 1 and i + 1 of the same line
+// (periodic over the line's p partitions; lanes i >= p read in-range slots
+// whose values are unused).
+template <int M, int KS, int KA, typename TIn>
+__device__ __forceinline__ void swarp_rows(const TIn* buf, const int p, const int g, const int i, TIn (&own)[M],
+                                           TIn (&lo_h)[KA], TIn (&hi_h)[KA]) {
+  constexpr int BD = kStridedWarpThreads;
+  const int prev = i == 0 ? p - 1 : i - 1, next = i + 1 >= p ? 0 : i + 1;
+  pipe_rows<M, TIn, false, BD>(buf, own, slot_col<kStridedWarp>(32 * g + i));
+  const TIn* bp = buf + slot_col<kStridedWarp>(32 * g + prev);
+  const TIn* bn = buf + slot_col<kStridedWarp>(32 * g + next);
+#pragma unroll
+  for (int q = 0; q < KS; q++) {
+    lo_h[q] = bp[(M - KS + q) * BD];
+    hi_h[q] = bn[q * BD];
   }
 }
 
@@ -1365,6 +1388,8 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
       TIn own[M], lo_h[KA], hi_h[KA];
       if constexpr (TILEX) {
         tilex_rows<M, KS, KA>(pslots, t, g, i, lane_ok, own, lo_h, hi_h);
+      } else if constexpr (SWARP) {
+        swarp_rows<M, KS, KA>(pslots, t.p, g, i, own, lo_h, hi_h);
       } else {
         pipe_rows<M, TIn, DIRECT>(pslots, own, col);
 #pragma unroll
@@ -1393,9 +1418,10 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         }
         if (bad) {  // a zero or a value outside [2^-103, 2^128) in this thread's rows:
                     // split them again (re-read from the slots) the general way
-          if constexpr (TILEX) {
+          if constexpr (TILEX || SWARP) {
             TIn again[M], lo_a[KA], hi_a[KA];
-            tilex_rows<M, KS, KA>(pslots, t, g, i, lane_ok, again, lo_a, hi_a);
+            if constexpr (TILEX) tilex_rows<M, KS, KA>(pslots, t, g, i, lane_ok, again, lo_a, hi_a);
+            else swarp_rows<M, KS, KA>(pslots, t.p, g, i, again, lo_a, hi_a);
 #pragma unroll
             for (int k = 0; k < M; k++) {
               sv = split_f64((double)again[k]);
@@ -1610,7 +1636,7 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     // kStridedLines consecutive x positions of 32 / kStridedLines rows
     static_assert(sizeof(TOut) == sizeof(TIn), "kStridedWarp: the slots hold the results");
     TOut* so = reinterpret_cast<TOut*>(const_cast<TIn*>(pslots));
-    const int bd = blockDim.x;
+    constexpr int bd = kStridedWarpThreads;
 #pragma unroll
     for (int k = 0; k < M; k++) so[(size_t)k * bd + col] = xo[k];
     __syncthreads();
@@ -1697,8 +1723,10 @@ __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTa
     const int gp = threadIdx.x % kStridedLines, ip = threadIdx.x / kStridedLines;
     if (gp < tr.nl && ip < t.p) {
       const TIn* gline = (const TIn*)a.in + tr.base + gp;
-      prefetch_rows<M, KS, true, TIn, false>(slots + (size_t)buf * NS * bd + slot_col<LAYOUT>(gp * t.pw + ip), gline,
-                                             tr.es, ip * M, M, t.n);
+      // own rows only: the halo rows are read from the neighbouring lanes' slots
+      prefetch_rows<M, 0, true, TIn, false, kStridedWarpThreads>(
+          slots + (size_t)buf * M * kStridedWarpThreads + slot_col<LAYOUT>(gp * t.pw + ip), gline, tr.es, ip * M, M,
+          t.n);
     }
   } else if (tp.lane_ok && tp.g < tr.nl) {
     const TIn* gline = (const TIn*)a.in + tr.base + (LAYOUT == kDirectStrided ? (int64_t)tp.g : (int64_t)tp.g * t.n);
@@ -1715,8 +1743,8 @@ __device__ __forceinline__ void prefetch_tile(const LineArgs& a, const DevLineTa
 // the asynchronous copies of the next tile's rows into the other half of a
 // double buffer of thread-private shared-memory slots, so HBM traffic
 // overlaps the arithmetic.  Shared memory: the message buffer (strided
-// layout only, kCtaXchgSlots 64-bit slots per thread) followed by 2 x
-// (M + 2 KS) slots of TIn per thread.
+// layout only, kCtaXchgSlots 64-bit slots per thread) followed by the two
+// halves of the double buffer (pipe_buf_elems elements of TIn each).
 template <int R, int M, int MODE, int KS, typename TIn, typename TOut, int LAYOUT, int ST = 0>
 __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
     line_kernel_pipe(const LineArgs a, const DevLineTables t, const int gx, const int ntiles) {
@@ -1738,7 +1766,7 @@ __global__ void __launch_bounds__(256, (refine_mode(MODE) || M == 32) ? 2 : 3)
       const int next = tile + gridDim.x;
       if (next < ntiles) prefetch_tile<M, KS, TIn, LAYOUT>(a, t, tp, gx, next, slots, buf ^ 1);
       line_tile<R, M, MODE, KS, TIn, TOut, true, LAYOUT, true, ST>(a, t, a.in, a.out, tile % gx, tile / gx, smem_raw,
-                                                                 slots + (size_t)buf * NS * bd);
+                                                                 slots + (size_t)buf * M * kStridedWarpThreads);
     }
     return;
   }
