@@ -193,8 +193,8 @@ def nvtx(torch, label):
 
 
 # ---------------------------------------------------------------- traffic record
-KERNEL_SOURCES = ("paper_2101_02286_gb300/csrc/cbs_line.cuh", "paper_2101_02286_gb300/csrc/cbs_line_launch.cuh",
-                  "paper_2101_02286_gb300/csrc/cbs_internal.h")
+KERNEL_SOURCES = ("paper_2101_02286_gb300/csrc/cbs_tma.cuh", "paper_2101_02286_gb300/csrc/cbs_tma_launch.cuh",
+                  "paper_2101_02286_gb300/csrc/cbs_line.cuh", "paper_2101_02286_gb300/csrc/cbs_internal.h")
 
 
 def kernel_source_hash() -> str:
@@ -688,13 +688,19 @@ def main():
         hbm = peaks.get("hbm_gbs", 6800.0)
         hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
         bytes_per_launch = 16.0 * n ** 3  # read f (FP64), write f' (FP64)
+        # dominant kernel: the slowest of the three launches of a step (all
+        # three run the TMA-fed refinement kernel, with the tile shape the
+        # autotuner picked for the direction)
         kdir = max(range(3), key=lambda d: dir_ref[d])
-        # dominant kernel: the pipelined refinement kernel in its strided layout,
-        # which runs the y and z lines (two of the three launches of a step)
-        ms_yz = (dir_ref[1] + dir_ref[2]) / 2
-        achieved = bytes_per_launch / (ms_yz * 1e-3) / 1e9
-        achieved_x = bytes_per_launch / (dir_ref[0] * 1e-3) / 1e9
-        traffic = traffic_record("line_kernel_refine_yz", n)
+        achieved = bytes_per_launch / (dir_ref[kdir] * 1e-3) / 1e9
+        info_ref = [p.info() for p in plans["fp32_refine"]]
+        traffic = traffic_record("refine_tma_%s" % "xyz"[kdir], n)
+        per_dir = {"xyz"[d]: {"ms_per_launch": dir_ref[d], "achieved": bytes_per_launch / (dir_ref[d] * 1e-3) / 1e9,
+                              "frac": bytes_per_launch / (dir_ref[d] * 1e-3) / 1e9 / hbm,
+                              "traffic": traffic_record("refine_tma_%s" % "xyz"[d], n),
+                              "kernel": "refine_tma_kernel" if info_ref[d]["tma"] and info_ref[d]["variant"] == 0
+                              else "line_kernel_pipe",
+                              "tile_lines": info_ref[d]["tile_lines"]} for d in range(3)}
         # FP64 path: bound by the FP64 pipe; 15 algorithmic FP64 flops per unknown
         fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
         fp64_flops = 15.0 * n ** 3
@@ -716,12 +722,11 @@ def main():
             "ms_per_direction": dir_ref,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": hbm_src,
-                         "kernel": "line_kernel_pipe refine, y and z lines (warp per line, rows and results through shared memory)",
-                         "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_yz,
+                         "kernel": "refine_tma_kernel (TMA tiles, warp per line, FP32 solves + one "
+                                   "FP64-accurate refinement sweep), %s lines" % "xyz"[kdir],
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": dir_ref[kdir],
                          "slowest_direction": "xyz"[kdir]},
-            "roofline_x": {"bound": "hbm", "achieved": achieved_x, "peak": hbm, "unit": "GB/s",
-                           "frac": achieved_x / hbm, "kernel": "line_kernel_pipe refine, x lines (per-warp contiguous tile copy)",
-                           "ms_per_launch": dir_ref[0]},
+            "roofline_per_direction": per_dir,
             "refine_fp64_interface": {"value": job_throughput(units, world, ms_i64), "unit": "Gunknowns/s",
                                       "ms_per_step": ms_i64, "ms_per_direction": dir_i64,
                                       "max_rel_err": err.get("fp32_refine_i64"),

@@ -53,7 +53,10 @@ enum {
     CBS_ERR_SINGULAR = 3,    /* zero / non-finite pivot or interface block    */
     CBS_ERR_TIMEOUT = 4,     /* a bounded device wait expired                 */
     CBS_ERR_CUDA = 5,        /* a CUDA runtime call failed                    */
-    CBS_ERR_NO_MEMORY = 6    /* host or device allocation failed              */
+    CBS_ERR_NO_MEMORY = 6,   /* host or device allocation failed              */
+    CBS_ERR_RANGE = 7        /* device: an input or result outside the range
+                                of the FP32 modes (magnitude >= 2^126, inf or
+                                nan); the affected lines' output is not valid */
 };
 
 /* Arithmetic of the solve. */
@@ -149,6 +152,11 @@ typedef struct cbs_plan_info {
      * inner_*: the segment-level system of a long-line plan (kernel 1). */
     int32_t message_stages, message_stages_f32;
     int32_t inner_message_stages, inner_message_stages_f32;
+    /* Kernel variant setting (cbs_plan_set_variant), whether the plan
+     * qualifies for the TMA-fed refinement kernel (1: it runs when the arrays
+     * start on 16-byte boundaries and the variant is 0), and the lines per
+     * tile of that kernel for y/z lines (0: the default). */
+    int32_t variant, tma, tile_lines;
 } cbs_plan_info;
 
 /* Create a plan: validates the descriptor, chooses p when segments == 0,
@@ -176,15 +184,38 @@ cbs_status cbs_plan_set_bands(cbs_plan* plan, const void* bands);
 
 /* Autotuner: times every admissible partition count for `desc` (p = 1..32
  * lanes for lines that fit one warp, divisors giving 64..8192-row segments
- * for long lines) on scratch buffers it allocates and frees on the current
- * device (inputs filled with a fixed pattern), with `reps` timed solves each
- * after two warm-ups, and records the fastest in a per-process cache keyed by
- * (dims, direction, bandwidth, precision, dtypes, stencil, bands kind).
- * Later cbs_plan_create calls with segments == 0 use the cached choice.
+ * for long lines), and for on-chip plans both kernel variants
+ * (cbs_plan_set_variant), on scratch buffers it allocates and frees on the
+ * current device (inputs filled with a fixed pattern), with `reps` timed
+ * solves each after two warm-ups, and records the fastest in a per-process
+ * cache keyed by (dims, direction, bandwidth, precision, dtypes, stencil,
+ * bands kind).  Later cbs_plan_create calls with segments == 0 use the
+ * cached choice (partition count and variant).
  * Writes the choice to *best_segments and its time per solve to *best_ms
  * (either may be NULL).  Synchronises the device.  Errors: as
  * cbs_plan_create, CUDA, NO_MEMORY. */
 cbs_status cbs_autotune(const cbs_desc* desc, int32_t reps, int32_t* best_segments, double* best_ms);
+
+/* Kernel variant and tile walk of an on-chip plan (cbs_plan_info kernel ==
+ * 0), used by cbs_solve and cbs_solve_transpose.  variant:
+ *   0 = automatic (default): the TMA-fed refinement kernel when the plan
+ *       qualifies -- FP32_REFINE(_I64) with one sweep, cyclic tridiagonal
+ *       Toeplitz bands, 32 partitions of 8 or 16 rows (n = 256 or 512), the
+ *       central stencil of at most two terms or none, FP64 in and out, both
+ *       arrays on 16-byte boundaries, even nx for y/z lines -- otherwise the
+ *       pipelined / staged line kernels;
+ *   1 = always the pipelined / staged line kernels.
+ * Both give results within the refinement's tolerance of the FP64 solution
+ * (they round differently).  tile_lines: the tile shape of the TMA kernel,
+ * adjacent lines per tile (for y/z lines also the contiguous bytes per row of
+ * a tile load: 8 bytes per line): x-lines 4 or 8 (a warp per line, two tile
+ * buffers per CTA); y/z lines 4, 8 (as x), 16 (one buffer, 8 warps of two
+ * lines each) or 32 (16 lines, 16 warps, two buffers); 0 = the default of
+ * the direction.  Only the arrangement of the work changes, not the
+ * results.  cbs_autotune times the variants and tile shapes with the
+ * partition counts and records the fastest.  Errors: INVALID_ARG (variant
+ * not 0 or 1, tile_lines not 0, 4, 8, 16 or 32, NULL plan). */
+cbs_status cbs_plan_set_variant(cbs_plan* plan, int32_t variant, int32_t tile_lines);
 
 /* Destroy a plan and free its device memory (synchronises the device). */
 cbs_status cbs_plan_destroy(cbs_plan* plan);
@@ -214,8 +245,12 @@ cbs_status cbs_solve_transpose(cbs_plan* plan, const void* g, const void* x,
 cbs_status cbs_band_grad(cbs_plan* plan, const void* lambda, const void* x,
                          void* grad_bands, void* stream);
 
-/* Read (and clear) the plan's device status word: CBS_OK, CBS_ERR_SINGULAR or
- * CBS_ERR_TIMEOUT from kernels that already ran.  Synchronises the device. */
+/* Read (and clear) the plan's device status word from kernels that already
+ * ran: CBS_OK; CBS_ERR_SINGULAR (a variable-band solve met a zero or
+ * non-finite pivot or interface block); CBS_ERR_RANGE (an FP32 mode met an
+ * input or result outside its range); CBS_ERR_TIMEOUT (a bounded wait of the
+ * TMA-fed kernel for its tile expired -- the only device wait in the
+ * library).  Synchronises the device. */
 cbs_status cbs_status_poll(cbs_plan* plan, int32_t* device_status);
 
 /* Fill *info with the plan's choices and interface schedule counts. */

@@ -16,20 +16,21 @@ LIB_PATH = os.path.join(_HERE, "libcbs.so")
 
 # status codes (cbs.h)
 CBS_OK, CBS_ERR_INVALID_ARG, CBS_ERR_UNSUPPORTED, CBS_ERR_SINGULAR, CBS_ERR_TIMEOUT, CBS_ERR_CUDA, \
-    CBS_ERR_NO_MEMORY = range(7)
+    CBS_ERR_NO_MEMORY, CBS_ERR_RANGE = range(8)
 CBS_FP64, CBS_FP32, CBS_FP32_REFINE, CBS_FP32_REFINE_I64 = 0, 1, 2, 3
 CBS_DTYPE_F64, CBS_DTYPE_F32 = 0, 1
 CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE = 0, 1
 CBS_RHS_NONE, CBS_RHS_CENTRAL, CBS_RHS_STAGGERED, CBS_RHS_MIDPOINT = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA",
-                6: "NO_MEMORY"}
+                6: "NO_MEMORY", 7: "RANGE"}
 
 # every entry point declared in include/cbs.h
 EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transpose", "cbs_band_grad",
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
            "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
-           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune")
+           "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune",
+           "cbs_plan_set_variant")
 
 
 class CbsError(RuntimeError):
@@ -70,6 +71,7 @@ class cbs_plan_info(ctypes.Structure):
         ("lines", ctypes.c_int64),
         ("message_stages", ctypes.c_int32), ("message_stages_f32", ctypes.c_int32),
         ("inner_message_stages", ctypes.c_int32), ("inner_message_stages_f32", ctypes.c_int32),
+        ("variant", ctypes.c_int32), ("tma", ctypes.c_int32), ("tile_lines", ctypes.c_int32),
     ]
 
 
@@ -100,6 +102,7 @@ def _load():
         "cbs_plan_set_bands": ([vp, vp], st),
         "cbs_solve_noalloc": ([vp, vp, vp, vp], st),
         "cbs_autotune": ([P(cbs_desc), i32, P(i32), P(ctypes.c_double)], st),
+        "cbs_plan_set_variant": ([vp, i32, i32], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -137,6 +140,13 @@ def cbs_plan_destroy(plan: int) -> None:
 
 def cbs_plan_set_bands(plan: int, bands: int) -> None:
     _check(_lib.cbs_plan_set_bands(plan, bands))
+
+
+def cbs_plan_set_variant(plan: int, variant: int, tile_lines: int = 0) -> None:
+    """variant 0 = automatic (TMA-fed refinement kernel where it qualifies),
+    1 = the pipelined / staged line kernels; tile_lines: lines per tile of
+    the TMA kernel on y/z lines (4, 8 or 16; 0 = the default, 8)."""
+    _check(_lib.cbs_plan_set_variant(plan, variant, tile_lines))
 
 
 def cbs_solve(plan: int, inp: int, out: int, stream: int = 0) -> None:

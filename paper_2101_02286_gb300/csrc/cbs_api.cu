@@ -31,22 +31,27 @@ cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitem
 size_t batch_problem_bytes();
 void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant);
 constexpr int kBatchMax = 256;
+bool tma_eligible(int mode, int KS, bool staggered, bool in64, bool out64, const LineArgs& a, const DevLineTables& t);
+cudaError_t launch_tma(int mode, int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, cudaStream_t s);
 }  // namespace cbs
 
 namespace {
 
-// autotuner cache: descriptor key -> partitions per line
+// autotuner cache: descriptor key -> (partitions per line, kernel variant)
 using TuneKey = std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int>;
+struct TuneChoice {
+  int segments = 0, variant = 0, tile_lines = 0;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, TuneChoice> g_tune_cache;
 TuneKey tune_key(const cbs_desc* d) {
   return TuneKey(d->dims[0], d->dims[1], d->dims[2], d->direction, d->bandwidth, d->precision, d->in_dtype,
                  d->out_dtype, d->rhs_kind, d->rhs_terms, d->lhs_kind);
 }
-int tuned_segments(const cbs_desc* d) {
+TuneChoice tuned_choice(const cbs_desc* d) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune_cache.find(tune_key(d));
-  return it == g_tune_cache.end() ? 0 : it->second;
+  return it == g_tune_cache.end() ? TuneChoice() : it->second;
 }
 
 thread_local std::string g_err;
@@ -59,6 +64,27 @@ cbs_status fail(cbs_status s, const std::string& msg) {
 cbs_status cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return CBS_ERR_CUDA;
+}
+
+// Autotuner input: values in [lo, lo + span) from a hash of the element
+// index (varying, so the kernels take their usual paths; a constant field
+// would make every derivative zero).
+template <typename T>
+__global__ void tune_fill_kernel(T* p, int64_t n, double lo, double span) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 0x9E3779B9u ^ (uint32_t)(i >> 32);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    p[i] = (T)(lo + span * (double)(h >> 8) * (1.0 / 16777216.0));
+  }
+}
+
+cudaError_t tune_fill(void* p, int64_t n, bool f64, double lo, double span) {
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  if (f64) tune_fill_kernel<double><<<blocks, 256>>>((double*)p, n, lo, span);
+  else tune_fill_kernel<float><<<blocks, 256>>>((float*)p, n, lo, span);
+  return cudaGetLastError();
 }
 
 int next_pow2(int p) {
@@ -453,6 +479,25 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   return CBS_OK;
 }
 
+// The on-chip line kernel of plan P with arguments a: `ks` stencil terms
+// compiled in, staggered stencil or not, element types tin -> tout.  Variant
+// 0 takes the TMA-fed refinement kernel when the plan and arrays qualify.
+cudaError_t launch_line_plan(const cbs_plan* P, const LineArgs& a, int ks, bool stag, int tin, int tout,
+                             cudaStream_t s) {
+  const int mode = mode_of(P->desc.precision);
+  if (P->variant == 0 && tma_eligible(mode, ks, stag, tin == CBS_DTYPE_F64, tout == CBS_DTYPE_F64, a, P->dev)) {
+    const cudaError_t e = launch_tma(mode, ks, a, P->dev, P->tile_lines, s);
+    if (e != cudaErrorNotSupported) return e;  // NotSupported: a tensor map was refused
+  }
+  const int R = P->r;
+#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, stag, tin, tout, a, P->dev, s)
+  if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
+  if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
+  if (mode == kModeRefine) return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
+  return (R == 1) ? CBS_L(3, 1) : CBS_L(3, 2);
+#undef CBS_L
+}
+
 }  // namespace
 
 extern "C" {
@@ -536,7 +581,12 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   }
   P->nlines = d->dims[0] * d->dims[1] * d->dims[2] / P->n;
   P->var = d->lhs_kind == CBS_LHS_VARIABLE;
-  int p = d->segments ? d->segments : tuned_segments(d);
+  const TuneChoice tuned = tuned_choice(d);
+  int p = d->segments ? d->segments : tuned.segments;
+  if (!d->segments && tuned.segments) {
+    P->variant = tuned.variant;
+    P->tile_lines = tuned.tile_lines;
+  }
   if (p) {
     cbs_desc dd = *d;
     dd.segments = p;
@@ -716,6 +766,28 @@ cbs_status cbs_plan_info_get(const cbs_plan* P, cbs_plan_info* info) {
     info->inner_message_stages = count(P->inner, 1);
     info->inner_message_stages_f32 = count(P->inner, 2);
   }
+  info->variant = P->variant;
+  info->tile_lines = P->tile_lines;
+  if (P->kind == 0 && !P->var) {
+    static const double aligned[2] = {0.0, 0.0};  // any 16-byte aligned address stands in for the arrays
+    LineArgs a = P->args;
+    void* al = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(aligned) + 15) & ~(uintptr_t)15);
+    a.in = al;
+    a.out = al;
+    info->tma = tma_eligible(mode_of(P->desc.precision), P->ks, is_staggered(&P->desc),
+                             P->desc.in_dtype == CBS_DTYPE_F64, P->desc.out_dtype == CBS_DTYPE_F64, a, P->dev)
+                    ? 1 : 0;
+  }
+  return CBS_OK;
+}
+
+cbs_status cbs_plan_set_variant(cbs_plan* P, int32_t variant, int32_t tile_lines) {
+  if (!P) return fail(CBS_ERR_INVALID_ARG, "null plan");
+  if (variant != 0 && variant != 1) return fail(CBS_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (tile_lines != 0 && tile_lines != 4 && tile_lines != 8 && tile_lines != 16 && tile_lines != 32)
+    return fail(CBS_ERR_INVALID_ARG, "tile_lines must be 0, 4, 8, 16 or 32");
+  P->variant = variant;
+  P->tile_lines = tile_lines;
   return CBS_OK;
 }
 
@@ -751,15 +823,8 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
   LineArgs a = P->args;
   a.in = in;
   a.out = out;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaErrorInvalidValue;
-  const int R = P->r;
-#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, P->ks, is_staggered(&d), d.in_dtype, d.out_dtype, a, P->dev, s)
-  if (mode == kModeF64) e = (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
-  else if (mode == kModeF32) e = (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
-  else if (mode == kModeRefine) e = (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
-  else e = (R == 1) ? CBS_L(3, 1) : CBS_L(3, 2);
-#undef CBS_L
+  const cudaError_t e =
+      launch_line_plan(P, a, P->ks, is_staggered(&d), d.in_dtype, d.out_dtype, (cudaStream_t)stream);
   if (e == cudaErrorNotSupported) return fail(CBS_ERR_UNSUPPORTED, "no kernel variant for these element types");
   if (e != cudaSuccess) return cuda_fail(e, "line kernel launch");
   g_launches = 1;
@@ -793,16 +858,9 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
   if (d.in_dtype != d.out_dtype) return fail(CBS_ERR_UNSUPPORTED, "transpose needs in_dtype == out_dtype");
   if (!d.cyclic) return fail(CBS_ERR_UNSUPPORTED, "transpose of acyclic plans");
   if (grad_bands) return fail(CBS_ERR_INVALID_ARG, "Toeplitz plans have no band field");
-  const int mode = mode_of(d.precision);
-  const int R = P->r;
   int launches = 0;
   auto run = [&](const LineArgs& a, int ks) -> cudaError_t {
-#define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, ks > 0 && is_staggered(&d), d.out_dtype, d.in_dtype, a, P->dev, s)
-    if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
-    if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
-    if (mode == kModeRefine) return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
-    return (R == 1) ? CBS_L(3, 1) : CBS_L(3, 2);
-#undef CBS_L
+    return launch_line_plan(P, a, ks, ks > 0 && is_staggered(&d), d.out_dtype, d.in_dtype, s);
   };
   if (lambda) {
     LineArgs a = P->args;
@@ -982,11 +1040,10 @@ cbs_status cbs_autotune(const cbs_desc* d, int32_t reps, int32_t* best_segments,
   cudaError_t e = cudaMalloc(&in, elems * isz);
   if (e == cudaSuccess) e = cudaMalloc(&out, elems * osz);
   if (e == cudaSuccess && d->lhs_kind == CBS_LHS_VARIABLE) e = cudaMalloc(&bands, elems * isz);
-  // fixed byte patterns: 0x3F.. is a normal finite value in FP64 (4.8e-4)
-  // and FP32 (0.75); 0x3E.. keeps variable bands diagonally dominant (FP64
-  // 7.1e-9, FP32 0.19).  Solve times do not depend on the values.
-  if (e == cudaSuccess) e = cudaMemset(in, 0x3F, elems * isz);
-  if (e == cudaSuccess && bands) e = cudaMemset(bands, 0x3E, elems * isz);
+  // inputs: varying values in [-1, 1); variable bands in [0.1, 0.4)
+  // (diagonally dominant), as the kernels' fast paths see real data
+  if (e == cudaSuccess) e = tune_fill(in, elems, d->in_dtype == CBS_DTYPE_F64, -1.0, 2.0);
+  if (e == cudaSuccess && bands) e = tune_fill(bands, elems, d->in_dtype == CBS_DTYPE_F64, 0.1, 0.3);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -995,7 +1052,7 @@ cbs_status cbs_autotune(const cbs_desc* d, int32_t reps, int32_t* best_segments,
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(e, "autotune buffers");
   }
-  int best = 0;
+  TuneChoice best;
   double bms = 1e300;
   for (int p : cand) {
     cbs_desc dd = *d;
@@ -1003,32 +1060,50 @@ cbs_status cbs_autotune(const cbs_desc* d, int32_t reps, int32_t* best_segments,
     if (bands) dd.bands = bands;
     cbs_plan* P = nullptr;
     if (cbs_plan_create(&P, &dd) != CBS_OK) continue;  // not admissible for this kernel
-    bool ok = true;
-    for (int w = 0; w < 2 && ok; w++) ok = cbs_solve(P, in, out, nullptr) == CBS_OK;
-    float ms = 0.f;
-    if (ok) {
-      cudaEventRecord(e0, nullptr);
-      for (int k = 0; k < reps && ok; k++) ok = cbs_solve(P, in, out, nullptr) == CBS_OK;
-      cudaEventRecord(e1, nullptr);
-      ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cbs_plan_info info;
+    cbs_plan_info_get(P, &info);
+    // (variant, tile shape) pairs: the line kernels, and for plans the TMA
+    // kernel takes, its tile shapes for the direction
+    std::vector<std::pair<int, int>> kinds = {{0, 0}};
+    if (info.tma) {
+      kinds = {{1, 0}, {0, 4}, {0, 8}};
+      if (d->direction != 0) {
+        kinds.push_back({0, 16});
+        kinds.push_back({0, 32});
+      }
+    }
+    for (const auto& kind : kinds) {
+      P->variant = kind.first;
+      P->tile_lines = kind.second;
+      bool ok = true;
+      for (int w = 0; w < 2 && ok; w++) ok = cbs_solve(P, in, out, nullptr) == CBS_OK;
+      float ms = 0.f;
+      if (ok) {
+        cudaEventRecord(e0, nullptr);
+        for (int k = 0; k < reps && ok; k++) ok = cbs_solve(P, in, out, nullptr) == CBS_OK;
+        cudaEventRecord(e1, nullptr);
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      }
+      if (ok && ms / reps < bms) {
+        bms = ms / reps;
+        best.segments = p;
+        best.variant = kind.first;
+        best.tile_lines = kind.second;
+      }
     }
     cbs_plan_destroy(P);
-    if (ok && ms / reps < bms) {
-      bms = ms / reps;
-      best = p;
-    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(in);
   cudaFree(out);
   if (bands) cudaFree(bands);
-  if (!best) return fail(CBS_ERR_UNSUPPORTED, "no admissible partition count for this descriptor");
+  if (!best.segments) return fail(CBS_ERR_UNSUPPORTED, "no admissible partition count for this descriptor");
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[tune_key(d)] = best;
   }
-  if (best_segments) *best_segments = best;
+  if (best_segments) *best_segments = best.segments;
   if (best_ms) *best_ms = bms;
   return CBS_OK;
 }

@@ -71,7 +71,8 @@ class Plan:
 
     def __init__(self, shape_zyx, direction: int, **kw):
         """kw as for make_desc; segments="tune" times every admissible
-        partition count first (cbs_autotune) and uses the fastest."""
+        partition count and kernel variant first (cbs_autotune) and creates
+        the plan from the tuner's record (segments = 0)."""
         self.shape = tuple(int(s) for s in shape_zyx)
         self.direction = int(direction)
         self.in_dtype = kw.get("in_dtype", torch.float64)
@@ -82,7 +83,7 @@ class Plan:
             kw = dict(kw, segments=0)
         self.desc = make_desc(self.shape, direction, **kw)
         if tune:
-            self.desc.segments, self.tuned_ms = abi.cbs_autotune(self.desc)
+            _, self.tuned_ms = abi.cbs_autotune(self.desc)
         self.handle = abi.cbs_plan_create(self.desc)
 
     def info(self) -> dict:
