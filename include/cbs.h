@@ -13,7 +13,9 @@
  *   - y_i = D_i^{-1} b_i inside each partition (Eq. 17);
  *   - the reduced cyclic block-tridiagonal interface system A-hat x~ = b-hat
  *     (Eq. 11, 18-21) is solved by block PCR with detach/reattach
- *     (Algorithms 1-4), always in FP64;
+ *     (Algorithms 1-4), in the precision of the solve: FP64 for CBS_FP64 and
+ *     CBS_FP32_REFINE_I64, FP32 for CBS_FP32 and CBS_FP32_REFINE (see the
+ *     precision enum);
  *   - back-substitution x_i = y_i - S_i x~_i - R_i x~_{i+1} (Eq. 22).
  *
  * Everything RHS-independent (S_i, R_i, the reduced blocks and the PCR
@@ -28,8 +30,9 @@
  *   - A field has dims (nx, ny, nz) with x contiguous: element (i, j, k) is at
  *     offset i + nx * (j + ny * k).  Lines run along `direction`.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
- *     Launches are asynchronous; device-side errors are reported through
- *     cbs_status_poll.
+ *     Launches are asynchronous; device-side errors (a singular
+ *     variable-band system, values outside the range of the FP32 modes, an
+ *     expired wait) are reported through cbs_status_poll.
  *   - Every call returns a cbs_status; no C++ exception crosses the ABI.
  *     cbs_last_error_string() describes the last failure of the calling thread.
  *   - A plan may be used from several host threads, but concurrent launches on
@@ -217,6 +220,16 @@ cbs_status cbs_autotune(const cbs_desc* desc, int32_t reps, int32_t* best_segmen
  * not 0 or 1, tile_lines not 0, 4, 8, 16 or 32, NULL plan). */
 cbs_status cbs_plan_set_variant(cbs_plan* plan, int32_t variant, int32_t tile_lines);
 
+/* Fault injection for tests of the device timeout path (no GPU fault is
+ * involved).  kind 1: in solves that run the TMA-fed refinement kernel
+ * (cbs_plan_info tma == 1, variant 0), CTA 0 does not issue its first tile
+ * load and the limit of the tile waits drops from 1 s to 1 ms, so that wait
+ * expires: the kernel sets CBS_ERR_TIMEOUT in the status word, lets its
+ * other load in flight land (bounded wait), and the CTA returns; the
+ * context stays usable and the output of the affected CTA's tiles is not
+ * written.  kind 0: no fault (default).  Errors: INVALID_ARG. */
+cbs_status cbs_plan_inject_fault(cbs_plan* plan, int32_t kind);
+
 /* Destroy a plan and free its device memory (synchronises the device). */
 cbs_status cbs_plan_destroy(cbs_plan* plan);
 
@@ -287,6 +300,9 @@ cbs_status cbs_batch_destroy(cbs_batch* batch);
  * graph when the pointers are fixed. */
 cbs_status cbs_batch_solve(cbs_batch* batch, const void* const* ins,
                            void* const* outs, void* stream);
+/* Read (and clear) the device status words of every problem of the batch,
+ * as cbs_status_poll does for a plan; *device_status is the first non-OK
+ * value found (problem order), else CBS_OK.  Synchronises the device. */
 cbs_status cbs_batch_status_poll(cbs_batch* batch, int32_t* device_status);
 
 /* Allocation-free variant of cbs_solve for long-line plans (cbs_plan_info

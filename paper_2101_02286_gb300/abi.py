@@ -30,7 +30,7 @@ EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transp
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
            "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
            "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune",
-           "cbs_plan_set_variant")
+           "cbs_plan_set_variant", "cbs_plan_inject_fault")
 
 
 class CbsError(RuntimeError):
@@ -103,6 +103,7 @@ def _load():
         "cbs_solve_noalloc": ([vp, vp, vp, vp], st),
         "cbs_autotune": ([P(cbs_desc), i32, P(i32), P(ctypes.c_double)], st),
         "cbs_plan_set_variant": ([vp, i32, i32], st),
+        "cbs_plan_inject_fault": ([vp, i32], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -147,6 +148,12 @@ def cbs_plan_set_variant(plan: int, variant: int, tile_lines: int = 0) -> None:
     1 = the pipelined / staged line kernels; tile_lines: lines per tile of
     the TMA kernel on y/z lines (4, 8 or 16; 0 = the default, 8)."""
     _check(_lib.cbs_plan_set_variant(plan, variant, tile_lines))
+
+
+def cbs_plan_inject_fault(plan: int, kind: int) -> None:
+    """Test of the device timeout path (1: a tile wait of the TMA kernel
+    expires after 1 ms; 0: none)."""
+    _check(_lib.cbs_plan_inject_fault(plan, kind))
 
 
 def cbs_solve(plan: int, inp: int, out: int, stream: int = 0) -> None:

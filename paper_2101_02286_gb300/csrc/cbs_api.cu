@@ -32,7 +32,8 @@ size_t batch_problem_bytes();
 void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant);
 constexpr int kBatchMax = 256;
 bool tma_eligible(int mode, int KS, bool staggered, bool in64, bool out64, const LineArgs& a, const DevLineTables& t);
-cudaError_t launch_tma(int mode, int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, cudaStream_t s);
+cudaError_t launch_tma(int mode, int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, int fault,
+                       cudaStream_t s);
 }  // namespace cbs
 
 namespace {
@@ -486,7 +487,7 @@ cudaError_t launch_line_plan(const cbs_plan* P, const LineArgs& a, int ks, bool 
                              cudaStream_t s) {
   const int mode = mode_of(P->desc.precision);
   if (P->variant == 0 && tma_eligible(mode, ks, stag, tin == CBS_DTYPE_F64, tout == CBS_DTYPE_F64, a, P->dev)) {
-    const cudaError_t e = launch_tma(mode, ks, a, P->dev, P->tile_lines, s);
+    const cudaError_t e = launch_tma(mode, ks, a, P->dev, P->tile_lines, P->fault, s);
     if (e != cudaErrorNotSupported) return e;  // NotSupported: a tensor map was refused
   }
   const int R = P->r;
@@ -781,6 +782,13 @@ cbs_status cbs_plan_info_get(const cbs_plan* P, cbs_plan_info* info) {
   return CBS_OK;
 }
 
+cbs_status cbs_plan_inject_fault(cbs_plan* P, int32_t kind) {
+  if (!P) return fail(CBS_ERR_INVALID_ARG, "null plan");
+  if (kind != 0 && kind != 1) return fail(CBS_ERR_INVALID_ARG, "fault kind must be 0 or 1");
+  P->fault = kind;
+  return CBS_OK;
+}
+
 cbs_status cbs_plan_set_variant(cbs_plan* P, int32_t variant, int32_t tile_lines) {
   if (!P) return fail(CBS_ERR_INVALID_ARG, "null plan");
   if (variant != 0 && variant != 1) return fail(CBS_ERR_INVALID_ARG, "variant must be 0 or 1");
@@ -1017,9 +1025,13 @@ cbs_status cbs_batch_solve(cbs_batch* B, const void* const* ins, void* const* ou
 
 cbs_status cbs_batch_status_poll(cbs_batch* B, int32_t* st) {
   if (!B || !st) return fail(CBS_ERR_INVALID_ARG, "null argument");
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return cuda_fail(e, "batch status");
   *st = CBS_OK;
+  for (cbs_plan* P : B->plans) {  // each problem's kernels report to its plan's status word
+    int32_t v = CBS_OK;
+    const cbs_status r = cbs_status_poll(P, &v);
+    if (r) return r;
+    if (v && !*st) *st = v;
+  }
   return CBS_OK;
 }
 

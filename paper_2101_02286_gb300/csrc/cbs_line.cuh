@@ -1590,6 +1590,14 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
     else if constexpr (FULL) residual_sym<R, M, false>(bh, bl, xh, xh, v, i, t, xch);
     else residual_df<R, M, false, FULL>(bh, bl, xh, xh, v, size, i, t, xch);
     solve_partition<float, R, M, TIR, FULL>(v, size, i, lane_ok, t, xch);
+    // an input of 2^128 or more (inf after the split), or a non-finite one,
+    // leaves x0 or the correction non-finite: CBS_ERR_RANGE (integer tests)
+    unsigned nonfin = 0u;
+#pragma unroll
+    for (int k = 0; k < M; k++)
+      nonfin |= ((__float_as_uint(xh[k]) & 0x7f800000u) == 0x7f800000u) ||
+                ((__float_as_uint(v[k]) & 0x7f800000u) == 0x7f800000u) ? 1u : 0u;
+    if (nonfin && ok) atomicExch(a.status, CBS_ERR_RANGE);
     if (a.sweeps < 2) {
       // x = x0 + delta: one FP64 add (the FP64 pipe is idle otherwise on this
       // path); x0 is widened with integer operations, delta too in the

@@ -29,7 +29,8 @@ struct cbs_plan {
   cbs_desc desc;
   int n = 0, r = 1, kind = 0, M = 16, ks = 0;
   int variant = 0;     // cbs_plan_set_variant: 0 automatic (TMA kernel where it qualifies), 1 line kernels
-  int tile_lines = 0;  // TMA kernel, y/z lines: lines per tile (0: the default, 8)
+  int tile_lines = 0;  // TMA kernel: lines per tile (0: the default of the direction)
+  int fault = 0;       // cbs_plan_inject_fault (test of the timeout path)
   int64_t nlines = 0;
   LineTables host;
   DevLineTables dev;

@@ -66,6 +66,8 @@ bool make_iface(const DevLineTables& D, bool fp64, TmaIface& f) {
   }
   f.scaled = scale;
   f.scalef = (float)scale;
+  f.wait_ns = 1000000000ull;  // 1 s
+  f.fault = 0;
   return true;
 }
 
@@ -89,12 +91,13 @@ bool tma_eligible(int mode, int KS, bool staggered, bool in64, bool out64, const
 
 // cudaErrorNotSupported: the driver refused a tensor map (the caller then
 // runs the pipelined line kernel instead).
-cudaError_t launch_tma(int mode, int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, cudaStream_t s) {
+cudaError_t launch_tma(int mode, int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, int fault,
+                       cudaStream_t s) {
   if (mode == kModeRefineI64)
-    return t.rows_big == 16 ? launch_tma_m<16, double>(KS, a, t, tile_lines, s)
-                            : launch_tma_m<8, double>(KS, a, t, tile_lines, s);
-  return t.rows_big == 16 ? launch_tma_m<16, float>(KS, a, t, tile_lines, s)
-                          : launch_tma_m<8, float>(KS, a, t, tile_lines, s);
+    return t.rows_big == 16 ? launch_tma_m<16, double>(KS, a, t, tile_lines, fault, s)
+                            : launch_tma_m<8, double>(KS, a, t, tile_lines, fault, s);
+  return t.rows_big == 16 ? launch_tma_m<16, float>(KS, a, t, tile_lines, fault, s)
+                          : launch_tma_m<8, float>(KS, a, t, tile_lines, fault, s);
 }
 
 }  // namespace cbs

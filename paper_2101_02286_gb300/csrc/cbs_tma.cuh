@@ -68,13 +68,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of barrier `bar`; false after ~1 s without it.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+// Wait for phase `parity` of barrier `bar`; false after `limit_ns` without it.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (int spin = 0; spin < (1 << 26); spin++) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((spin & 255) == 255 && global_ns() - t0 > 1000000000ull) return false;
+    if ((spin & 255) == 255 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -147,6 +147,11 @@ struct TmaIface {
   double cd[kTmaMaxMsg][3];  // in FP64 (interface of the _I64 mode)
   float scalef;
   double scaled;
+  // limit of a tile wait (1 s), and the fault injected for tests of the
+  // timeout path: 1 = CTA 0 does not issue its first tile load, so its wait
+  // for that tile expires (cbs_plan_inject_fault)
+  unsigned long long wait_ns;
+  int fault;
 };
 
 // ---------------------------------------------------------------- shared memory
@@ -539,14 +544,14 @@ __global__ void __launch_bounds__(W * 32, tma_ctas_per_sm<M, TL, W, NBUF>())
   __syncthreads();
   int tile = blockIdx.x;
   if (leader) {
-    if (tile < ntiles) load(tile, 0);
+    if (tile < ntiles && !(f.fault == 1 && blockIdx.x == 0)) load(tile, 0);
     if (NBUF == 2 && tile + (int)gridDim.x < ntiles) load(tile + gridDim.x, 1);
   }
   int flag = 0;
   for (int it = 0; tile < ntiles; it++, tile += gridDim.x) {
     const int b = NBUF == 2 ? (it & 1) : 0;
     const unsigned parity = (unsigned)(NBUF == 2 ? (it >> 1) : it) & 1u;
-    const bool arrived = mbar_wait_bounded(b ? bar1 : bar0, parity);
+    const bool arrived = mbar_wait_bounded(b ? bar1 : bar0, parity, f.wait_ns);
     const int nl = STRIDED ? (int)min((int64_t)TL, a.nx - (int64_t)(tile % gx) * TL)
                            : (int)min((int64_t)TL, a.nlines - (int64_t)tile * TL);
 #pragma unroll 1
@@ -560,9 +565,9 @@ __global__ void __launch_bounds__(W * 32, tma_ctas_per_sm<M, TL, W, NBUF>())
         atomicExch(a.status, CBS_ERR_TIMEOUT);
         // give the overdue load (and the next one, if issued) another bounded
         // wait to land before the CTA's shared memory is released
-        mbar_wait_bounded(b ? bar1 : bar0, parity);
+        if (!(f.fault == 1 && blockIdx.x == 0 && it == 0)) mbar_wait_bounded(b ? bar1 : bar0, parity, f.wait_ns);
         if (NBUF == 2 && tile + (int)gridDim.x < ntiles)
-          mbar_wait_bounded(b ? bar0 : bar1, (unsigned)((it + 1) >> 1) & 1u);
+          mbar_wait_bounded(b ? bar0 : bar1, (unsigned)((it + 1) >> 1) & 1u, f.wait_ns);
       }
       break;
     }

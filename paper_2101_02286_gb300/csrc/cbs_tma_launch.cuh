@@ -47,10 +47,14 @@ bool tile_map(CUtensorMap* map, const void* ptr, const LineArgs& a) {
 constexpr int kTmaMaxDevices = 64;
 
 template <int M, int KS, typename TIR, bool STRIDED, int TL, int W, int NBUF>
-cudaError_t launch_tma_t(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
+cudaError_t launch_tma_t(const LineArgs& a, const DevLineTables& t, int fault, cudaStream_t s) {
   alignas(64) CUtensorMap tin, tout;
   TmaIface f;
   if (!make_iface(t, sizeof(TIR) == 8, f)) return cudaErrorNotSupported;
+  if (fault == 1) {  // test of the timeout path: a 1 ms limit on the wait that CTA 0 cannot satisfy
+    f.fault = 1;
+    f.wait_ns = 1000000ull;
+  }
   if (!tile_map<M, STRIDED, TL>(&tin, a.in, a) || !tile_map<M, STRIDED, TL>(&tout, a.out, a))
     return cudaErrorNotSupported;
   int gx = 1;
@@ -96,25 +100,25 @@ cudaError_t launch_tma_t(const LineArgs& a, const DevLineTables& t, cudaStream_t
 // 8 warps of two lines each) or, for 32, 16 lines with 16 warps and two
 // buffers.  0 = the default of the direction.
 template <int M, typename TIR>
-cudaError_t launch_tma_m(int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, cudaStream_t s);
+cudaError_t launch_tma_m(int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, int fault, cudaStream_t s);
 
 #define CBS_DEFINE_TMA_LAUNCH(M, TIR)                                                                        \
   template <>                                                                                                \
-  cudaError_t launch_tma_m<M, TIR>(int KS, const LineArgs& a, const DevLineTables& t, int tl, cudaStream_t s) { \
+  cudaError_t launch_tma_m<M, TIR>(int KS, const LineArgs& a, const DevLineTables& t, int tl, int fault, cudaStream_t s) { \
     if (a.dir == 0) {                                                                                        \
-      if (tl == 8) return KS == 2 ? launch_tma_t<M, 2, TIR, false, 8, 8, 2>(a, t, s)                         \
-                                  : launch_tma_t<M, 0, TIR, false, 8, 8, 2>(a, t, s);                        \
-      return KS == 2 ? launch_tma_t<M, 2, TIR, false, 4, 4, 2>(a, t, s)                                      \
-                     : launch_tma_t<M, 0, TIR, false, 4, 4, 2>(a, t, s);                                     \
+      if (tl == 8) return KS == 2 ? launch_tma_t<M, 2, TIR, false, 8, 8, 2>(a, t, fault, s)                         \
+                                  : launch_tma_t<M, 0, TIR, false, 8, 8, 2>(a, t, fault, s);                        \
+      return KS == 2 ? launch_tma_t<M, 2, TIR, false, 4, 4, 2>(a, t, fault, s)                                      \
+                     : launch_tma_t<M, 0, TIR, false, 4, 4, 2>(a, t, fault, s);                                     \
     }                                                                                                        \
     if (tl == 0) tl = a.dir == 1 ? 4 : 16;                                                                   \
-    if (tl == 16) return KS == 2 ? launch_tma_t<M, 2, TIR, true, 16, 8, 1>(a, t, s)                          \
-                                 : launch_tma_t<M, 0, TIR, true, 16, 8, 1>(a, t, s);                         \
-    if (tl == 32) return KS == 2 ? launch_tma_t<M, 2, TIR, true, 16, 16, 2>(a, t, s)                         \
-                                 : launch_tma_t<M, 0, TIR, true, 16, 16, 2>(a, t, s);                        \
-    if (tl == 8) return KS == 2 ? launch_tma_t<M, 2, TIR, true, 8, 8, 2>(a, t, s)                            \
-                                : launch_tma_t<M, 0, TIR, true, 8, 8, 2>(a, t, s);                           \
-    return KS == 2 ? launch_tma_t<M, 2, TIR, true, 4, 4, 2>(a, t, s) : launch_tma_t<M, 0, TIR, true, 4, 4, 2>(a, t, s); \
+    if (tl == 16) return KS == 2 ? launch_tma_t<M, 2, TIR, true, 16, 8, 1>(a, t, fault, s)                          \
+                                 : launch_tma_t<M, 0, TIR, true, 16, 8, 1>(a, t, fault, s);                         \
+    if (tl == 32) return KS == 2 ? launch_tma_t<M, 2, TIR, true, 16, 16, 2>(a, t, fault, s)                         \
+                                 : launch_tma_t<M, 0, TIR, true, 16, 16, 2>(a, t, fault, s);                        \
+    if (tl == 8) return KS == 2 ? launch_tma_t<M, 2, TIR, true, 8, 8, 2>(a, t, fault, s)                            \
+                                : launch_tma_t<M, 0, TIR, true, 8, 8, 2>(a, t, fault, s);                           \
+    return KS == 2 ? launch_tma_t<M, 2, TIR, true, 4, 4, 2>(a, t, fault, s) : launch_tma_t<M, 0, TIR, true, 4, 4, 2>(a, t, fault, s); \
   }
 
 }  // namespace cbs

@@ -227,6 +227,15 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
   // geometrically with the partition size (diagonal dominance) and square at
   // every PCR step, so this usually ends the loop after a few steps.
   const T tiny = sizeof(T) == 8 ? T(8.673617379884035e-19) : T(9.313225746154785e-10);  // 2^-60, 2^-30
+  // Singular (or numerically singular) interface system: a block divided by
+  // that is zero, non-finite, or below 2^-40 (FP64) / 2^-16 (FP32) of the
+  // magnitude of its row -- e.g. alpha = 1/2 on a cyclic line of even length,
+  // whose symbol 1 + cos(theta) vanishes.  Reported as CBS_ERR_SINGULAR.
+  const T sthr = sizeof(T) == 8 ? T(9.094947017729282e-13) : T(1.52587890625e-05);  // 2^-40, 2^-16
+  bool sing = false;
+  auto check = [&](T den, T scale) {
+    if (!(fabs(den) > sthr * scale)) sing = true;  // also true for nan
+  };
   bool decoupled = false;
   for (int st = 0; st < t.nstage; st++) {
     if (!decoupled)
@@ -235,9 +244,16 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
       const int type = a.stage_type[st], s = a.stage_s[st], na = a.stage_na[st];
       if (!lane_ok) continue;
       if (type == kFinal) {
-        if (i < na) xt = xt * rcp_(t.cyclic ? (W + Lh + Uh) : W);
+        if (i < na) {
+          const T den = t.cyclic ? (W + Lh + Uh) : W;
+          check(den, fabs(W) + fabs(Lh) + fabs(Uh));
+          xt = xt * rcp_(den);
+        }
       } else if (type == kReattach) {
-        if (i >= na && i < na + s) xt = xt * rcp_(W);
+        if (i >= na && i < na + s) {
+          check(W, fabs(W) + fabs(Lh) + fabs(Uh));
+          xt = xt * rcp_(W);
+        }
       }
       continue;
     }
@@ -261,12 +277,14 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
     if (!lane_ok) continue;
     if (type == kDetach) {
       if (i >= na - s && i < na) {
+        check(W1, fabs(W1) + fabs(L1) + fabs(U1));
         const T k = Uh * rcp_(W1);
         W -= k * L1;
         xt -= k * X1;
         Uh = -k * U1;
       }
       if (i < s) {
+        check(W2, fabs(W2) + fabs(L2) + fabs(U2));
         const T k = Lh * rcp_(W2);
         W -= k * U2;
         xt -= k * X2;
@@ -274,6 +292,8 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
       }
     } else if (type == kPcr) {
       if (i < na) {
+        check(W1, fabs(W1) + fabs(L1) + fabs(U1));
+        check(W2, fabs(W2) + fabs(L2) + fabs(U2));
         const T kp = Uh * rcp_(W1), km = Lh * rcp_(W2);
         const T Wn = W - kp * L1 - km * U2;
         const T xn = xt - kp * X1 - km * X2;
@@ -284,9 +304,16 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
         Uh = Un;
       }
     } else if (type == kFinal) {
-      if (i < na) xt = xt * rcp_(t.cyclic ? (W + Lh + Uh) : W);
+      if (i < na) {
+        const T den = t.cyclic ? (W + Lh + Uh) : W;
+        check(den, fabs(W) + fabs(Lh) + fabs(Uh));
+        xt = xt * rcp_(den);
+      }
     } else {
-      if (i >= na && i < na + s) xt = (xt - Lh * X1 - Uh * X2) * rcp_(W);
+      if (i >= na && i < na + s) {
+        check(W, fabs(W) + fabs(Lh) + fabs(Uh));
+        xt = (xt - Lh * X1 - Uh * X2) * rcp_(W);
+      }
     }
   }
   const T xn = __shfl_sync(kFull, xt, next, pw);
@@ -296,6 +323,19 @@ __global__ void __launch_bounds__(256, 1) var_kernel(const VarArgs a, const DevL
   x[0] = xa;
 #pragma unroll
   for (int k = 1; k < M; k++) x[k] = y[k] - sc[k] * xa - rc[k] * xb;
+  // a zero or non-finite bulk pivot shows as a non-finite result (integer
+  // tests: no FP64-pipe work)
+  if (ok) {
+    unsigned nf = 0u;
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      if (k < size) {
+        if constexpr (sizeof(T) == 8) nf |= (((unsigned)__double2hiint((double)x[k]) & 0x7ff00000u) == 0x7ff00000u) ? 1u : 0u;
+        else nf |= ((__float_as_uint((float)x[k]) & 0x7f800000u) == 0x7f800000u) ? 1u : 0u;
+      }
+    }
+    if (nf || (lane_ok && sing)) atomicExch(a.status, CBS_ERR_SINGULAR);
+  }
 
   if (!ADJ) {
     __syncwarp();
