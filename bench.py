@@ -701,8 +701,10 @@ def main():
                               "kernel": "refine_tma_kernel" if info_ref[d]["tma"] and info_ref[d]["variant"] == 0
                               else "line_kernel_pipe",
                               "tile_lines": info_ref[d]["tile_lines"]} for d in range(3)}
-        # FP64 path: bound by the FP64 pipe; 15 algorithmic FP64 flops per unknown
-        fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+        # FP64 path: bound by the FP64 pipe; 15 algorithmic FP64 flops per
+        # unknown against the FP64 fma throughput measured on this device
+        from paper_2101_02286_gb300 import abi as _abi
+        fp64_peak_tflops = _abi.cbs_probe_fp64_peak()
         fp64_flops = 15.0 * n ** 3
         fp64_ach = fp64_flops / (sum(dir_64) / 3 * 1e-3) / 1e12
         clocks = sampler.summary()
@@ -737,7 +739,8 @@ def main():
                           "segments": [p.info()["segments"] for p in plans["fp64"]],
                           "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak_tflops,
                                        "unit": "TFLOP/s (FP64)", "frac": fp64_ach / fp64_peak_tflops,
-                                       "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+                                       "peak_source": "measured: cbs_probe_fp64_peak (register-resident "
+                                                      "FP64 fma chains, CUDA events)"},
                           "hbm_frac": 16.0 * n ** 3 / (sum(dir_64) / 3 * 1e-3) / 1e9 / hbm},
             "speedup_refine_vs_fp64": ms_64 / ms_ref,
             "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": "Gunknowns/s",

@@ -321,6 +321,15 @@ cbs_status cbs_batch_status_poll(cbs_batch* batch, int32_t* device_status);
  * cbs_solve. */
 cbs_status cbs_solve_noalloc(cbs_plan* plan, const void* in, void* out, void* stream);
 
+/* Measurement support for rooflines (not part of the method): the current
+ * device's FP64 fused multiply-add throughput, timed with CUDA events on a
+ * register-resident kernel of independent fma chains (4 CTAs of 256
+ * threads per SM, 2^14 steps of 8 chains per thread, after a warm-up
+ * launch).  Writes TFLOP/s (2 flops per fma) to *tflops.  Allocates and
+ * frees a small device buffer; synchronises the device.  Errors:
+ * INVALID_ARG, CUDA. */
+cbs_status cbs_probe_fp64_peak(double* tflops);
+
 /* Number of kernel launches the last cbs_solve / cbs_batch_solve of this
  * thread issued (for launch accounting). */
 int32_t cbs_last_launch_count(void);

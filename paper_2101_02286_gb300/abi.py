@@ -30,7 +30,7 @@ EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transp
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
            "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
            "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune",
-           "cbs_plan_set_variant", "cbs_plan_inject_fault")
+           "cbs_plan_set_variant", "cbs_plan_inject_fault", "cbs_probe_fp64_peak")
 
 
 class CbsError(RuntimeError):
@@ -104,6 +104,7 @@ def _load():
         "cbs_autotune": ([P(cbs_desc), i32, P(i32), P(ctypes.c_double)], st),
         "cbs_plan_set_variant": ([vp, i32, i32], st),
         "cbs_plan_inject_fault": ([vp, i32], st),
+        "cbs_probe_fp64_peak": ([P(ctypes.c_double)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -235,6 +236,13 @@ def cbs_batch_solve(batch: int, ins: list[int], outs: list[int], stream: int = 0
 def cbs_batch_status_poll(batch: int) -> int:
     v = ctypes.c_int32()
     _check(_lib.cbs_batch_status_poll(batch, ctypes.byref(v)))
+    return v.value
+
+
+def cbs_probe_fp64_peak() -> float:
+    """Measured FP64 fma throughput of the current device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(_lib.cbs_probe_fp64_peak(ctypes.byref(v)))
     return v.value
 
 

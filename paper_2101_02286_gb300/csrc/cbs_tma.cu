@@ -1,6 +1,8 @@
 // cbs_tma.cu -- host side of the TMA-fed refinement line kernel
 // (cbs_tma.cuh): eligibility, the tensor-map encoder, the interface tables
 // and the dispatch over rows per partition and interface precision.
+#include <cmath>
+
 #include "cbs_tma_launch.cuh"
 
 namespace cbs {
@@ -64,10 +66,64 @@ bool make_iface(const DevLineTables& D, bool fp64, TmaIface& f) {
       scale *= C;
     }
   }
+  // the scaling commutes with the message stages: fold it into the last one
+  if (f.nmsg > 0) {
+    const int k = f.nmsg - 1;
+    for (int m = 0; m < 3; m++) {
+      f.cd[k][m] *= scale;
+      f.cf[k][m] = (float)((double)f.cf[k][m] * scale);
+    }
+    scale = 1.0;
+  }
   f.scaled = scale;
   f.scalef = (float)scale;
   f.wait_ns = 1000000000ull;  // 1 s
   f.fault = 0;
+  return true;
+}
+
+bool tma_integer_bands(const LineArgs& a, const DevLineTables& t, LineArgs& a2, DevLineTables& t2, TmaIface& f) {
+  f.ib = 0;
+  f.dband = 1.f;
+  f.invdf = 1.f;
+  f.invdd = 1.0;
+  const double alpha = t.band[0];
+  // a stencil is needed to form D b exactly (the weights take D)
+  if (a.K < 1 || !(alpha > 0.0) || t.band[1] != 1.0 || t.band[2] != alpha) return false;
+  const double D = std::nearbyint(1.0 / alpha);
+  if (D < 2.0 || D > 6.0 || std::fabs(alpha * D - 1.0) > std::ldexp(1.0, -48)) return false;
+  a2 = a;
+  for (int q = 0; q < kMaxRhsTerms; q++) {  // stencil weights of D b
+    const double w = a.w[q] * D;
+    a2.w[q] = w;
+    a2.wHi[q] = (float)w;
+    a2.wLo[q] = (float)(w - (double)a2.wHi[q]);
+  }
+  pack_weights(a2);
+  t2 = t;
+  for (int j = 0; j < kMaxBulk; j++) {  // bulk pivot reciprocals of A' = D A: y' = y / D
+    t2.fac[j * 3 + 1] = t.fac[j * 3 + 1] / D;
+    t2.facF[j * 3 + 1] = (float)t2.fac[j * 3 + 1];
+  }
+  // b-hat' = b~' - D L~ y'_{i-1} - D U~ y'_i = D b-hat: the interface then
+  // returns D x~, undone by the final scaling (or the last message stage)
+  t2.Lt[0][0] = t.Lt[0][0] * D;
+  t2.Ut[0][0] = t.Ut[0][0] * D;
+  t2.LtF[0][0] = (float)t2.Lt[0][0];
+  t2.UtF[0][0] = (float)t2.Ut[0][0];
+  if (f.nmsg > 0) {
+    for (int m = 0; m < 3; m++) {
+      f.cd[f.nmsg - 1][m] /= D;
+      f.cf[f.nmsg - 1][m] = (float)f.cd[f.nmsg - 1][m];
+    }
+  } else {
+    f.scaled /= D;
+    f.scalef = (float)f.scaled;
+  }
+  f.ib = 1;
+  f.dband = (float)D;
+  f.invdd = 1.0 / D;
+  f.invdf = (float)f.invdd;
   return true;
 }
 

@@ -139,7 +139,8 @@ constexpr int kTmaMaxMsg = 6;    // interface stages with messages (p = 32: at m
 // precision, each x~ <- C x~ - KM x~_{i-s} - KP x~_{i+s}, in order; every
 // other stage is a uniform scaling x~ <- C x~, and since all lanes scale
 // alike these commute with the message stages and are applied at the end as
-// one product.
+// one product (folded into the last message stage's blocks when there is
+// one).
 struct TmaIface {
   int nmsg;
   int s[kTmaMaxMsg];
@@ -152,6 +153,16 @@ struct TmaIface {
   // for that tile expires (cbs_plan_inject_fault)
   unsigned long long wait_ns;
   int fault;
+  // Integer bands: alpha = 1/D with D in 2..6.  The launch then solves
+  // A' = D A = (1, D, 1) with right-hand side D b (host-side: stencil
+  // weights times D; bulk pivot reciprocals divided by D; the b-hat blocks
+  // L~, U~ times D and the interface's final scaling divided by D, so the
+  // interface rows need no division), and the residual D b - A' x0q is
+  // formed with D x0q + (x0q_{k-1} + x0q_{k+1}) exact in one FMA on a 21-bit
+  // grid.
+  int ib;
+  float dband, invdf;
+  double invdd;
 };
 
 // ---------------------------------------------------------------- shared memory
@@ -226,11 +237,17 @@ __device__ __forceinline__ void tma_solve(float (&v)[M], const int i, const DevL
     if (j + 1 < NB) s -= t.facF[j * 3 + 2] * v[2 + j];
     v[1 + j] = s;
   }
-  // a3: b-hat_i = b~_i - L~_i y_{i-1}[last] - U~_i y_i[first] (Eq. 21)
+  // a3: b-hat_i = b~_i - L~_i y_{i-1}[last] - U~_i y_i[first] (Eq. 21); an
+  // FP64 interface widens its inputs with integer operations (the FP64
+  // pipe, which also runs conversions, is the bound of that mode)
   const float yp = __shfl_sync(kFull, v[M - 1], (i + 31) & 31);
-  TI xt = (TI)v[0];
-  xt -= ITab<TI>::Lt(t, 0, 0) * (TI)yp;
-  xt -= ITab<TI>::Ut(t, 0, 0) * (TI)v[1];
+  auto widen = [](float x) -> TI {
+    if constexpr (sizeof(TI) == 8) return f32_to_f64(x);
+    else return x;
+  };
+  TI xt = widen(v[0]);
+  xt -= ITab<TI>::Lt(t, 0, 0) * widen(yp);
+  xt -= ITab<TI>::Ut(t, 0, 0) * widen(v[1]);
   // a3: interface system (message stages, then the product of the others)
 #pragma unroll
   for (int st = 0; st < kTmaMaxMsg; st++) {
@@ -248,11 +265,21 @@ __device__ __forceinline__ void tma_solve(float (&v)[M], const int i, const DevL
       }
     }
   }
-  if constexpr (sizeof(TI) == 8) xt *= f.scaled;
-  else xt *= f.scalef;
+  if (f.nmsg == 0) {  // otherwise folded into the last message stage
+    if constexpr (sizeof(TI) == 8) xt *= f.scaled;
+    else xt *= f.scalef;
+  }
   // a4: x_i = y_i - S_i x~_i - R_i x~_{i+1} (Eq. 22)
   const TI xn = __shfl_sync(kFull, xt, (i + 1) & 31);
-  const float xa = (float)xt, xb = (float)xn;
+  float xa, xb;
+  if constexpr (sizeof(TI) == 8) {  // narrowed with integer operations (hi + lo of the FP32 split)
+    const f2 sa = split_f64(xt), sb = split_f64(xn);
+    xa = __fadd_rn(sa.hi, sa.lo);
+    xb = __fadd_rn(sb.hi, sb.lo);
+  } else {
+    xa = xt;
+    xb = xn;
+  }
 #pragma unroll
   for (int j = 0; j < NB; j++) {
     float s = v[1 + j];
@@ -418,8 +445,9 @@ __device__ __forceinline__ void tma_line(const LineArgs& a, const DevLineTables&
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
   const unsigned mb = __float_as_uint(m) & 0x7f800000u;  // biased exponent e_b << 23
   const unsigned eb = mb >> 23;
-  if (eb > 252u) flag = CBS_ERR_RANGE;  // |x0| >= 2^126 or non-finite
-  const float C = __uint_as_float((mb + (2u << 23)) | 0x00400000u);
+  if (eb > 251u) flag = CBS_ERR_RANGE;  // |x0| >= 2^125 or non-finite
+  // grid: 22 bits below 2^(E+1) (integer bands: 21 bits, room for D x + sum)
+  const float C = __uint_as_float((mb + ((f.ib ? 3u : 2u) << 23)) | 0x00400000u);
   float xq[M];
   {
     const f32x2 C2 = pk(C, C);
@@ -444,17 +472,40 @@ __device__ __forceinline__ void tma_line(const LineArgs& a, const DevLineTables&
       const f32x2 lo = fma2(NAL, sg, add2(add2(se, NE), bl));
       unpk(add2(rh, lo), v[k], v[k + H]);
     };
-    if constexpr (STRIDED) {
+    // integer bands: r' = (b'_hi - (D x0q + sum)) + b'_lo, the bracket exact
+    const f32x2 DB = pk(f.dband, f.dband);
+    auto pair_ib = [&](int k, f32x2 bh, f32x2 bl) {
+      const f32x2 sg = add2(pk(xr(k - 1), xr(k + H - 1)), pk(xr(k + 1), xr(k + H + 1)));  // exact
+      const f32x2 tq = fma2(DB, pk(xq[k], xq[k + H]), sg);                                 // exact
+      unpk(add2(sub2(bh, tq), bl), v[k], v[k + H]);
+    };
+    if (f.ib) {
+      if constexpr (STRIDED) {
 #pragma unroll
-      for (int k = 0; k < H; k++) pair(k, lds_b64(ys + k * RS), lds_b64(ys + (k + H) * RS));
+        for (int k = 0; k < H; k++) pair_ib(k, lds_b64(ys + k * RS), lds_b64(ys + (k + H) * RS));
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; k += 2) {
+          f32x2 bh0, bh1, bl0, bl1;
+          lds_v2b64(ux(k / 2), bh0, bh1);
+          lds_v2b64(ux((k + H) / 2), bl0, bl1);
+          pair_ib(k, bh0, bl0);
+          pair_ib(k + 1, bh1, bl1);
+        }
+      }
     } else {
+      if constexpr (STRIDED) {
 #pragma unroll
-      for (int k = 0; k < H; k += 2) {
-        f32x2 bh0, bh1, bl0, bl1;
-        lds_v2b64(ux(k / 2), bh0, bh1);
-        lds_v2b64(ux((k + H) / 2), bl0, bl1);
-        pair(k, bh0, bl0);
-        pair(k + 1, bh1, bl1);
+        for (int k = 0; k < H; k++) pair(k, lds_b64(ys + k * RS), lds_b64(ys + (k + H) * RS));
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; k += 2) {
+          f32x2 bh0, bh1, bl0, bl1;
+          lds_v2b64(ux(k / 2), bh0, bh1);
+          lds_v2b64(ux((k + H) / 2), bl0, bl1);
+          pair(k, bh0, bl0);
+          pair(k + 1, bh1, bl1);
+        }
       }
     }
   }

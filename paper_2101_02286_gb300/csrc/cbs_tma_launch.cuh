@@ -46,11 +46,19 @@ bool tile_map(CUtensorMap* map, const void* ptr, const LineArgs& a) {
 
 constexpr int kTmaMaxDevices = 64;
 
+// Integer bands (alpha = 1/D, D in 2..6, to 2^-48): the launch arguments of
+// the scaled system A' = D A (stencil weights times D, bulk pivot
+// reciprocals divided by D); false otherwise.
+bool tma_integer_bands(const LineArgs& a, const DevLineTables& t, LineArgs& a2, DevLineTables& t2, TmaIface& f);
+
 template <int M, int KS, typename TIR, bool STRIDED, int TL, int W, int NBUF>
-cudaError_t launch_tma_t(const LineArgs& a, const DevLineTables& t, int fault, cudaStream_t s) {
+cudaError_t launch_tma_t(const LineArgs& a0, const DevLineTables& t0, int fault, cudaStream_t s) {
   alignas(64) CUtensorMap tin, tout;
   TmaIface f;
-  if (!make_iface(t, sizeof(TIR) == 8, f)) return cudaErrorNotSupported;
+  if (!make_iface(t0, sizeof(TIR) == 8, f)) return cudaErrorNotSupported;
+  LineArgs a = a0;
+  DevLineTables t = t0;
+  tma_integer_bands(a0, t0, a, t, f);
   if (fault == 1) {  // test of the timeout path: a 1 ms limit on the wait that CTA 0 cannot satisfy
     f.fault = 1;
     f.wait_ns = 1000000ull;

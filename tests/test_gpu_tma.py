@@ -22,9 +22,16 @@ pytestmark = pytest.mark.gpu
 TRI = W.LELE6_TRI
 
 
-def solve(f, direction, precision="fp32_refine", rhs=True, variant=0, expect_tma=True, out_offset=0, tile_lines=0):
+# alpha = 1/3 takes the integer-band residual (A' = 3 A); alpha = 0.3 the
+# general one (same sixth-order stencil coefficients: the oracle solves any
+# alpha, the kernels do not depend on the scheme being consistent)
+LHS = {"int": TRI["lhs"], "gen": (0.3,)}
+
+
+def solve(f, direction, precision="fp32_refine", rhs=True, variant=0, expect_tma=True, out_offset=0, tile_lines=0,
+          lhs="int"):
     n = f.shape[2 - direction]
-    plan = Plan(f.shape, direction, lhs=TRI["lhs"], rhs=TRI["rhs"] if rhs else None, h=W.grid_spacing(n),
+    plan = Plan(f.shape, direction, lhs=LHS[lhs], rhs=TRI["rhs"] if rhs else None, h=W.grid_spacing(n),
                 precision=precision, segments=32)
     info = plan.info()
     assert info["tma"] == (1 if expect_tma else 0), info
@@ -42,11 +49,11 @@ def solve(f, direction, precision="fp32_refine", rhs=True, variant=0, expect_tma
     return y.cpu().numpy(), st
 
 
-def reference(f, direction, rhs=True):
+def reference(f, direction, rhs=True, lhs="int"):
     n = f.shape[2 - direction]
     if rhs:
-        return oracle.derivative(f, TRI["lhs"], TRI["rhs"], W.grid_spacing(n), axis=2 - direction)
-    return oracle.solve_cyclic(oracle.toeplitz_bands(n, TRI["lhs"]), f, axis=2 - direction)
+        return oracle.derivative(f, LHS[lhs], TRI["rhs"], W.grid_spacing(n), axis=2 - direction)
+    return oracle.solve_cyclic(oracle.toeplitz_bands(n, LHS[lhs]), f, axis=2 - direction)
 
 
 def field(direction, n, other, seed):
@@ -58,14 +65,15 @@ def field(direction, n, other, seed):
     return rng.uniform(-1.0, 1.0, size=shape)
 
 
+@pytest.mark.parametrize("lhs", ["int", "gen"])
 @pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_i64"])
 @pytest.mark.parametrize("n", [512, 256])
 @pytest.mark.parametrize("direction", [0, 1, 2])
-def test_parity_directions(cuda, direction, n, precision):
-    f = field(direction, n, (5, 14), 100 + direction + n)  # 70 lines: 8 full tiles and one of 6
-    got, st = solve(f, direction, precision)
+def test_parity_directions(cuda, direction, n, precision, lhs):
+    f = field(direction, n, (5, 14), 100 + direction + n)  # 70 lines: tiles of 4 / 16 and a ragged last one
+    got, st = solve(f, direction, precision, lhs=lhs)
     assert st == 0
-    assert oracle.rel_err(got, reference(f, direction)) < 1e-12
+    assert oracle.rel_err(got, reference(f, direction, lhs=lhs)) < 1e-12
 
 
 @pytest.mark.parametrize("direction", [0, 1, 2])
@@ -105,6 +113,25 @@ def test_variants_agree(cuda, direction):
     got1, _ = solve(f, direction, variant=1)
     assert oracle.rel_err(got0, ref) < 1e-12
     assert oracle.rel_err(got1, ref) < 1e-12
+
+
+@pytest.mark.parametrize("lhs", ["int", "gen"])
+def test_closed_form_mode(cuda, lhs):
+    # a single Fourier mode along x: the scheme's modified wavenumber (Eq. 1)
+    # k'h = (a sin kh + (b/2) sin 2kh) / (1 + 2 alpha cos kh), here for the
+    # alpha of each residual path
+    n, k = 512, 37
+    h = W.grid_spacing(n)
+    xg = np.arange(n) * h
+    f = np.broadcast_to(np.sin(k * xg), (2, 4, n)).copy()
+    got, st = solve(f, 0, lhs=lhs)
+    assert st == 0
+    a, b = TRI["rhs"]
+    al = LHS[lhs][0]
+    th = k * h
+    kp = (a * np.sin(th) + 0.5 * b * np.sin(2 * th)) / (1 + 2 * al * np.cos(th)) / h
+    exact = np.broadcast_to(kp * np.cos(k * xg), f.shape)
+    assert oracle.rel_err(got, exact) < 1e-12
 
 
 def test_special_values(cuda):
