@@ -63,6 +63,11 @@ def parse():
                          "256^3 variable-alpha forward + adjoint (var) or the ragged batch of 48 grids (batch)")
     ap.add_argument("--segments", default="tune",
                     help="partitions per line: 'tune' (autotuner) or a fixed count")
+    ap.add_argument("--profile-shape", default=None,
+                    help="--profile on a seeded U(-1,1) field of this shape NZ,NY,NX instead of the n^3 cube "
+                         "(smaller captures of the same kernels)")
+    ap.add_argument("--directions", default="0,1,2",
+                    help="--profile: the line directions solved per step (0 = x, 1 = y, 2 = z)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (64^3 Fourier, long lines, ragged batch, variable alpha)")
     return ap.parse_args()
@@ -538,17 +543,22 @@ def main():
         profile_other(args, dev, stream, rank)
         return
     n = args.size
-    f_host, modes = W.noisy_cube(n)  # seeded: U(-1,1) + one plane wave
+    if args.profile and args.profile_shape:
+        shape = tuple(int(v) for v in args.profile_shape.split(","))
+        f_host = np.random.default_rng(W.SEEDS["cube512"]).uniform(-1.0, 1.0, size=shape)
+    else:
+        f_host, modes = W.noisy_cube(n)  # seeded: U(-1,1) + one plane wave
     f_pin = torch.from_numpy(f_host).pin_memory()
     f = f_pin.to(dev)
     h = W.grid_spacing(n)
     sch = W.LELE6_TRI
+    dirs = [int(v) for v in args.directions.split(",")] if args.profile else [0, 1, 2]
 
     def make(prec):
         # partition count per direction picked by the library's autotuner
         seg = "tune" if args.segments == "tune" else int(args.segments)
-        return [Plan(f.shape, d, lhs=sch["lhs"], rhs=sch["rhs"], h=h, precision=prec, sweeps=1, segments=seg)
-                for d in range(3)]
+        return {d: Plan(f.shape, d, lhs=sch["lhs"], rhs=sch["rhs"], h=W.grid_spacing(f.shape[2 - d]), precision=prec,
+                        sweeps=1, segments=seg) for d in dirs}
 
     plans = {"fp32_refine": make("fp32_refine")} if not args.profile else {args.precision: make(args.precision)}
     if args.profile:
@@ -557,8 +567,8 @@ def main():
         outs = [torch.empty_like(f) for _ in range(3)]
 
     def step(ps):
-        for d in range(3):
-            ps[d].solve(f, outs[d], stream)
+        for k, d in enumerate(dirs):
+            ps[d].solve(f, outs[k], stream)
 
     if args.profile:
         # headline solves only: W warm-up steps, then K steps (x, y, z each)
@@ -566,9 +576,9 @@ def main():
             step(plans[args.precision])
         torch.cuda.synchronize(dev)
         if rank == 0:
-            print(json.dumps({"profile": True, "size": n, "steps": args.steps, "warmup": args.warmup,
-                              "precision": args.precision,
-                              "segments": [p.info()["segments"] for p in plans[args.precision]]}))
+            print(json.dumps({"profile": True, "shape": list(f.shape), "directions": dirs, "steps": args.steps,
+                              "warmup": args.warmup, "precision": args.precision,
+                              "segments": [plans[args.precision][d].info()["segments"] for d in dirs]}))
         return
     plans["fp64"] = make("fp64")
     plans["fp32_refine_i64"] = make("fp32_refine_i64")
@@ -693,7 +703,7 @@ def main():
         # autotuner picked for the direction)
         kdir = max(range(3), key=lambda d: dir_ref[d])
         achieved = bytes_per_launch / (dir_ref[kdir] * 1e-3) / 1e9
-        info_ref = [p.info() for p in plans["fp32_refine"]]
+        info_ref = [plans["fp32_refine"][d].info() for d in range(3)]
         traffic = traffic_record("refine_tma_%s" % "xyz"[kdir], n)
         per_dir = {"xyz"[d]: {"ms_per_launch": dir_ref[d], "achieved": bytes_per_launch / (dir_ref[d] * 1e-3) / 1e9,
                               "frac": bytes_per_launch / (dir_ref[d] * 1e-3) / 1e9 / hbm,
@@ -719,7 +729,7 @@ def main():
             "data": "synthetic (seeded U(-1,1) + one plane wave, numpy PCG64 seed 1)",
             "config": dict(CONFIG, grid=[n, n, n], parallelism="replicas" if world > 1 else "single GPU",
                            precision="fp32_refine", sweeps=1,
-                           segments=[p.info()["segments"] for p in plans["fp32_refine"]]),
+                           segments=[plans["fp32_refine"][d].info()["segments"] for d in range(3)]),
             "max_rel_err": err.get("fp32_refine"),
             "ms_per_direction": dir_ref,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -736,7 +746,7 @@ def main():
                                               "solve in FP64"},
             "fp64_path": {"value": job_throughput(units, world, ms_64), "unit": "Gunknowns/s",
                           "ms_per_step": ms_64, "ms_per_direction": dir_64, "max_rel_err": err.get("fp64"),
-                          "segments": [p.info()["segments"] for p in plans["fp64"]],
+                          "segments": [plans["fp64"][d].info()["segments"] for d in range(3)],
                           "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak_tflops,
                                        "unit": "TFLOP/s (FP64)", "frac": fp64_ach / fp64_peak_tflops,
                                        "peak_source": "measured: cbs_probe_fp64_peak (register-resident "
@@ -755,7 +765,7 @@ def main():
         }
         print(json.dumps(rec))
     for ps in plans.values():
-        for p in ps:
+        for p in ps.values():
             p.close()
     if world > 1:
         dist.destroy_process_group()
