@@ -176,6 +176,27 @@ def test_schur_complement_identity(r, n, p):
     assert Ahat.shape == (p * r, p * r)
 
 
+def test_partition_convention_fig3():
+    # the interface-row convention of the reduced system, against cases worked
+    # by hand from Fig. 3 / Eq. 7-8 (interface rows first in each partition)
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "partition_fig3.txt")
+    cases = 0
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        head, starts, sizes, iface, bulk = (part.split() for part in line.split("|"))
+        n, p, r = (int(v) for v in head)
+        got_starts, got_sizes = oracle.partition_bounds(n, p)
+        assert got_starts == [int(v) for v in starts] and got_sizes == [int(v) for v in sizes]
+        bands = _random_bands(np.random.default_rng(n + p), n, r)
+        Ahat, gi, gb = oracle.reduced_system_dense(bands, p)
+        assert gi == [int(v) for v in iface] and gb == [int(v) for v in bulk]
+        assert Ahat.shape == (p * r, p * r)
+        cases += 1
+    assert cases == 4
+
+
 # ---------------------------------------------------------------- adjoint
 def test_transpose_bands_is_dense_transpose():
     rng = np.random.default_rng(3)
