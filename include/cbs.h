@@ -2,7 +2,8 @@
  * cbs.h -- C-ABI of the GB300 cyclic compact banded solver.
  *
  * The library solves many independent cyclic (periodic) compact banded linear
- * systems A x = b, tridiagonal (bandwidth w = 3) or pentadiagonal (w = 5), one
+ * systems A x = b, tridiagonal (bandwidth w = 3), pentadiagonal (w = 5) or
+ * heptadiagonal (w = 7, the generalised bands of Sec. 2, Eq. 3-6), one
  * per grid line of a 3-D field, with the two-level partition method of Song et
  * al., "Scalable Parallel Linear Solver for Compact Banded Systems on
  * Heterogeneous Architectures" (arXiv 2101.02286):
@@ -109,10 +110,12 @@ typedef struct cbs_desc {
     int64_t dims[3];        /* nx, ny, nz (>= 1); x contiguous                     */
     int32_t direction;      /* 0 = x, 1 = y, 2 = z: the solve axis; n = dims[dir]  */
     /* matrix */
-    int32_t bandwidth;      /* 3 or 5                                              */
+    int32_t bandwidth;      /* 3, 5 or 7 (7: Toeplitz, on-chip lines of <= 32
+                               partitions, no batches)                             */
     int32_t cyclic;         /* 1 = periodic; 0 = acyclic (corner blocks zero)      */
     int32_t lhs_kind;       /* CBS_LHS_*                                            */
-    double  alpha, beta;    /* Toeplitz bands (beta ignored for bandwidth 3)       */
+    double  alpha, beta, gamma; /* Toeplitz bands a_{+-1}, a_{+-2}, a_{+-3} (diagonal
+                               1; beta ignored below bandwidth 5, gamma below 7) */
     const void* bands;      /* CBS_LHS_VARIABLE: device array of alpha_i, same dims
                                and dtype as the input; read at every solve (the
                                caller keeps it alive and may change its values)    */

@@ -48,6 +48,7 @@ class cbs_desc(ctypes.Structure):
         ("lhs_kind", ctypes.c_int32),
         ("alpha", ctypes.c_double),
         ("beta", ctypes.c_double),
+        ("gamma", ctypes.c_double),
         ("bands", ctypes.c_void_p),
         ("rhs_kind", ctypes.c_int32),
         ("rhs_terms", ctypes.c_int32),

@@ -108,6 +108,19 @@ int mode_of(int precision) {
                                         : kModeRefineI64;
 }
 
+// Symmetric Toeplitz bands of half width r with unit diagonal: a_{+-1} =
+// alpha, a_{+-2} = d->beta, a_{+-3} = d->gamma.
+Bands desc_bands(const cbs_desc* d, int r, double alpha) {
+  Bands A;
+  A.r = r;
+  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
+  A.v[r] = 1.0;
+  A.v[r - 1] = A.v[r + 1] = alpha;
+  if (r >= 2) A.v[r - 2] = A.v[r + 2] = d->beta;
+  if (r >= 3) A.v[r - 3] = A.v[r + 3] = d->gamma;
+  return A;
+}
+
 bool is_staggered(const cbs_desc* d) { return d->rhs_kind == CBS_RHS_STAGGERED || d->rhs_kind == CBS_RHS_MIDPOINT; }
 
 cbs_status validate(const cbs_desc* d) {
@@ -115,7 +128,8 @@ cbs_status validate(const cbs_desc* d) {
   for (int k = 0; k < 3; k++)
     if (d->dims[k] < 1) return fail(CBS_ERR_INVALID_ARG, "dims must be >= 1");
   if (d->direction < 0 || d->direction > 2) return fail(CBS_ERR_INVALID_ARG, "direction must be 0, 1 or 2");
-  if (d->bandwidth != 3 && d->bandwidth != 5) return fail(CBS_ERR_INVALID_ARG, "bandwidth must be 3 or 5");
+  if (d->bandwidth != 3 && d->bandwidth != 5 && d->bandwidth != 7)
+    return fail(CBS_ERR_INVALID_ARG, "bandwidth must be 3, 5 or 7");
   if (d->cyclic != 0 && d->cyclic != 1) return fail(CBS_ERR_INVALID_ARG, "cyclic must be 0 or 1");
   if (d->lhs_kind != CBS_LHS_TOEPLITZ && d->lhs_kind != CBS_LHS_VARIABLE)
     return fail(CBS_ERR_INVALID_ARG, "bad lhs_kind");
@@ -132,6 +146,7 @@ cbs_status validate(const cbs_desc* d) {
       return fail(CBS_ERR_INVALID_ARG, "h must be positive");
     if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the staggered stencils are periodic: needs cyclic = 1");
     if (d->lhs_kind != CBS_LHS_TOEPLITZ) return fail(CBS_ERR_UNSUPPORTED, "staggered stencils: Toeplitz bands only");
+    if (d->bandwidth > 5) return fail(CBS_ERR_UNSUPPORTED, "staggered stencils: bandwidth 3 or 5");
   }
   if (d->precision < CBS_FP64 || d->precision > CBS_FP32_REFINE_I64) return fail(CBS_ERR_INVALID_ARG, "bad precision");
   if (is_refine(d->precision) && (d->refine_sweeps < 1 || d->refine_sweeps > 2))
@@ -140,7 +155,8 @@ cbs_status validate(const cbs_desc* d) {
   if (d->out_dtype != CBS_DTYPE_F64 && d->out_dtype != CBS_DTYPE_F32) return fail(CBS_ERR_INVALID_ARG, "bad out_dtype");
   if (d->precision != CBS_FP32 && d->out_dtype != CBS_DTYPE_F64)
     return fail(CBS_ERR_INVALID_ARG, "FP64 and FP32_REFINE write FP64 output");
-  if (!std::isfinite(d->alpha) || !std::isfinite(d->beta)) return fail(CBS_ERR_INVALID_ARG, "non-finite bands");
+  if (!std::isfinite(d->alpha) || !std::isfinite(d->beta) || !std::isfinite(d->gamma))
+    return fail(CBS_ERR_INVALID_ARG, "non-finite bands");
   if (d->precision == CBS_FP32 && d->in_dtype != d->out_dtype)
     return fail(CBS_ERR_UNSUPPORTED, "FP32 mode: input and output share the element type");
   if (d->precision != CBS_FP32 && d->in_dtype == CBS_DTYPE_F32 && d->rhs_kind != CBS_RHS_NONE)
@@ -347,6 +363,7 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   if (d->rhs_kind != CBS_RHS_NONE || !d->cyclic || d->lhs_kind != CBS_LHS_TOEPLITZ)
     return fail(CBS_ERR_UNSUPPORTED, "long lines: right-hand side given, cyclic Toeplitz bands");
   const int n = P->n, r = P->r;
+  if (r > 2) return fail(CBS_ERR_UNSUPPORTED, "long lines: bandwidth 3 or 5");
   // y/z lines run a tile of adjacent lines per CTA (kLongLines, or half as
   // many above 512 / kLongLines inner partitions): at most 1024 / kLongLines
   // inner partitions (segments of about 2048 rows)
@@ -359,12 +376,7 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
     if ((n - (int64_t)p * r) % 16 != 0)
       while (p < n && n % p) p++;
   }
-  Bands A;
-  A.r = r;
-  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
-  A.v[r] = 1.0;
-  A.v[r - 1] = A.v[r + 1] = d->alpha;
-  if (r == 2) A.v[0] = A.v[4] = d->beta;
+  const Bands A = desc_bands(d, r, d->alpha);
   bool singular = false;
   std::string msg;
   std::vector<double> G;
@@ -492,10 +504,10 @@ cudaError_t launch_line_plan(const cbs_plan* P, const LineArgs& a, int ks, bool 
   }
   const int R = P->r;
 #define CBS_L(MO, RR) launch_line_mode_r<MO, RR>(P->M, ks, stag, tin, tout, a, P->dev, s)
-  if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : CBS_L(0, 2);
-  if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : CBS_L(1, 2);
-  if (mode == kModeRefine) return (R == 1) ? CBS_L(2, 1) : CBS_L(2, 2);
-  return (R == 1) ? CBS_L(3, 1) : CBS_L(3, 2);
+  if (mode == kModeF64) return (R == 1) ? CBS_L(0, 1) : (R == 2) ? CBS_L(0, 2) : CBS_L(0, 3);
+  if (mode == kModeF32) return (R == 1) ? CBS_L(1, 1) : (R == 2) ? CBS_L(1, 2) : CBS_L(1, 3);
+  if (mode == kModeRefine) return (R == 1) ? CBS_L(2, 1) : (R == 2) ? CBS_L(2, 2) : CBS_L(2, 3);
+  return (R == 1) ? CBS_L(3, 1) : (R == 2) ? CBS_L(3, 2) : CBS_L(3, 3);
 #undef CBS_L
 }
 
@@ -526,12 +538,7 @@ cbs_status cbs_interface_model(const cbs_desc* d, int32_t p, double* dhat, doubl
   if (d->lhs_kind != CBS_LHS_TOEPLITZ) return fail(CBS_ERR_UNSUPPORTED, "Toeplitz LHS only");
   const int r = (d->bandwidth - 1) / 2, n = (int)d->dims[d->direction];
   if (p < 1 || n < 2 * r * p) return fail(CBS_ERR_INVALID_ARG, "need 1 <= p and n >= 2 r p");
-  Bands A;
-  A.r = r;
-  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
-  A.v[r] = 1.0;
-  A.v[r - 1] = A.v[r + 1] = d->alpha;
-  if (r == 2) A.v[0] = A.v[4] = d->beta;
+  const Bands A = desc_bands(d, r, d->alpha);
   LineTables T;
   bool singular = false;
   std::string msg = build_line_tables(T, n, A, p, d->cyclic != 0, &singular, /*max_lanes=*/1 << 30);
@@ -636,12 +643,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
     delete P;
     return fail(CBS_ERR_UNSUPPORTED, "more than 32 partitions per line needs the long-line kernel");
   }
-  Bands A;
-  A.r = P->r;
-  for (int k = 0; k < 2 * kMaxR + 1; k++) A.v[k] = 0.0;
-  A.v[P->r] = 1.0;
-  A.v[P->r - 1] = A.v[P->r + 1] = P->var ? 0.25 : d->alpha;  // variable: geometry only
-  if (P->r == 2) A.v[0] = A.v[4] = d->beta;
+  const Bands A = desc_bands(d, P->r, P->var ? 0.25 : d->alpha);  // variable: geometry only
   bool singular = false;
   std::string msg = build_line_tables(P->host, P->n, A, p, d->cyclic != 0, &singular, kMaxLanes);
   if (!msg.empty()) {
@@ -650,7 +652,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   }
   const LineTables& T = P->host;
   const int maxM = (is_refine(d->precision) || P->var) ? 16 : 32;
-  int M = 8;
+  int M = P->r == 3 ? 16 : 8;  // heptadiagonal bands are compiled for 16 and 32 rows per lane
   while (M < T.rows_big) M *= 2;
   if (M > maxM || T.nmax > kMaxBulk) {
     delete P;

@@ -8,7 +8,7 @@
 
 namespace cbs {
 
-constexpr int kMaxR = 2;            // half bandwidth (pentadiagonal)
+constexpr int kMaxR = 3;            // half bandwidth (heptadiagonal)
 constexpr int kMaxLanes = 32;       // partitions per line in the on-chip kernel
 constexpr int kMaxStages = 16;      // >= 2 (popcount(p)-1) + floor(log2 p) + 1 for p <= 32
 constexpr int kMaxRhsTerms = 3;

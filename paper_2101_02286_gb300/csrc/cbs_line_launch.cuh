@@ -137,7 +137,10 @@ cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream
 // in use, a.K <= 2) have their own kernels with two terms.
 template <int R, int M, int MODE, typename TIn, typename TOut>
 cudaError_t launch_ks(int KS, bool staggered, const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
-  if (staggered) return KS == 2 ? launch_variant<R, M, MODE, 2, TIn, TOut, 1>(a, t, s) : cudaErrorNotSupported;
+  if (staggered) {  // staggered stencils: tri- and pentadiagonal bands
+    if constexpr (R <= 2) return KS == 2 ? launch_variant<R, M, MODE, 2, TIn, TOut, 1>(a, t, s) : cudaErrorNotSupported;
+    return cudaErrorNotSupported;
+  }
   switch (KS) {
     case 0: return launch_variant<R, M, MODE, 0, TIn, TOut>(a, t, s);
     case 2: return launch_variant<R, M, MODE, 2, TIn, TOut>(a, t, s);
@@ -173,7 +176,9 @@ template <int MODE, int R>
 inline cudaError_t launch_line_mode_r(int M, int KS, bool stag, int tin, int tout, const LineArgs& a,
                                       const DevLineTables& t, cudaStream_t s) {
   switch (M) {
-    case 8: return launch_line_mrm<MODE, R, 8>(KS, stag, tin, tout, a, t, s);
+    case 8:  // heptadiagonal plans take M >= 16
+      if constexpr (R <= 2) return launch_line_mrm<MODE, R, 8>(KS, stag, tin, tout, a, t, s);
+      break;
     case 16: return launch_line_mrm<MODE, R, 16>(KS, stag, tin, tout, a, t, s);
     case 32:
       if constexpr (!refine_mode(MODE)) return launch_line_mrm<MODE, R, 32>(KS, stag, tin, tout, a, t, s);

@@ -11,6 +11,7 @@
 //     products precomputed), so a solve only updates x~.
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "cbs_internal.h"
 
@@ -62,7 +63,7 @@ std::vector<Stage> build_schedule(int p, bool cyclic) {
 
 namespace {
 
-// r x r row-major blocks, r <= 2.
+// r x r row-major blocks, r <= kMaxR.
 struct Blk {
   int r;
   double a[kMaxR * kMaxR];
@@ -108,20 +109,61 @@ double maxabs(const Blk& x) {
 // Inverse; returns false when non-finite or numerically singular, i.e. when
 // |det| <= 1e-12 * scale^r with `scale` the magnitude of the blocks that were
 // combined into x (so rounding residue of an exactly singular block counts).
+// Closed forms for r = 1, 2; Gauss-Jordan elimination with partial pivoting
+// above (det = the product of the pivots, up to sign).
 bool inv(const Blk& x, Blk& out, double scale = 0.0) {
-  out = Blk(x.r);
+  const int r = x.r;
   scale = std::fmax(scale, maxabs(x));
-  if (x.r == 1) {
+  if (r == 1) {
+    out = Blk(1);
     if (!std::isfinite(x.a[0]) || !(std::fabs(x.a[0]) > 1e-12 * scale)) return false;
     out.a[0] = 1.0 / x.a[0];
     return true;
   }
-  double det = x(0, 0) * x(1, 1) - x(0, 1) * x(1, 0);
-  if (!std::isfinite(det) || !(std::fabs(det) > 1e-12 * scale * scale)) return false;
-  out(0, 0) = x(1, 1) / det;
-  out(1, 1) = x(0, 0) / det;
-  out(0, 1) = -x(0, 1) / det;
-  out(1, 0) = -x(1, 0) / det;
+  if (r == 2) {
+    out = Blk(2);
+    const double det = x(0, 0) * x(1, 1) - x(0, 1) * x(1, 0);
+    if (!std::isfinite(det) || !(std::fabs(det) > 1e-12 * scale * scale)) return false;
+    out(0, 0) = x(1, 1) / det;
+    out(1, 1) = x(0, 0) / det;
+    out(0, 1) = -x(0, 1) / det;
+    out(1, 0) = -x(1, 0) / det;
+    return true;
+  }
+  out = Blk::eye(r);
+  Blk w = x;
+  double det = 1.0;
+  for (int c = 0; c < r; c++) {
+    int piv = c;
+    for (int i = c + 1; i < r; i++)
+      if (std::fabs(w(i, c)) > std::fabs(w(piv, c))) piv = i;
+    if (piv != c)
+      for (int j = 0; j < r; j++) {
+        std::swap(w(c, j), w(piv, j));
+        std::swap(out(c, j), out(piv, j));
+      }
+    const double d = w(c, c);
+    det *= d;
+    if (!std::isfinite(d) || d == 0.0) return false;
+    for (int j = 0; j < r; j++) {
+      w(c, j) /= d;
+      out(c, j) /= d;
+    }
+    for (int i = 0; i < r; i++) {
+      if (i == c) continue;
+      const double f = w(i, c);
+      if (f == 0.0) continue;
+      for (int j = 0; j < r; j++) {
+        w(i, j) -= f * w(c, j);
+        out(i, j) -= f * out(c, j);
+      }
+    }
+  }
+  double tol = 1e-12;
+  for (int k = 0; k < r; k++) tol *= scale;
+  if (!std::isfinite(det) || !(std::fabs(det) > tol)) return false;
+  for (int k = 0; k < r * r; k++)
+    if (!std::isfinite(out.a[k])) return false;
   return true;
 }
 

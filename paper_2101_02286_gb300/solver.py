@@ -23,8 +23,8 @@ def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 
               shift: int = 0) -> abi.cbs_desc:
     """Descriptor for lines along `direction` of a (nz, ny, nx) field.
 
-    lhs: (alpha,) tridiagonal or (alpha, beta) pentadiagonal Toeplitz bands
-    (diagonal 1), or "variable" with bands_ptr pointing at a per-point alpha
+    lhs: (alpha,) tridiagonal, (alpha, beta) pentadiagonal or (alpha, beta,
+    gamma) heptadiagonal Toeplitz bands (diagonal 1), or "variable" with bands_ptr pointing at a per-point alpha
     field.  rhs: None (input is b) or the coefficients (c_1, .., c_K) of the
     periodic stencil named by `stencil`: "central" (Eq. 1, spacing h),
     "staggered" (staggered first derivative, App. A.2) or "midpoint" (compact
@@ -45,6 +45,7 @@ def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 
         d.lhs_kind = abi.CBS_LHS_TOEPLITZ
         d.alpha = float(lhs[0])
         d.beta = float(lhs[1]) if len(lhs) > 1 else 0.0
+        d.gamma = float(lhs[2]) if len(lhs) > 2 else 0.0
     d.cyclic = int(bool(cyclic))
     if rhs is None:
         d.rhs_kind = abi.CBS_RHS_NONE

@@ -11,6 +11,10 @@ Operators (inputs to both sides):
                    a = 14/9, b = 1/9.
   * PENTA10     -- pentadiagonal (beta, alpha) = (1/20, 1/2) with the
                    10th-order right-hand side a = 17/12, b = 101/150, c = 1/100.
+  * HEPTA12     -- heptadiagonal (alpha, beta, gamma) = (9/16, 9/100, 1/400)
+                   with a = 21/16, b = 231/250, c = 147/2000: the
+                   12th-order member of the generalised bands of Sec. 2
+                   (w = 7), every coefficient fixed by Taylor matching.
   * CENTRAL4    -- explicit 4th-order central difference (alpha = 0):
                    a = 4/3, b = -1/3 in Lele's form.
   * STAGGERED6  -- 6th-order staggered first derivative (App. A.2):
@@ -27,6 +31,7 @@ import numpy as np
 
 LELE6_TRI = {"lhs": (1.0 / 3.0,), "rhs": (14.0 / 9.0, 1.0 / 9.0)}
 PENTA10 = {"lhs": (1.0 / 2.0, 1.0 / 20.0), "rhs": (17.0 / 12.0, 101.0 / 150.0, 1.0 / 100.0)}
+HEPTA12 = {"lhs": (9.0 / 16.0, 9.0 / 100.0, 1.0 / 400.0), "rhs": (21.0 / 16.0, 231.0 / 250.0, 147.0 / 2000.0)}
 CENTRAL4 = {"rhs": (4.0 / 3.0, -1.0 / 3.0)}
 STAGGERED6 = {"lhs": (9.0 / 62.0,), "rhs": (63.0 / 62.0, 17.0 / 62.0)}
 MIDPOINT6 = {"lhs": (3.0 / 10.0,), "rhs": (3.0 / 2.0, 1.0 / 10.0)}

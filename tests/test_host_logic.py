@@ -51,10 +51,10 @@ def test_schedule_counts_acyclic(p):
 
 def _cases():
     out = []
-    for lhs in [(1 / 3,), (0.45,), (1 / 2, 1 / 20), (0.3, 0.02)]:
+    for lhs in [(1 / 3,), (0.45,), (1 / 2, 1 / 20), (0.3, 0.02), (9 / 16, 9 / 100, 1 / 400)]:
         r = len(lhs)
         for n, p in [(16, 1), (16, 2), (17, 3), (24, 4), (33, 5), (40, 7), (64, 11), (64, 16), (96, 13),
-                     (128, 32), (130, 31)]:
+                     (128, 32), (130, 31), (192, 32), (200, 31)]:
             if n >= 2 * r * p:
                 out.append((lhs, n, p))
     return out
@@ -107,7 +107,7 @@ def test_invalid_descriptors_rejected():
     with pytest.raises(abi.CbsError) as e:
         abi.cbs_interface_model(d, 5)  # n < 2 r p
     assert e.value.status == abi.CBS_ERR_INVALID_ARG
-    d.bandwidth = 7
+    d.bandwidth = 9
     with pytest.raises(abi.CbsError):
         abi.cbs_interface_model(d, 2)
 

@@ -47,6 +47,9 @@ def test_scheme_coefficients_orders():
     assert _taylor_order([f(1, 3)], [f(14, 9), f(1, 9)]) == 6
     assert _taylor_order([f(1, 2), f(1, 20)], [f(17, 12), f(101, 150), f(1, 100)]) == 10
     assert _taylor_order([], [f(4, 3), f(-1, 3)]) == 4
+    assert _taylor_order([f(9, 16), f(9, 100), f(1, 400)], [f(21, 16), f(231, 250), f(147, 2000)]) == 12
+    assert W.HEPTA12["lhs"] == (9 / 16, 9 / 100, 1 / 400) and W.HEPTA12["rhs"] == (21 / 16, 231 / 250, 147 / 2000)
+    assert _taylor_order([f(9, 16), f(9, 100), f(1, 401)], [f(21, 16), f(231, 250), f(147, 2000)]) < 12
     # the float constants used by the workloads are these rationals
     assert W.LELE6_TRI["lhs"] == (1 / 3,) and W.LELE6_TRI["rhs"] == (14 / 9, 1 / 9)
     assert W.PENTA10["lhs"] == (1 / 2, 1 / 20) and W.PENTA10["rhs"] == (17 / 12, 101 / 150, 1 / 100)
@@ -63,7 +66,7 @@ def modified_wavenumber(k, n, lhs, rhs):
     return num / den / (2 * np.pi / n)
 
 
-@pytest.mark.parametrize("scheme", [W.LELE6_TRI, W.PENTA10, {"lhs": (), "rhs": W.CENTRAL4["rhs"]}])
+@pytest.mark.parametrize("scheme", [W.LELE6_TRI, W.PENTA10, W.HEPTA12, {"lhs": (), "rhs": W.CENTRAL4["rhs"]}])
 @pytest.mark.parametrize("axis_dir", [0, 1, 2])
 def test_closed_form_fourier_cube(scheme, axis_dir):
     # config "64^3, sum of 8 seeded modes": exact answer by linearity
@@ -99,8 +102,7 @@ def _random_bands(rng, n, r):
     return b
 
 
-@pytest.mark.parametrize("r", [1, 2])
-@pytest.mark.parametrize("n", [8, 9, 13, 16, 31, 64])
+@pytest.mark.parametrize("r,n", [(r, n) for r in (1, 2, 3) for n in (8, 9, 13, 16, 31, 64) if n >= 4 * r])
 def test_cyclic_solve_vs_dense(r, n):
     rng = np.random.default_rng(100 + 7 * n + r)
     bands = _random_bands(rng, n, r)
@@ -133,7 +135,7 @@ def test_per_line_bands_batch():
         assert oracle.rel_err(x[l], np.linalg.solve(oracle.dense_matrix(bands[l]), d[l])) < 1e-12
 
 
-@pytest.mark.parametrize("lhs", [(1 / 3,), (1 / 2, 1 / 20), (0.45,)])
+@pytest.mark.parametrize("lhs", [(1 / 3,), (1 / 2, 1 / 20), (0.45,), (9 / 16, 9 / 100, 1 / 400)])
 @pytest.mark.parametrize("n", [512, 1000, 4096])
 def test_circulant_fft(lhs, n):
     rng = np.random.default_rng(n)
@@ -161,7 +163,8 @@ def test_special_cases():
 
 
 # ---------------------------------------------------------------- block-LU identity (Sec. 3)
-@pytest.mark.parametrize("r,n,p", [(1, 24, 4), (1, 23, 5), (1, 12, 1), (1, 12, 2), (2, 40, 5), (2, 33, 3)])
+@pytest.mark.parametrize("r,n,p", [(1, 24, 4), (1, 23, 5), (1, 12, 1), (1, 12, 2), (2, 40, 5), (2, 33, 3),
+                                   (3, 48, 4), (3, 43, 5)])
 def test_schur_complement_identity(r, n, p):
     rng = np.random.default_rng(n * 10 + p)
     bands = _random_bands(rng, n, r)
@@ -255,7 +258,7 @@ def test_adjoint_finite_differences():
 
 
 # ---------------------------------------------------------------- acyclic systems
-@pytest.mark.parametrize("lhs", [(1 / 3,), (0.5, 0.05)])
+@pytest.mark.parametrize("lhs", [(1 / 3,), (0.5, 0.05), (9 / 16, 9 / 100, 1 / 400)])
 @pytest.mark.parametrize("n", [9, 16, 41])
 def test_acyclic_solve_matches_dense_lapack(lhs, n):
     # Sec. 3 acyclic case: no wrapped corners; brute force by LAPACK
@@ -269,7 +272,7 @@ def test_acyclic_solve_matches_dense_lapack(lhs, n):
 
 def test_acyclic_matrix_is_cyclic_without_corners():
     n = 12
-    for lhs in [(1 / 3,), (0.5, 0.05)]:
+    for lhs in [(1 / 3,), (0.5, 0.05), (9 / 16, 9 / 100, 1 / 400)]:
         B = oracle.toeplitz_bands(n, lhs)
         diff = oracle.dense_matrix(B) - oracle.acyclic_dense_matrix(B)
         r = len(lhs)
