@@ -135,6 +135,20 @@ typedef struct cbs_desc {
                                (nodes -> half points); ignored otherwise.  The
                                staggered kinds need cyclic = 1, a Toeplitz LHS and
                                on-chip lines (no batches)                          */
+    /* One-sided boundary closures of an acyclic derivative (cyclic = 0 with
+     * CBS_RHS_CENTRAL; 0 rows = none).  The first closure_rows rows of every
+     * line carry their own equations, read from the host array `closure` by
+     * cbs_plan_create (not kept): row k < closure_rows is
+     *     sum_j L[k][j] x_j = sum_j R[k][j] f_j / h,   j < closure_width,
+     * stored as closure[k*2W + j] = L[k][j], closure[k*2W + W + j] = R[k][j]
+     * (W = closure_width).  The last closure_rows rows are the mirror image:
+     * row n-1-k has L[k][j] on x_{n-1-j} and -R[k][j] / h on f_{n-1-j} (a
+     * first derivative changes sign under reflection).  Rows in between use
+     * the Toeplitz bands and the central stencil, which must stay inside the
+     * line: closure_rows >= max(r, rhs_terms).  On-chip lines only.        */
+    int32_t closure_rows;   /* 0..4                                                */
+    int32_t closure_width;  /* 1..16                                               */
+    const double* closure;  /* host array, 2 * closure_width doubles per row      */
 } cbs_desc;
 
 typedef struct cbs_plan cbs_plan;
@@ -163,6 +177,12 @@ typedef struct cbs_plan_info {
      * start on 16-byte boundaries and the variant is 0), and the lines per
      * tile of that kernel for y/z lines (0: the default). */
     int32_t variant, tma, tile_lines;
+    /* Long-line plans (kernel 1) of x-lines whose segments hold 32 (or 31)
+     * inner partitions of 16 rows and whose outer interface system is
+     * decoupled to FP64 rounding: 1 when a solve runs one warp per segment
+     * (one launch per segment size, variant 0), 0 for the end-row /
+     * interface / segment launches. */
+    int32_t segment_warp;
 } cbs_plan_info;
 
 /* Create a plan: validates the descriptor, chooses p when segments == 0,
@@ -211,6 +231,9 @@ cbs_status cbs_autotune(const cbs_desc* desc, int32_t reps, int32_t* best_segmen
  *       arrays on 16-byte boundaries, even nx for y/z lines -- otherwise the
  *       pipelined / staged line kernels;
  *   1 = always the pipelined / staged line kernels.
+ * For long-line plans (kernel 1): 0 runs a warp per segment where the plan
+ * qualifies (cbs_plan_info.segment_warp), 1 always the end-row / interface /
+ * segment launches.
  * Both give results within the refinement's tolerance of the FP64 solution
  * (they round differently).  tile_lines: the tile shape of the TMA kernel,
  * adjacent lines per tile (for y/z lines also the contiguous bytes per row of

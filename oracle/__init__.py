@@ -23,6 +23,12 @@ What the oracle computes is the plain definition of the method's result:
                        / ``midpoint_interpolation`` solve with them.
 * ``solve_acyclic``    x = B^{-1} d for the non-periodic banded B (Sec. 3,
                        acyclic case): banded LU without pivoting.
+* ``closure_matrices`` / ``derivative_closure``  the acyclic first derivative
+                       with one-sided boundary rows: the dense matrices A_c,
+                       B_c written out row by row (interior rows: Eq. 1; the
+                       first and last rows: the given closure rows and their
+                       mirror image), x = A_c^{-1} B_c f by a dense solve.  The
+                       paper prints no closure; the rows are inputs.
 * ``dense_matrix`` / ``acyclic_dense_matrix`` / ``dense_solve``  brute force
                        for tiny n (partial pivoting).
 * ``adjoint_variable_tri``  gradients of L = <g, x> for x = A(alpha)^{-1} S f:
@@ -306,6 +312,43 @@ def derivative(f, lhs, coefs, h, axis=-1):
     """Compact first derivative along `axis`: x = A^{-1} S f (Eq. 1)."""
     n = np.shape(f)[axis]
     return solve_cyclic(toeplitz_bands(n, lhs), central_rhs(f, coefs, h, axis), axis)
+
+
+def closure_matrices(n, lhs, coefs, closure, h):
+    """Dense (A_c, B_c) of the acyclic compact first derivative A_c x = B_c f.
+
+    Interior rows c <= i < n - c follow Eq. 1: A_c[i, i] = 1, A_c[i, i +- q] =
+    lhs[q-1], B_c[i, i +- q] = +- coefs[q-1] / (2 q h).  closure = (L, R), c x W
+    arrays: row k < c reads sum_j L[k][j] x_j = sum_j R[k][j] f_j / h, and row
+    n-1-k is its mirror image, sum_j L[k][j] x_{n-1-j} = -sum_j R[k][j]
+    f_{n-1-j} / h (the derivative of f(-x) is -f'(-x))."""
+    L, R = (np.asarray(a, dtype=np.float64) for a in closure)
+    c, W = L.shape
+    A = np.zeros((n, n))
+    B = np.zeros((n, n))
+    for i in range(c, n - c):
+        A[i, i] = 1.0
+        for q, a in enumerate(lhs, start=1):
+            A[i, i - q] = A[i, i + q] = a
+        for q, cq in enumerate(coefs, start=1):
+            B[i, i + q] += cq / (2 * q * h)
+            B[i, i - q] -= cq / (2 * q * h)
+    for k in range(c):
+        for j in range(W):
+            A[k, j] = L[k, j]
+            B[k, j] = R[k, j] / h
+            A[n - 1 - k, n - 1 - j] = L[k, j]
+            B[n - 1 - k, n - 1 - j] = -R[k, j] / h
+    return A, B
+
+
+def derivative_closure(f, lhs, coefs, closure, h, axis=-1):
+    """Acyclic compact first derivative with boundary closures along `axis`:
+    x = A_c^{-1} (B_c f), A_c and B_c from closure_matrices (dense LAPACK solve)."""
+    f2, shape = _lines(f, axis)
+    A, B = closure_matrices(f2.shape[1], lhs, coefs, closure, h)
+    x2 = np.linalg.solve(A, B @ f2.T).T
+    return _unlines(np.ascontiguousarray(x2), shape, axis)
 
 
 def staggered_derivative(f, lhs, coefs, h, shift=0, axis=-1):

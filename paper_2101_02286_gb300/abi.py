@@ -60,6 +60,9 @@ class cbs_desc(ctypes.Structure):
         ("in_dtype", ctypes.c_int32),
         ("out_dtype", ctypes.c_int32),
         ("rhs_shift", ctypes.c_int32),
+        ("closure_rows", ctypes.c_int32),
+        ("closure_width", ctypes.c_int32),
+        ("closure", ctypes.c_void_p),
     ]
 
 
@@ -73,6 +76,7 @@ class cbs_plan_info(ctypes.Structure):
         ("message_stages", ctypes.c_int32), ("message_stages_f32", ctypes.c_int32),
         ("inner_message_stages", ctypes.c_int32), ("inner_message_stages_f32", ctypes.c_int32),
         ("variant", ctypes.c_int32), ("tma", ctypes.c_int32), ("tile_lines", ctypes.c_int32),
+        ("segment_warp", ctypes.c_int32),
     ]
 
 

@@ -137,7 +137,8 @@ cbs_status validate(const cbs_desc* d) {
   if (d->rhs_kind == CBS_RHS_CENTRAL) {
     if (d->rhs_terms < 1 || d->rhs_terms > 3) return fail(CBS_ERR_INVALID_ARG, "rhs_terms must be 1..3");
     if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(CBS_ERR_INVALID_ARG, "h must be positive");
-    if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the central stencil is periodic: needs cyclic = 1");
+    if (!d->cyclic && d->closure_rows == 0)
+      return fail(CBS_ERR_UNSUPPORTED, "an acyclic derivative needs boundary closures (closure_rows)");
   }
   if (is_staggered(d)) {
     if (d->rhs_terms < 1 || d->rhs_terms > 2) return fail(CBS_ERR_INVALID_ARG, "staggered stencils: rhs_terms 1..2");
@@ -147,6 +148,14 @@ cbs_status validate(const cbs_desc* d) {
     if (!d->cyclic) return fail(CBS_ERR_UNSUPPORTED, "the staggered stencils are periodic: needs cyclic = 1");
     if (d->lhs_kind != CBS_LHS_TOEPLITZ) return fail(CBS_ERR_UNSUPPORTED, "staggered stencils: Toeplitz bands only");
     if (d->bandwidth > 5) return fail(CBS_ERR_UNSUPPORTED, "staggered stencils: bandwidth 3 or 5");
+  }
+  if (d->closure_rows < 0) return fail(CBS_ERR_INVALID_ARG, "closure_rows must be >= 0");
+  if (d->closure_rows > 0) {
+    if (d->cyclic || d->rhs_kind != CBS_RHS_CENTRAL || d->lhs_kind != CBS_LHS_TOEPLITZ)
+      return fail(CBS_ERR_UNSUPPORTED, "boundary closures: acyclic lines, central stencil, Toeplitz bands");
+    if (!d->closure) return fail(CBS_ERR_INVALID_ARG, "boundary closures need the host array");
+    if (d->closure_rows > cbs::kMaxClosureRows || d->closure_width < 1 || d->closure_width > cbs::kMaxClosureWidth)
+      return fail(CBS_ERR_INVALID_ARG, "closure_rows 1..4, closure_width 1..16");
   }
   if (d->precision < CBS_FP64 || d->precision > CBS_FP32_REFINE_I64) return fail(CBS_ERR_INVALID_ARG, "bad precision");
   if (is_refine(d->precision) && (d->refine_sweeps < 1 || d->refine_sweeps > 2))
@@ -350,6 +359,49 @@ static int truncated_inverse_rows(const LineTables& T, int N, int r, std::vector
   return K;
 }
 
+// Segment count of the warp-per-segment layout for x-lines of n rows: the
+// smallest p with n - p r a multiple of 16 whose segments get 32 x 16 + r or
+// 31 x 16 + r rows; 0 when there is none (n below two such segments).
+int warp_layout_segments(int n, int r) {
+  for (int64_t p = std::max<int64_t>(2, (n + 16 * 32 + r - 1) / (16 * 32 + r)); p <= n / (16 * 31 + r); p++) {
+    if ((n - p * r) % 16 != 0) continue;
+    const int64_t T16 = (n - p * r) / 16, K16 = (T16 + p - 1) / p;
+    if (K16 == 32) return (int)p;
+    if (K16 < 32) break;
+  }
+  return 0;
+}
+
+// The outer interface system of a long-line plan decoupled to FP64 rounding:
+// every coupling block below 2^-60 of the diagonal blocks, which agree to
+// 2^-50.  Then x~_i = D-hat^{-1} b-hat_i; Dinv gets D-hat^{-1} (r x r).
+bool outer_decoupled(const LineTables& T, int r, double* Dinv) {
+  const int p = T.p, rr = r * r;
+  if ((int)T.Dhat.size() < p * rr || (int)T.Lhat.size() < p * rr || (int)T.Uhat.size() < p * rr) return false;
+  double dmax = 0.0, cmax = 0.0, ddiff = 0.0;
+  for (int e = 0; e < rr; e++) dmax = std::fmax(dmax, std::fabs(T.Dhat[e]));
+  for (int i = 0; i < p; i++)
+    for (int e = 0; e < rr; e++) {
+      ddiff = std::fmax(ddiff, std::fabs(T.Dhat[(size_t)i * rr + e] - T.Dhat[e]));
+      cmax = std::fmax(cmax, std::fmax(std::fabs(T.Lhat[(size_t)i * rr + e]), std::fabs(T.Uhat[(size_t)i * rr + e])));
+    }
+  if (!(dmax > 0.0) || !(cmax <= std::ldexp(dmax, -60)) || !(ddiff <= std::ldexp(dmax, -50))) return false;
+  const double* D = T.Dhat.data();
+  if (r == 1) {
+    if (!(std::fabs(D[0]) > 0.0)) return false;
+    Dinv[0] = 1.0 / D[0];
+    return std::isfinite(Dinv[0]);
+  }
+  if (r != 2) return false;
+  const double det = D[0] * D[3] - D[1] * D[2];
+  if (!(std::fabs(det) > 1e-12 * dmax * dmax)) return false;
+  Dinv[0] = D[3] / det;
+  Dinv[1] = -D[1] / det;
+  Dinv[2] = -D[2] / det;
+  Dinv[3] = D[0] / det;
+  return std::isfinite(Dinv[0]) && std::isfinite(Dinv[1]) && std::isfinite(Dinv[2]) && std::isfinite(Dinv[3]);
+}
+
 // Long lines: p segments per line, one CTA per segment (cbs_long.cu).
 //
 // Segment layout.  When n - p r is a multiple of 16, the segments get
@@ -364,12 +416,14 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
     return fail(CBS_ERR_UNSUPPORTED, "long lines: right-hand side given, cyclic Toeplitz bands");
   const int n = P->n, r = P->r;
   if (r > 2) return fail(CBS_ERR_UNSUPPORTED, "long lines: bandwidth 3 or 5");
+  if (d->closure_rows > 0) return fail(CBS_ERR_UNSUPPORTED, "long lines: no boundary closures");
   // y/z lines run a tile of adjacent lines per CTA (kLongLines, or half as
   // many above 512 / kLongLines inner partitions): at most 1024 / kLongLines
   // inner partitions (segments of about 2048 rows)
   const bool tiled = d->direction != 0;
   const int max_inner = tiled ? 1024 / kLongLines : 512;
   int p = d->segments;
+  if (!p && !tiled) p = warp_layout_segments(n, r);  // x-lines: a warp per segment where it applies
   if (!p) {  // segments of about 512 rows (y/z: tiles of 8 lines x 32 inner partitions), 1024 (x, n <= 2^16),
              // 4096 (longer x-lines)
     p = tiled ? (n + 511) / 512 : n <= 65536 ? (n + 1023) / 1024 : (n + 4095) / 4096;
@@ -444,6 +498,13 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
         return fail(CBS_ERR_UNSUPPORTED, "long lines: segments too short for this band (choose p dividing n)");
     }
   }
+  // x-lines whose segments have 32 (31) whole 16-row inner partitions and
+  // whose outer system is decoupled: a warp per segment (cbs_long_warp.cu)
+  double Dinv[kMaxR * kMaxR] = {};
+  P->long_warp = !tiled && full && m == 16 * 32 + r && (sizes[0] == p || sizes[2] == 16 * 31 + r) && p >= 2 &&
+                 K <= 16 * 31 && outer_decoupled(P->host, r, Dinv);
+  if (!P->long_warp && 2 * (size_t)p * r * sizeof(double) > 227 * 1024)
+    return fail(CBS_ERR_UNSUPPORTED, "long lines: more than 14528 interface unknowns per line (raise the segment size)");
   cbs_status st = fill_dev_tables(P->dev, P->host, A, d, 0, &P->dbuf, false);
   if (st) return st;
   const int threads = ((pin + 31) / 32) * 32;
@@ -457,13 +518,21 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   P->inner_full = full;
   // scratch: yb, cc (2r per segment), xt (r per segment), then G
   const size_t nseg = (size_t)P->nlines * p;
-  const size_t bytes = (nseg * (5 * r) + G.size()) * sizeof(double);
+  // G as float pairs for the warp-per-segment path (double-float dot products)
+  std::vector<float> Gf(2 * G.size());
+  for (size_t k = 0; k < G.size(); k++) {
+    Gf[k] = (float)G[k];
+    Gf[G.size() + k] = (float)(G[k] - (double)Gf[k]);
+  }
+  const size_t bytes = (nseg * (5 * r) + G.size()) * sizeof(double) + Gf.size() * sizeof(float);
   cudaError_t e = cudaMalloc(&P->sbuf, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&P->dstatus, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->dstatus, 0, sizeof(int));
   double* sb = (double*)P->sbuf;
   if (e == cudaSuccess)
     e = cudaMemcpy(sb + nseg * 5 * r, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
+  float* gf = reinterpret_cast<float*>(sb + nseg * 5 * r + G.size());
+  if (e == cudaSuccess) e = cudaMemcpy(gf, Gf.data(), Gf.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "long-line scratch");
   LongArgs& a = P->largs;
   std::memset(&a, 0, sizeof(a));
@@ -489,6 +558,19 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   P->kind = 1;
   P->M = 16;
   P->inner_threads = threads;
+  if (P->long_warp) {
+    LongWarpArgs& w = P->lwargs;
+    std::memset(&w, 0, sizeof(w));
+    for (int q = 0; q < r; q++)
+      for (int e = 0; e < r; e++) {
+        w.Dinv[q * r + e] = Dinv[q * r + e];
+        w.Lt[q * r + e] = P->host.Lt[q][e];
+        w.Ut[q * r + e] = P->host.Ut[q][e];
+      }
+    w.status = P->dstatus;
+    w.Gh = gf;
+    w.Gl = gf + G.size();
+  }
   return CBS_OK;
 }
 
@@ -570,6 +652,52 @@ cbs_status cbs_interface_model(const cbs_desc* d, int32_t p, double* dhat, doubl
     }
     std::memcpy(xt, x.data(), (size_t)p * r * sizeof(double));
   }
+  return CBS_OK;
+}
+
+// Closure tables of plan P (cbs_closure.cuh), uploaded to one device buffer.
+static cbs_status setup_closure(cbs_plan* P, const cbs_desc* d) {
+  ClosureTables C;
+  bool singular = false;
+  const LineArgs& a = P->args;
+  const std::string msg = closure_build(C, P->n, P->r, P->dev.band, a.K, a.w, d->closure_rows, d->closure_width,
+                                        d->closure, d->h, &singular);
+  if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_INVALID_ARG, msg);
+  const size_t ints = C.wrow.size() + C.urow.size();
+  const size_t ioff = (ints * sizeof(int) + 15) / 16 * 16;
+  const size_t dbl = C.Df.size() + C.Ey.size() + C.Minv.size() + C.Zt.size();
+  std::vector<unsigned char> host(ioff + dbl * sizeof(double));
+  int* ip = reinterpret_cast<int*>(host.data());
+  std::copy(C.wrow.begin(), C.wrow.end(), ip);
+  std::copy(C.urow.begin(), C.urow.end(), ip + C.wrow.size());
+  double* dp = reinterpret_cast<double*>(host.data() + ioff);
+  size_t o = 0;
+  for (const std::vector<double>* v : {&C.Df, &C.Ey, &C.Minv, &C.Zt}) {
+    std::copy(v->begin(), v->end(), dp + o);
+    o += v->size();
+  }
+  cudaError_t e = cudaMalloc(&P->cbuf, host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(P->cbuf, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "closure tables");
+  ClosureArgs& c = P->cargs;
+  std::memset(&c, 0, sizeof(c));
+  c.lines = P->nlines;
+  c.nx = d->dims[0];
+  c.ny = d->dims[1];
+  c.dir = d->direction;
+  c.n = P->n;
+  c.c2 = C.c2;
+  c.nw = (int)C.wrow.size();
+  c.nu = (int)C.urow.size();
+  const int* di = static_cast<const int*>(P->cbuf);
+  c.wrow = di;
+  c.urow = di + C.wrow.size();
+  const double* dd = reinterpret_cast<const double*>(static_cast<const unsigned char*>(P->cbuf) + ioff);
+  c.Df = dd;
+  c.Ey = dd + C.Df.size();
+  c.Minv = dd + C.Df.size() + C.Ey.size();
+  c.Zt = dd + C.Df.size() + C.Ey.size() + C.Minv.size();
+  P->closure = true;
   return CBS_OK;
 }
 
@@ -718,6 +846,14 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
     }
     v.status = P->dstatus;
   }
+  if (d->closure_rows > 0) {
+    st = setup_closure(P, d);
+    if (st) {
+      cbs_plan_destroy(P);
+      return st;
+    }
+  }
+  P->desc.closure = nullptr;  // the caller's host array is not kept
   *out = P;
   return CBS_OK;
 }
@@ -738,6 +874,7 @@ cbs_status cbs_plan_destroy(cbs_plan* P) {
   if (P->lbuf_small) cudaFree(P->lbuf_small);
   if (P->sbuf) cudaFree(P->sbuf);
   if (P->dstatus) cudaFree(P->dstatus);
+  if (P->cbuf) cudaFree(P->cbuf);
   delete P;
   return CBS_OK;
 }
@@ -757,6 +894,7 @@ cbs_status cbs_plan_info_get(const cbs_plan* P, cbs_plan_info* info) {
   info->stage_count = (int32_t)P->host.stages.size();
   info->kernel = P->kind;
   info->threads_per_line = P->kind == 1 ? P->inner_threads : P->dev.pw;
+  info->segment_warp = P->kind == 1 && P->long_warp && P->variant == 0;
   info->lines = P->nlines;
   auto count = [](const LineTables& T, int bit) {
     int c = 0;
@@ -822,10 +960,14 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     la.in = in;
     la.out = out;
     int launches = 0;
-    cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->lgeom,
-                                P->dev,
-                                P->dev_inner, la.cbig < la.p ? &P->dev_inner_small : nullptr,
-                                P->inner_full, (cudaStream_t)stream, &launches);
+    cudaError_t e =
+        P->long_warp && P->variant == 0
+            ? launch_long_warp(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->dev_inner,
+                               la.cbig < la.p ? &P->dev_inner_small : nullptr, P->lwargs, (cudaStream_t)stream,
+                               &launches)
+            : launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->lgeom, P->dev,
+                          P->dev_inner, la.cbig < la.p ? &P->dev_inner_small : nullptr, P->inner_full,
+                          (cudaStream_t)stream, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "long-line kernel launch");
     g_launches = launches;
     return CBS_OK;
@@ -838,6 +980,15 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
   if (e == cudaErrorNotSupported) return fail(CBS_ERR_UNSUPPORTED, "no kernel variant for these element types");
   if (e != cudaSuccess) return cuda_fail(e, "line kernel launch");
   g_launches = 1;
+  if (P->closure) {  // boundary rows: the Woodbury correction on the rows near both ends
+    ClosureArgs c = P->cargs;
+    c.f = in;
+    c.x = out;
+    const cudaError_t ec =
+        launch_closure(c, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, (cudaStream_t)stream);
+    if (ec != cudaSuccess) return cuda_fail(ec, "closure kernel launch");
+    g_launches = 2;
+  }
   return CBS_OK;
 }
 
@@ -941,10 +1092,10 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   for (int k = 0; k < count; k++) {
     const cbs_desc& d = descs[k];
     if (d.lhs_kind != CBS_LHS_TOEPLITZ || d.in_dtype != CBS_DTYPE_F64 || d.out_dtype != CBS_DTYPE_F64 ||
-        (d.precision != CBS_FP64 && d.precision != CBS_FP32_REFINE) || is_staggered(&d)) {
+        (d.precision != CBS_FP64 && d.precision != CBS_FP32_REFINE) || is_staggered(&d) || d.closure_rows) {
       cbs_batch_destroy(B);
       return fail(CBS_ERR_UNSUPPORTED,
-                  "batch problems: Toeplitz, FP64 in/out, FP64 or FP32_REFINE, no staggered stencil");
+                  "batch problems: Toeplitz, FP64 in/out, FP64 or FP32_REFINE, no staggered stencil or closures");
     }
     cbs_plan* P = nullptr;
     cbs_status st = cbs_plan_create(&P, &d);

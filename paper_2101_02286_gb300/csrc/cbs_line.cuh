@@ -1332,12 +1332,12 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
 #pragma unroll
     for (int k = 0; k < M; k++) w[KS + k] = (ok && (FULL || k < size)) ? SL[k * t.sp + i] : TT(0);
 #pragma unroll
-    for (int q = 0; q < KS; q++) {
+    for (int q = 0; q < KS; q++) {  // acyclic lines (boundary closures): the end values extended
       int rlo = start - KS + q;
-      rlo += (rlo < 0) ? n : 0;
+      rlo = rlo >= 0 ? rlo : t.cyclic ? rlo + n : 0;
       w[q] = ok ? SL[slot_of(t, rlo)] : TT(0);
       int rhi = start + size + q;
-      rhi -= (rhi >= n) ? n : 0;
+      rhi = rhi < n ? rhi : t.cyclic ? rhi - n : n - 1;
       hh[q] = ok ? SL[slot_of(t, rhi)] : TT(0);
     }
   }
@@ -1550,14 +1550,14 @@ __device__ __forceinline__ void line_tile(const LineArgs& a, const DevLineTables
         fl[KS + k] = sv.lo;
       }
 #pragma unroll
-      for (int q = 0; q < KS; q++) {
+      for (int q = 0; q < KS; q++) {  // acyclic lines (boundary closures): the end values extended
         int rlo = start - KS + q;
-        rlo += (rlo < 0) ? n : 0;
+        rlo = rlo >= 0 ? rlo : t.cyclic ? rlo + n : 0;
         const f2 a0 = split_in(ok ? SL[slot_of(t, rlo)] : TT(0));
         fh[q] = a0.hi;
         fl[q] = a0.lo;
         int rhi = start + size + q;
-        rhi -= (rhi >= n) ? n : 0;
+        rhi = rhi < n ? rhi : t.cyclic ? rhi - n : n - 1;
         const f2 a1 = split_in(ok ? SL[slot_of(t, rhi)] : TT(0));
         hhh[q] = a1.hi;
         hhl[q] = a1.lo;

@@ -114,7 +114,9 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 template <int R, int M, int MODE, int KSV, typename TIn, typename TOut, int ST = 0>
 cudaError_t launch_variant(const LineArgs& a, const DevLineTables& t, cudaStream_t s) {
   if constexpr (sizeof(TIn) == 8 && sizeof(TOut) == 8) {
-    if (tile_full(t, M) && (a.dir != 0 || (aligned16(a.in) && aligned16(a.out)))) {
+    // acyclic lines with a stencil (boundary closures) extend the end values
+    // in the stencil halo, which only the staged layout does
+    if (tile_full(t, M) && (a.dir != 0 || (aligned16(a.in) && aligned16(a.out))) && (KSV == 0 || t.cyclic)) {
       // the refinement kernel holds 2 CTAs per SM (registers), too few to
       // hide HBM latency without the pipelined prefetch; the FP64 / FP32
       // kernels keep 3 CTAs per SM and load directly

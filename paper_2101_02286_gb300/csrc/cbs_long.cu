@@ -35,12 +35,6 @@ namespace cbs {
 
 
 
-// First row and row count of segment s (the first cbig segments have m rows,
-// the rest msmall).
-__device__ __forceinline__ int64_t seg_start(const LongArgs& a, int s) {
-  return s < a.cbig ? (int64_t)s * a.m : (int64_t)a.cbig * a.m + (int64_t)(s - a.cbig) * a.msmall;
-}
-__device__ __forceinline__ int seg_rows(const LongArgs& a, int s) { return s < a.cbig ? a.m : a.msmall; }
 
 // Element offset of row 0 of a line (row k at + k * es); line < 2^31.
 __device__ __forceinline__ int64_t long_base(const LongArgs& a, const LongGeom& gm, int64_t line) {
@@ -612,6 +606,24 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
   if (in == out) return set_error(CBS_ERR_INVALID_ARG, "out must not alias in");
   if (P->kind != 1) return set_error(CBS_ERR_UNSUPPORTED, "cbs_solve_noalloc runs long-line plans (segments per CTA)");
   const LongArgs& pa = P->largs;
+  const cbs_desc& d = P->desc;
+  const int mode = d.precision == CBS_FP64 ? kModeF64
+                   : d.precision == CBS_FP32 ? kModeF32
+                   : d.precision == CBS_FP32_REFINE ? kModeRefine
+                                                    : kModeRefineI64;
+  if (P->long_warp && P->variant == 0) {  // a warp per segment: no per-solve scratch at all
+    LongArgs a = pa;
+    a.in = in;
+    a.out = out;
+    int launches = 0;
+    const cudaError_t e = launch_long_warp(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a,
+                                           P->dev_inner, a.cbig < a.p ? &P->dev_inner_small : nullptr, P->lwargs,
+                                           (cudaStream_t)stream, &launches);
+    if (e != cudaSuccess)
+      return set_error(CBS_ERR_CUDA, std::string("long-line kernel launch: ") + cudaGetErrorString(e));
+    set_launch_count(launches);
+    return CBS_OK;
+  }
   const size_t nseg = (size_t)pa.lines * pa.p;
   const size_t need = nseg * 5 * pa.r;
   if (need > kNoAllocScratchDoubles)
@@ -626,11 +638,6 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
   a.yb = scratch;
   a.cc = scratch + nseg * 2 * a.r;
   a.xt = scratch + nseg * 4 * a.r;
-  const cbs_desc& d = P->desc;
-  const int mode = d.precision == CBS_FP64 ? kModeF64
-                   : d.precision == CBS_FP32 ? kModeF32
-                   : d.precision == CBS_FP32_REFINE ? kModeRefine
-                                                    : kModeRefineI64;
   int launches = 0;
   cudaError_t e = launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a, P->lgeom,
                               P->dev,

@@ -25,6 +25,13 @@ struct LongArgs {
   double band[2 * kMaxR + 1];
 };
 
+// First row and row count of segment s (the first cbig segments have m rows,
+// the rest msmall).
+__host__ __device__ __forceinline__ int64_t seg_start(const LongArgs& a, int s) {
+  return s < a.cbig ? (int64_t)s * a.m : (int64_t)a.cbig * a.m + (int64_t)(s - a.cbig) * a.msmall;
+}
+__host__ __device__ __forceinline__ int seg_rows(const LongArgs& a, int s) { return s < a.cbig ? a.m : a.msmall; }
+
 // Geometry of the lines, passed to the kernels after their other arguments:
 // lines along dir (0 = x, 1 = y, 2 = z) of an (nx, ny, nz) field; es = row
 // stride in elements (1, nx or nx ny).  y-lines are numbered x + nx z and
@@ -32,6 +39,20 @@ struct LongArgs {
 struct LongGeom {
   int64_t nx, ny, es;
   int dir;
+};
+
+// The warp-per-segment path for x-lines (cbs_long_warp.cu): segments of
+// 32 x 16 + r rows (or 31 x 16 + r), whose outer interface system is
+// decoupled to FP64 rounding.  Launch for segments seg0 .. seg0 + nseg - 1
+// (all of one size), kLongWarps consecutive segments of one line per CTA.
+constexpr int kLongWarps = 8;
+struct LongWarpArgs {
+  double Dinv[kMaxR * kMaxR];            // inverse of the outer diagonal block D-hat (r x r)
+  double Lt[kMaxR * kMaxR], Ut[kMaxR * kMaxR];  // b-hat assembly (Eq. 21)
+  const float* Gh;                       // [r][K] leading entries of D^{-1}'s first rows as
+  const float* Gl;                       //   float pairs (G = Gh + Gl)
+  int seg0, nseg, nchunks;               // nchunks = ceil(nseg / kLongWarps)
+  int* status;                           // device status word
 };
 
 }  // namespace cbs

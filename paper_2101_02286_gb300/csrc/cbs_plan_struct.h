@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include "cbs_closure.cuh"
 #include "cbs_internal.h"
 #include "cbs_line.cuh"
 #include "cbs_long.cuh"
@@ -14,6 +15,7 @@ using cbs::LineArgs;
 using cbs::LineTables;
 using cbs::LongArgs;
 using cbs::LongGeom;
+using cbs::LongWarpArgs;
 using cbs::VarArgs;
 
 struct cbs_batch {
@@ -49,6 +51,12 @@ struct cbs_plan {
   void* lbuf_small = nullptr;
   void* sbuf = nullptr;
   int inner_threads = 0;
+  bool long_warp = false;             // x-lines, a warp per segment (decoupled outer system)
+  cbs::LongWarpArgs lwargs;
+  // one-sided boundary closures (acyclic derivatives): the correction launch
+  bool closure = false;
+  cbs::ClosureArgs cargs;
+  void* cbuf = nullptr;
 };
 
 namespace cbs {
@@ -58,6 +66,9 @@ cbs_status set_error(cbs_status s, const std::string& msg);
 void set_launch_count(int n);
 // inner_small: tables of the msmall-row segments (whole-16-row layout), or
 // null when every segment uses `inner`.
+cudaError_t launch_long_warp(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& inner,
+                             const DevLineTables* inner_small, const LongWarpArgs& wa, cudaStream_t s,
+                             int* launches);
 cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const LongGeom& gm,
                         const DevLineTables& outer,
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,

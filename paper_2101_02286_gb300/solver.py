@@ -20,7 +20,7 @@ _STENCIL = {"central": abi.CBS_RHS_CENTRAL, "staggered": abi.CBS_RHS_STAGGERED, 
 def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 1.0, segments: int = 0,
               precision: str = "fp64", sweeps: int = 1, in_dtype=torch.float64, out_dtype=None,
               cyclic: bool = True, bands_ptr: int | None = None, stencil: str = "central",
-              shift: int = 0) -> abi.cbs_desc:
+              shift: int = 0, closure=None) -> abi.cbs_desc:
     """Descriptor for lines along `direction` of a (nz, ny, nx) field.
 
     lhs: (alpha,) tridiagonal, (alpha, beta) pentadiagonal or (alpha, beta,
@@ -29,7 +29,10 @@ def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 
     periodic stencil named by `stencil`: "central" (Eq. 1, spacing h),
     "staggered" (staggered first derivative, App. A.2) or "midpoint" (compact
     interpolation, Eq. 2); the two staggered kinds map half points to nodes
-    (shift 0) or nodes to half points (shift 1).
+    (shift 0) or nodes to half points (shift 1).  closure: (L, R), two
+    equal-shape (rows, width) arrays of one-sided boundary rows for an
+    acyclic derivative (row k: sum_j L[k][j] x_j = sum_j R[k][j] f_j / h; the
+    right end is their mirror image, see cbs.h).
     """
     nz, ny, nx = (int(s) for s in shape_zyx)
     d = abi.cbs_desc()
@@ -64,6 +67,15 @@ def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 
     if out_dtype is None:
         out_dtype = torch.float64 if precision != "fp32" else in_dtype
     d.out_dtype = _DT[out_dtype]
+    if closure is not None:
+        import numpy as np
+        L, R = (np.asarray(a, dtype=np.float64) for a in closure)
+        if L.ndim != 2 or L.shape != R.shape:
+            raise ValueError("closure: two equal-shape (rows, width) arrays")
+        buf = np.ascontiguousarray(np.concatenate([L, R], axis=1))
+        d._closure_buf = buf  # kept alive with the descriptor
+        d.closure_rows, d.closure_width = L.shape
+        d.closure = buf.ctypes.data
     return d
 
 

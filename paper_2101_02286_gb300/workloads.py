@@ -15,6 +15,13 @@ Operators (inputs to both sides):
                    with a = 21/16, b = 231/250, c = 147/2000: the
                    12th-order member of the generalised bands of Sec. 2
                    (w = 7), every coefficient fixed by Taylor matching.
+  * CLOSURE3_4  -- one-sided boundary rows for acyclic derivatives (rows
+                   k = 0, 1: the third-order one-sided row
+                   x_0 + 2 x_1 = (-5/2 f_0 + 2 f_1 + 1/2 f_2) / h and the
+                   fourth-order tridiagonal row (1/4, 1, 1/4) with
+                   3/4 (f_2 - f_0) / h); CLOSURE3_4_6 adds row 2, the
+                   sixth-order tridiagonal scheme, for the pentadiagonal
+                   interior.  (L, R): LHS and RHS coefficients per row.
   * CENTRAL4    -- explicit 4th-order central difference (alpha = 0):
                    a = 4/3, b = -1/3 in Lele's form.
   * STAGGERED6  -- 6th-order staggered first derivative (App. A.2):
@@ -33,6 +40,11 @@ LELE6_TRI = {"lhs": (1.0 / 3.0,), "rhs": (14.0 / 9.0, 1.0 / 9.0)}
 PENTA10 = {"lhs": (1.0 / 2.0, 1.0 / 20.0), "rhs": (17.0 / 12.0, 101.0 / 150.0, 1.0 / 100.0)}
 HEPTA12 = {"lhs": (9.0 / 16.0, 9.0 / 100.0, 1.0 / 400.0), "rhs": (21.0 / 16.0, 231.0 / 250.0, 147.0 / 2000.0)}
 CENTRAL4 = {"rhs": (4.0 / 3.0, -1.0 / 3.0)}
+CLOSURE3_4 = ([[1.0, 2.0, 0.0], [0.25, 1.0, 0.25]],
+              [[-2.5, 2.0, 0.5], [-0.75, 0.0, 0.75]])
+CLOSURE3_4_6 = ([[1.0, 2.0, 0.0, 0.0, 0.0], [0.25, 1.0, 0.25, 0.0, 0.0], [0.0, 1.0 / 3.0, 1.0, 1.0 / 3.0, 0.0]],
+                [[-2.5, 2.0, 0.5, 0.0, 0.0], [-0.75, 0.0, 0.75, 0.0, 0.0],
+                 [-1.0 / 36.0, -7.0 / 9.0, 0.0, 7.0 / 9.0, 1.0 / 36.0]])
 STAGGERED6 = {"lhs": (9.0 / 62.0,), "rhs": (63.0 / 62.0, 17.0 / 62.0)}
 MIDPOINT6 = {"lhs": (3.0 / 10.0,), "rhs": (3.0 / 2.0, 1.0 / 10.0)}
 

@@ -144,6 +144,34 @@ def test_plan_create_validates_before_any_device_work():
     assert e.value.status == abi.CBS_ERR_INVALID_ARG
 
 
+def test_closure_descriptors_validated_before_device_work():
+    from paper_2101_02286_gb300 import workloads as W
+    cl = W.CLOSURE3_4
+    tri = W.LELE6_TRI
+    d = make_desc((2, 2, 64), 0, lhs=tri["lhs"], rhs=tri["rhs"], h=0.1, cyclic=False)
+    with pytest.raises(abi.CbsError) as e:  # an acyclic derivative needs closures
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+    d = make_desc((2, 2, 64), 0, lhs=tri["lhs"], rhs=tri["rhs"], h=0.1, cyclic=True, closure=cl)
+    with pytest.raises(abi.CbsError) as e:  # closures on a periodic line
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+    d = make_desc((2, 2, 64), 0, lhs=tri["lhs"], rhs=tri["rhs"], h=0.1, cyclic=False, closure=cl)
+    d.closure = None
+    with pytest.raises(abi.CbsError) as e:  # rows without their array
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG
+    d = make_desc((2, 2, 64), 0, lhs=tri["lhs"], rhs=tri["rhs"], h=0.1, cyclic=False, closure=cl)
+    d.closure_width = 17
+    with pytest.raises(abi.CbsError) as e:
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG
+    d = make_desc((2, 2, 64), 0, lhs=tri["lhs"], rhs=None, cyclic=False, closure=cl)
+    with pytest.raises(abi.CbsError) as e:  # closures belong to a stencil
+        abi.cbs_plan_create(d)
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+
+
 def test_staggered_descriptors_validated_before_device_work():
     from paper_2101_02286_gb300 import workloads as W
     from paper_2101_02286_gb300.solver import Plan

@@ -402,3 +402,84 @@ def test_staggered_transpose_is_dense_transpose(shift):
         # S^T is the other shift's stencil, negated for the derivative
         S_other = np.stack([fwd(I[j], 1 - shift) for j in range(n)], axis=1)
         assert np.allclose(ST, neg * S_other, atol=1e-14)
+
+
+# ---------------------------------------------------------------- boundary closures (acyclic derivative)
+def _row_order(L, R, kmax=10):
+    """Largest P such that the boundary row sum_j L_j f'(j) = sum_j R_j f(j)
+    (h = 1, nodes j = 0, 1, ...) is exact for every monomial x^k, k <= P."""
+    order = -1
+    for k in range(kmax + 1):
+        lhs = sum(Fr(l) * (k * Fr(j) ** (k - 1) if k >= 1 else 0) for j, l in enumerate(L))
+        rhs = sum(Fr(r) * Fr(j) ** k for j, r in enumerate(R))
+        if lhs != rhs:
+            break
+        order = k
+    return order
+
+
+def test_closure_rows_taylor_order():
+    f = Fr
+    third = ([1, 2, 0], [f(-5, 2), 2, f(1, 2)])
+    fourth = ([f(1, 4), 1, f(1, 4)], [f(-3, 4), 0, f(3, 4)])
+    sixth = ([0, f(1, 3), 1, f(1, 3), 0], [f(-1, 36), f(-7, 9), 0, f(7, 9), f(1, 36)])
+    assert _row_order(*third) == 3
+    assert _row_order(*fourth) == 4
+    assert _row_order(*sixth) == 6
+    assert _row_order([1, 2, 0], [f(-5, 2), 2, f(1, 3)]) < 3  # not vacuous
+    # the float constants of the workloads are these rationals (rounded)
+    def rat(rows):
+        return [[Fr(v).limit_denominator(1000) for v in r] for r in rows]
+    L, R = W.CLOSURE3_4
+    assert rat(L) == [third[0], fourth[0]] and rat(R) == [third[1], fourth[1]]
+    L, R = W.CLOSURE3_4_6
+    assert rat(L) == [third[0] + [0, 0], fourth[0] + [0, 0], sixth[0]]
+    assert rat(R) == [third[1] + [0, 0], fourth[1] + [0, 0], sixth[1]]
+
+
+def _poly_case(n, deg, L=1.3):
+    h = L / (n - 1)
+    x = np.arange(n) * h
+    c = np.random.default_rng(deg + n).uniform(-1, 1, size=deg + 1)
+    f = np.polyval(c, x)
+    fp = np.polyval(np.polyder(c), x) if deg > 0 else np.zeros(n)
+    return f, fp, h
+
+
+@pytest.mark.parametrize("scheme,closure", [(W.LELE6_TRI, W.CLOSURE3_4), (W.PENTA10, W.CLOSURE3_4_6)])
+@pytest.mark.parametrize("n", [24, 41, 64])
+def test_closure_oracle_exact_for_cubics(scheme, closure, n):
+    # the lowest-order row (third order) is exact for cubics, every other row
+    # for higher degrees, so A_c x = B_c f holds with x = f' exactly: the
+    # solve returns the derivative to rounding, on both ends of the line
+    for deg in range(4):
+        f, fp, h = _poly_case(n, deg)
+        x = oracle.derivative_closure(f[None], scheme["lhs"], scheme["rhs"], closure, h)[0]
+        assert np.max(np.abs(x - fp)) < 1e-12 * max(1.0, np.max(np.abs(fp))), deg
+    f, fp, h = _poly_case(n, 4)  # a quartic is not reproduced (the check is not vacuous)
+    x = oracle.derivative_closure(f[None], scheme["lhs"], scheme["rhs"], closure, h)[0]
+    assert np.max(np.abs(x - fp)) > 1e-8
+
+
+def test_closure_mirror_sign_matters():
+    # a plausible mistake planted in the oracle's matrices: the right end's
+    # RHS rows not negated.  The cubic pin then fails at the right boundary.
+    n = 32
+    f, fp, h = _poly_case(n, 2)
+    A, B = oracle.closure_matrices(n, W.LELE6_TRI["lhs"], W.LELE6_TRI["rhs"], W.CLOSURE3_4, h)
+    B[n - 2:] *= -1.0
+    x = np.linalg.solve(A, B @ f)
+    assert np.max(np.abs(x[n - 4:] - fp[n - 4:])) > 1e-2
+
+
+def test_closure_convergence_third_order():
+    # smooth non-periodic f: the error falls like h^3 (the third-order row)
+    errs = []
+    for n in (64, 128, 256):
+        h = 1.0 / (n - 1)
+        x = np.arange(n) * h
+        f = np.sin(3 * x) + np.exp(x)
+        got = oracle.derivative_closure(f[None], W.LELE6_TRI["lhs"], W.LELE6_TRI["rhs"], W.CLOSURE3_4, h)[0]
+        errs.append(np.max(np.abs(got - (3 * np.cos(3 * x) + np.exp(x)))))
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(2.9 < o < 4.0 for o in orders), orders

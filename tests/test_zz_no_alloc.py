@@ -19,20 +19,24 @@ from paper_2101_02286_gb300.solver import Plan
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_solve_twice(cuda):
+@pytest.mark.parametrize("variant", [1, 0])
+def test_noalloc_matches_solve_twice(cuda, variant):
+    # variant 1: the end-row / interface / segment launches on the fixed
+    # scratch; variant 0: a warp per segment (512-row segments), no scratch
     lines, n, p = 4, 8192, 16
     plan = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=p, precision="fp32_refine", sweeps=2,
                 in_dtype=torch.float32)
-    assert plan.info()["kernel"] == 1
+    abi.cbs_plan_set_variant(plan.handle, variant, 0)
+    assert plan.info()["kernel"] == 1 and plan.info()["segment_warp"] == (1 - variant)
     rng = np.random.default_rng(2024)
     for call in range(2):  # two calls in a row on the shared scratch
         d = rng.standard_normal((1, lines, n)).astype(np.float32)
         x = torch.from_numpy(d).cuda()
         ref = plan.solve(x)
-        solve_launches = abi.cbs_last_launch_count()  # 3, or 4 with two segment sizes
+        solve_launches = abi.cbs_last_launch_count()  # 3 or 4 (two segment sizes); 2 for the warp path
         out = torch.full_like(ref, float("nan"))
         abi.cbs_solve_noalloc(plan.handle, x.data_ptr(), out.data_ptr(), 0)
-        assert abi.cbs_last_launch_count() == solve_launches >= 3
+        assert abi.cbs_last_launch_count() == solve_launches >= (3 if variant else 2)
         torch.cuda.synchronize()
         got, want = out.cpu().numpy(), ref.cpu().numpy()
         assert np.isfinite(got).all()
