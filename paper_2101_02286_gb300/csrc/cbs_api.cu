@@ -402,6 +402,98 @@ bool outer_decoupled(const LineTables& T, int r, double* Dinv) {
   return std::isfinite(Dinv[0]) && std::isfinite(Dinv[1]) && std::isfinite(Dinv[2]) && std::isfinite(Dinv[3]);
 }
 
+// Compact stage list (LwIface) of an inner acyclic system T of P <= 32
+// partitions for the interface precision `bit` (1: FP64, 2: FP32): the
+// stages whose couplings exceed rounding keep their messages; the others
+// with C != I are local products, folded into the next message stage (its
+// KM and KP then act on the neighbours' values from before the fold: KM
+// P_{i-s}, KP P_{i+s}) or into one final product.  Blocks of lanes >= P are
+// zero.  False when a message stage is not a PCR step with partners i -+ s.
+bool lw_compact(const LineTables& T, int r, int bit, LwIface& f, std::vector<double>& tab) {
+  f = LwIface{};
+  tab.clear();
+  const int P = T.p, rr = r * r, ns = (int)T.stages.size();
+  if (P > 32 || ns > kMaxStages) return false;
+  auto cf = [&](int st, int m, int i, int e) { return T.coef[((size_t)(st * 3 + m) * rr + e) * P + i]; };
+  auto mul = [&](const double* A, const double* B, double* C) {  // C = A B (r x r)
+    for (int q = 0; q < r; q++)
+      for (int e = 0; e < r; e++) {
+        double v = 0.0;
+        for (int k = 0; k < r; k++) v += A[q * r + k] * B[k * r + e];
+        C[q * r + e] = v;
+      }
+  };
+  std::vector<double> pend((size_t)P * rr, 0.0);  // pending local product per lane
+  auto reset = [&] {
+    std::fill(pend.begin(), pend.end(), 0.0);
+    for (int i = 0; i < P; i++)
+      for (int q = 0; q < r; q++) pend[(size_t)i * rr + q * r + q] = 1.0;
+  };
+  reset();
+  bool has_pend = false;
+  auto push = [&](const std::vector<double>& blk) {  // blk[i * rr + e], lanes < P
+    for (int e = 0; e < rr; e++)
+      for (int i = 0; i < 32; i++) tab.push_back(i < P ? blk[(size_t)i * rr + e] : 0.0);
+  };
+  for (int st = 0; st < ns; st++) {
+    const bool msg = (T.stage_msg[st] & bit) != 0, hc = T.stage_has_c[st] != 0;
+    if (!msg && !hc) continue;
+    std::vector<double> C((size_t)P * rr);
+    for (int i = 0; i < P; i++) {
+      double Ci[kMaxR * kMaxR];
+      for (int e = 0; e < rr; e++) Ci[e] = cf(st, 0, i, e);
+      mul(Ci, &pend[(size_t)i * rr], &C[(size_t)i * rr]);
+    }
+    if (!msg) {
+      pend = C;
+      has_pend = true;
+      continue;
+    }
+    if (T.stages[st].type != kPcr || f.ne == kLwMaxEnt) return false;
+    const int s = T.stages[st].s;
+    std::vector<double> KM((size_t)P * rr, 0.0), KP((size_t)P * rr, 0.0);
+    for (int i = 0; i < P; i++) {
+      const int jm = i - s, jp = i + s;
+      double K[kMaxR * kMaxR];
+      for (int e = 0; e < rr; e++) K[e] = cf(st, 1, i, e);
+      if (jm >= 0) {
+        if (T.src[(size_t)(st * 2 + 0) * P + i] != jm) return false;
+        mul(K, &pend[(size_t)jm * rr], &KM[(size_t)i * rr]);
+      } else {
+        for (int e = 0; e < rr; e++)
+          if (K[e] != 0.0) return false;
+      }
+      for (int e = 0; e < rr; e++) K[e] = cf(st, 2, i, e);
+      if (jp < P) {
+        if (T.src[(size_t)(st * 2 + 1) * P + i] != jp) return false;
+        mul(K, &pend[(size_t)jp * rr], &KP[(size_t)i * rr]);
+      } else {
+        for (int e = 0; e < rr; e++)
+          if (K[e] != 0.0) return false;
+      }
+    }
+    const bool withc = hc || has_pend;
+    f.s[f.ne] = s;
+    f.flags[f.ne] = 1 | (withc ? 2 : 0);
+    f.off[f.ne] = (int)(tab.size() / 32);
+    if (withc) push(C);
+    push(KM);
+    push(KP);
+    f.ne++;
+    reset();
+    has_pend = false;
+  }
+  if (has_pend) {
+    if (f.ne == kLwMaxEnt) return false;
+    f.s[f.ne] = 0;
+    f.flags[f.ne] = 2;
+    f.off[f.ne] = (int)(tab.size() / 32);
+    push(pend);
+    f.ne++;
+  }
+  return true;
+}
+
 // Long lines: p segments per line, one CTA per segment (cbs_long.cu).
 //
 // Segment layout.  When n - p r is a multiple of 16, the segments get
@@ -558,6 +650,38 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   P->kind = 1;
   P->M = 16;
   P->inner_threads = threads;
+  if (P->long_warp) {
+    // compact inner systems in the interface precision of the mode's solves
+    const int mode = mode_of(d->precision);
+    const bool i64 = mode == kModeF64 || mode == kModeRefineI64;
+    std::vector<double> tb[2];
+    const bool two = sizes[0] < p;
+    bool okc = lw_compact(P->inner, r, i64 ? 1 : 2, P->lwifc[0], tb[0]);
+    if (okc && two) okc = lw_compact(P->inner_small, r, i64 ? 1 : 2, P->lwifc[1], tb[1]);
+    if (!okc) {
+      P->long_warp = false;
+      if (2 * (size_t)p * r * sizeof(double) > 227 * 1024)
+        return fail(CBS_ERR_UNSUPPORTED, "long lines: more than 14528 interface unknowns per line (raise the segment size)");
+    } else {
+      const size_t es = i64 ? 8 : 4;
+      const size_t n0 = tb[0].size(), n1 = two ? tb[1].size() : 0;
+      std::vector<unsigned char> hb((n0 + n1) * es);
+      for (size_t k = 0; k < n0 + n1; k++) {
+        const double v = k < n0 ? tb[0][k] : tb[1][k - n0];
+        if (i64) {
+          std::memcpy(hb.data() + k * es, &v, 8);
+        } else {
+          const float fv = (float)v;
+          std::memcpy(hb.data() + k * es, &fv, 4);
+        }
+      }
+      e = cudaMalloc(&P->lwbuf, hb.size());
+      if (e == cudaSuccess) e = cudaMemcpy(P->lwbuf, hb.data(), hb.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "long-line interface tables");
+      P->lwifc[0].tab = P->lwbuf;
+      if (two) P->lwifc[1].tab = static_cast<unsigned char*>(P->lwbuf) + n0 * es;
+    }
+  }
   if (P->long_warp) {
     LongWarpArgs& w = P->lwargs;
     std::memset(&w, 0, sizeof(w));
@@ -751,6 +875,7 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
         if (P->lbuf) cudaFree(P->lbuf);
         if (P->lbuf_small) cudaFree(P->lbuf_small);
         if (P->sbuf) cudaFree(P->sbuf);
+        if (P->lwbuf) cudaFree(P->lwbuf);
         if (P->dstatus) cudaFree(P->dstatus);
         delete P;
         return st;
@@ -875,6 +1000,7 @@ cbs_status cbs_plan_destroy(cbs_plan* P) {
   if (P->sbuf) cudaFree(P->sbuf);
   if (P->dstatus) cudaFree(P->dstatus);
   if (P->cbuf) cudaFree(P->cbuf);
+  if (P->lwbuf) cudaFree(P->lwbuf);
   delete P;
   return CBS_OK;
 }
@@ -963,8 +1089,8 @@ cbs_status cbs_solve(cbs_plan* P, const void* in, void* out, void* stream) {
     cudaError_t e =
         P->long_warp && P->variant == 0
             ? launch_long_warp(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->dev_inner,
-                               la.cbig < la.p ? &P->dev_inner_small : nullptr, P->lwargs, (cudaStream_t)stream,
-                               &launches)
+                               la.cbig < la.p ? &P->dev_inner_small : nullptr, P->lwargs, P->lwifc,
+                               (cudaStream_t)stream, &launches)
             : launch_long(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, la, P->lgeom, P->dev,
                           P->dev_inner, la.cbig < la.p ? &P->dev_inner_small : nullptr, P->inner_full,
                           (cudaStream_t)stream, &launches);

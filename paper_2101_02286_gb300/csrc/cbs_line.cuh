@@ -271,6 +271,14 @@ __device__ __forceinline__ double f32_to_f64_normal(float v) {
   return __hiloint2double((int)hw, (int)lw);
 }
 
+// FP64 value of a float by integer operations: exact for normal values; a
+// zero or subnormal input gives a value of magnitude below 2^-126.
+__device__ __forceinline__ double f32_to_f64_nz(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned hw = (((u >> 3) & 0x0fffffffu) + 0x38000000u) | (u & 0x80000000u);
+  return __hiloint2double((int)hw, (int)(u << 29));
+}
+
 // The double at or toward zero from hi + lo (exact when the pair spans <= 53
 // bits) for |lo| <= ulp(hi) as produced by two_sum; integer arithmetic on the
 // 53-bit significand.  Outside the normal FP32 range the result is hi alone.

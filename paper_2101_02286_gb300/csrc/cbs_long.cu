@@ -618,7 +618,7 @@ extern "C" cbs_status cbs_solve_noalloc(cbs_plan* P, const void* in, void* out, 
     int launches = 0;
     const cudaError_t e = launch_long_warp(mode, P->r, d.in_dtype == CBS_DTYPE_F64, d.out_dtype == CBS_DTYPE_F64, a,
                                            P->dev_inner, a.cbig < a.p ? &P->dev_inner_small : nullptr, P->lwargs,
-                                           (cudaStream_t)stream, &launches);
+                                           P->lwifc, (cudaStream_t)stream, &launches);
     if (e != cudaSuccess)
       return set_error(CBS_ERR_CUDA, std::string("long-line kernel launch: ") + cudaGetErrorString(e));
     set_launch_count(launches);

@@ -46,11 +46,25 @@ struct LongGeom {
 // decoupled to FP64 rounding.  Launch for segments seg0 .. seg0 + nseg - 1
 // (all of one size), kLongWarps consecutive segments of one line per CTA.
 constexpr int kLongWarps = 8;
+// The inner (segment-level) acyclic interface system of one segment size in
+// compact form: the stages that act, in order.  Entry e has flags bit 0 (a
+// message stage: x~ -= KM x~_{i-s} + KP x~_{i+s}, from the values before the
+// stage), bit 1 (x~ <- C x~; consecutive stages without messages are
+// multiplied into one), stride s, and its per-lane blocks at tab + 32 off:
+// [C (bit 1)] [KM, KP (bit 0)], each r x r entries x 32 lanes, lane
+// fastest, in the interface precision.
+constexpr int kLwMaxEnt = 8;
+struct LwIface {
+  const void* tab;
+  int ne;
+  int s[kLwMaxEnt], flags[kLwMaxEnt], off[kLwMaxEnt];
+};
 struct LongWarpArgs {
   double Dinv[kMaxR * kMaxR];            // inverse of the outer diagonal block D-hat (r x r)
   double Lt[kMaxR * kMaxR], Ut[kMaxR * kMaxR];  // b-hat assembly (Eq. 21)
   const float* Gh;                       // [r][K] leading entries of D^{-1}'s first rows as
   const float* Gl;                       //   float pairs (G = Gh + Gl)
+  LwIface ifc;                           // inner system of this launch's segment size
   int seg0, nseg, nchunks;               // nchunks = ceil(nseg / kLongWarps)
   int* status;                           // device status word
 };

@@ -49,6 +49,107 @@ __device__ __forceinline__ void df_madd(float& ah, float& al, float gh, float gl
   al += (s.lo + pe) + (gl * bs.hi + gh * bs.lo);
 }
 
+// a2-a4 for the lane's inner partition of 16 rows (whole-size, acyclic inner
+// system of P <= 32 partitions; lanes >= P hold zeros and zero blocks): on
+// entry v holds the partition's right-hand side, on exit its solution.  Bulk
+// in T, interface in TI through the compact stage list `f`.
+template <typename T, int R, typename TI>
+__device__ __forceinline__ void lw_solve(T (&v)[kWarpM], const int lane, const int P, const DevLineTables& t,
+                                         const LwIface& f) {
+  constexpr int M = kWarpM, NB = M - R, F = 2 * R + 1, rr = R * R;
+  // a2: y = D_i^{-1} b (pre-factorised LU of the bulk block, Eq. 17)
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    T s = v[R + j];
+#pragma unroll
+    for (int q = 1; q <= R; q++)
+      if (j - q >= 0) s -= Tab<T>::fac(t, j * F + q - 1) * v[R + j - q];
+    v[R + j] = s;
+  }
+#pragma unroll
+  for (int j = NB - 1; j >= 0; j--) {
+    T s = Tab<T>::fac(t, j * F + R) * v[R + j];
+#pragma unroll
+    for (int q = 1; q <= R; q++)
+      if (j + q < NB) s -= Tab<T>::fac(t, j * F + R + q) * v[R + j + q];
+    v[R + j] = s;
+  }
+  // a3: b-hat_i = b~_i - L~ y_{i-1}[last r] - U~ y_i[first r]   (Eq. 21)
+  TI xt[R];
+#pragma unroll
+  for (int q = 0; q < R; q++) xt[q] = (TI)v[q];
+#pragma unroll
+  for (int e = 0; e < R; e++) {
+    const T yp = __shfl_sync(kFull, v[M - R + e], lane > 0 ? lane - 1 : 0);
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      if (lane > 0) xt[q] -= ITab<TI>::Lt(t, q, e) * (TI)yp;
+      xt[q] -= ITab<TI>::Ut(t, q, e) * (TI)v[R + e];
+    }
+  }
+  // a3: the acting stages of block PCR (acyclic, Sec. 4), per-lane blocks;
+  // a stage's messages carry the values from before the stage
+  const TI* tab = static_cast<const TI*>(f.tab) + lane;
+#pragma unroll 1
+  for (int en = 0; en < f.ne; en++) {
+    const TI* b = tab + f.off[en] * 32;
+    const int fl = f.flags[en];
+    TI xm[R], xp[R], nx[R];
+    if (fl & 1) {
+      const int s = f.s[en];
+#pragma unroll
+      for (int q = 0; q < R; q++) {  // out-of-range partners carry zero blocks
+        xm[q] = __shfl_sync(kFull, xt[q], lane >= s ? lane - s : lane);
+        xp[q] = __shfl_sync(kFull, xt[q], lane + s < 32 ? lane + s : lane);
+      }
+    }
+    int o = 0;
+    if (fl & 2) {
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        TI acc = TI(0);
+#pragma unroll
+        for (int e = 0; e < R; e++) acc += __ldg(b + (q * R + e) * 32) * xt[e];
+        nx[q] = acc;
+      }
+      o = rr;
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; q++) nx[q] = xt[q];
+    }
+    if (fl & 1) {
+#pragma unroll
+      for (int q = 0; q < R; q++)
+#pragma unroll
+        for (int e = 0; e < R; e++)
+          nx[q] -= __ldg(b + (o + q * R + e) * 32) * xm[e] + __ldg(b + (o + rr + q * R + e) * 32) * xp[e];
+    }
+#pragma unroll
+    for (int q = 0; q < R; q++) xt[q] = nx[q];
+  }
+  // a4: back-substitution x_i = y_i - S x~_i - R x~_{i+1} (Eq. 22); the last
+  // partition has no next interface
+  T xa[R], xb[R];
+#pragma unroll
+  for (int q = 0; q < R; q++) {
+    const TI xn = __shfl_sync(kFull, xt[q], lane + 1 < 32 ? lane + 1 : lane);
+    xa[q] = (T)xt[q];
+    xb[q] = lane + 1 < P ? (T)xn : T(0);
+  }
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    T s = v[R + j];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      s -= Tab<T>::sr(t, true, j * 2 * R + q) * xa[q];
+      s -= Tab<T>::sr(t, true, j * 2 * R + R + q) * xb[q];
+    }
+    v[R + j] = s;
+  }
+#pragma unroll
+  for (int q = 0; q < R; q++) v[q] = xa[q];
+}
+
 }  // namespace
 
 // Shared memory of one CTA for truncation length K and input element size.
@@ -94,14 +195,14 @@ __global__ void __launch_bounds__(kLongWarps * 32, 2)
   // A: every warp stages its segment's bulk rows and b~; warp 0 the last K
   // bulk rows of the segment before the CTA, warp W - 1 the interface rows
   // and first K bulk rows of the segment after it (both cyclic)
+  // lane l moves bulk rows l + 32 t (coalesced): slot (l & 15) * 33 + (l >> 4) + 2 t
+  const int sb = (lane & 15) * kSlot + (lane >> 4);
   if (valid) {
-    TIn* S = slots(w);
-    const TIn* bb = bl + s0 + R;
-#pragma unroll 4
-    for (int t = 0; t < kWarpM; t++) {  // lane l: bulk rows l + 32 t (coalesced)
-      const int j = lane + 32 * t;
-      if (j < N) S[(j & 15) * kSlot + (j >> 4)] = __ldg(bb + j);
-    }
+    TIn* S = slots(w) + sb;
+    const TIn* bb = bl + s0 + R + lane;
+#pragma unroll
+    for (int t = 0; t < kWarpM; t++)
+      if (lane + 32 * t < N) S[2 * t] = __ldg(bb + 32 * t);
     if (lane < R) Bt[w * R + lane] = (double)__ldg(bl + s0 + lane);
   }
   if (w == 0) {
@@ -222,7 +323,7 @@ __global__ void __launch_bounds__(kLongWarps * 32, 2)
       if (k >= kWarpM - R) val -= conv<T>(cL[k - (kWarpM - R)]);
       v[k] = val;
     }
-    solve_partition<T, R, kWarpM, T, true>(v, kWarpM, lane, lane_ok, tin, xch);
+    lw_solve<T, R, T>(v, lane, P, tin, wa.ifc);
     __syncwarp();  // every lane has read its input slots
 #pragma unroll
     for (int k = 0; k < kWarpM; k++) O[k * kSlot + lane] = conv<TOut>(v[k]);
@@ -245,7 +346,7 @@ __global__ void __launch_bounds__(kLongWarps * 32, 2)
       blo[k] = dd.lo + (sv.lo - c.lo);
       v[k] = dd.hi;
     }
-    solve_partition<float, R, kWarpM, TIR, true>(v, kWarpM, lane, lane_ok, tin, xch);
+    lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
 #pragma unroll
     for (int k = 0; k < kWarpM; k++) {
       xh[k] = v[k];
@@ -254,7 +355,7 @@ __global__ void __launch_bounds__(kLongWarps * 32, 2)
     for (int sw = 0; sw < a.sweeps; sw++) {
       if (sw == 0) residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
       else residual_sym2<R, kWarpM, true>(bh, blo, xh, xlo, v, lane, tin, xch);
-      solve_partition<float, R, kWarpM, TIR, true>(v, kWarpM, lane, lane_ok, tin, xch);
+      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
 #pragma unroll
       for (int k = 0; k < kWarpM; k++) {
         const f2 t = two_sum(xh[k], v[k]);
@@ -264,19 +365,17 @@ __global__ void __launch_bounds__(kLongWarps * 32, 2)
     }
     __syncwarp();  // every lane has read its input slots
 #pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
+    for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
       bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
-      O[k * kSlot + lane] = (TOut)(f32_to_f64(xh[k]) + f32_to_f64(xlo[k]));
+      O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(xlo[k]));
     }
   }
   if (__any_sync(kFull, bad && lane_ok) && lane == 0 && wa.status) atomicExch(wa.status, (int)CBS_ERR_RANGE);
   __syncwarp();
-  TOut* xb0 = xl + s0 + R;
-#pragma unroll 4
-  for (int t = 0; t < kWarpM; t++) {  // lane l: bulk rows l + 32 t (coalesced)
-    const int j = lane + 32 * t;
-    if (j < N) xb0[j] = O[(j & 15) * kSlot + (j >> 4)];
-  }
+  TOut* xb0 = xl + s0 + R + lane;
+#pragma unroll
+  for (int t = 0; t < kWarpM; t++)  // lane l: bulk rows l + 32 t (coalesced)
+    if (lane + 32 * t < N) xb0[32 * t] = O[sb + 2 * t];
   if (lane < R) xl[s0 + lane] = (TOut)Xt[w * R + lane];  // the segment's interface rows
 }
 
@@ -319,11 +418,12 @@ cudaError_t launch_long_warp_r(int mode, bool in64, bool out64, const LongArgs& 
 // Both segment sizes: segments [0, cbig) with `inner` (32 inner partitions),
 // [cbig, p) with `inner_small` (31).
 cudaError_t launch_long_warp(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& inner,
-                             const DevLineTables* inner_small, const LongWarpArgs& wa0, cudaStream_t s,
-                             int* launches) {
+                             const DevLineTables* inner_small, const LongWarpArgs& wa0, const LwIface* ifc,
+                             cudaStream_t s, int* launches) {
   *launches = 0;
   for (int part = 0; part < 2; part++) {
     LongWarpArgs wa = wa0;
+    wa.ifc = ifc[part];
     wa.seg0 = part == 0 ? 0 : a.cbig;
     wa.nseg = part == 0 ? a.cbig : a.p - a.cbig;
     if (wa.nseg <= 0) continue;

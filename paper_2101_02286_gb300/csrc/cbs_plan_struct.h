@@ -16,6 +16,7 @@ using cbs::LineTables;
 using cbs::LongArgs;
 using cbs::LongGeom;
 using cbs::LongWarpArgs;
+using cbs::LwIface;
 using cbs::VarArgs;
 
 struct cbs_batch {
@@ -53,6 +54,8 @@ struct cbs_plan {
   int inner_threads = 0;
   bool long_warp = false;             // x-lines, a warp per segment (decoupled outer system)
   cbs::LongWarpArgs lwargs;
+  cbs::LwIface lwifc[2];              // compact inner systems: 32 and 31 partitions
+  void* lwbuf = nullptr;              // their device tables
   // one-sided boundary closures (acyclic derivatives): the correction launch
   bool closure = false;
   cbs::ClosureArgs cargs;
@@ -67,8 +70,8 @@ void set_launch_count(int n);
 // inner_small: tables of the msmall-row segments (whole-16-row layout), or
 // null when every segment uses `inner`.
 cudaError_t launch_long_warp(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& inner,
-                             const DevLineTables* inner_small, const LongWarpArgs& wa, cudaStream_t s,
-                             int* launches);
+                             const DevLineTables* inner_small, const LongWarpArgs& wa, const LwIface* ifc,
+                             cudaStream_t s, int* launches);
 cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& a, const LongGeom& gm,
                         const DevLineTables& outer,
                         const DevLineTables& inner, const DevLineTables* inner_small, bool full, cudaStream_t s,

@@ -214,14 +214,6 @@ __device__ __forceinline__ f2 split_tma(double x, unsigned& bad) {
   return r;
 }
 
-// FP64 value of a float by integer operations: exact for normal values; a
-// zero or subnormal input gives a value of magnitude below 2^-126.
-__device__ __forceinline__ double f32_to_f64_nz(float v) {
-  const unsigned u = __float_as_uint(v);
-  const unsigned hw = (((u >> 3) & 0x0fffffffu) + 0x38000000u) | (u & 0x80000000u);
-  return __hiloint2double((int)hw, (int)(u << 29));
-}
-
 // a2-a4 for one partition of M rows (lane i of a line of 32 partitions,
 // whole-size partitions, tridiagonal Toeplitz bands): on entry v holds b_i,
 // on exit x_i.  FP32 bulk; interface system in TI.
