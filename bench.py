@@ -59,7 +59,7 @@ def parse():
                     help="path run by --profile (the timed headline is always fp32_refine)")
     ap.add_argument("--workload", default="cube", choices=["cube", "long", "var", "batch"],
                     help="what --profile runs: the n^3 field (cube), the 32 x 2^22 pentadiagonal lines "
-                         "(long, FP32 right-hand side, refinement with 2 sweeps, 1024 segments), the "
+                         "(long, FP32 right-hand side, refinement with 1 sweep, default segments), the "
                          "256^3 variable-alpha forward + adjoint (var) or the ragged batch of 48 grids (batch)")
     ap.add_argument("--segments", default="tune",
                     help="partitions per line: 'tune' (autotuner) or a fixed count")
@@ -294,18 +294,25 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     lines, n = d.shape
     di = torch.from_numpy(d.reshape(1, lines, n)).to(dev)
     do = torch.empty((1, lines, n), dtype=torch.float64, device=dev)
-    for prec, sweeps in (("fp32_refine", 2), ("fp64", 1)):
-        pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=1024, precision=prec,
+    # default segments: 8168 of 514 / 498 rows, a warp per segment and 8
+    # segments per CTA (1021 thread blocks per line); p = 1024: the end-row /
+    # interface / segment launches (segments of ~4096 rows, a CTA each)
+    for prec, sweeps, seg in (("fp32_refine", 1, 0), ("fp32_refine", 2, 1024), ("fp64", 1, 0)):
+        pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=seg, precision=prec,
                   sweeps=sweeps, in_dtype=torch.float32)
+        info = pl.info()
         ms = time_ms(lambda: pl.solve(di, do, stream), stream, steps)
         err = None
         if check:
             k = int(rng.integers(0, lines))
             ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d[k:k + 1].astype(np.float64))
             err = oracle.rel_err(do[0, k:k + 1].cpu().numpy(), ref)
+        how = ("%d segments, a warp each, %d per thread block" % (info["segments"], 8) if info["segment_warp"]
+               else "%d segments across CTAs" % info["segments"])
         res.append(_entry("32 x 2^22 cyclic penta (1/20,1/2,1,1/2,1/20), N(0,1) rhs stored FP32, FP64 out, "
-                          "p=1024 segments across CTAs, %s sweeps=%d" % (prec, sweeps),
-                          lines * n, ms, 12, hbm, err, segments=1024, precision=prec, sampled_lines=1))
+                          "%s, %s sweeps=%d" % (how, prec, sweeps),
+                          lines * n, ms, 12, hbm, err, segments=info["segments"], precision=prec, sampled_lines=1,
+                          launches_per_step=abi.cbs_last_launch_count()))
         pl.close()
     del di, do, d
 
@@ -346,13 +353,14 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
 
     # the paper's single-GPU workload: 256^2 lines of 8192 along x, y and z
     # (fields 8192 x 256 x 256, 256 x 8192 x 256, 256 x 256 x 8192), cyclic
-    # tridiagonal alpha = 1/3, right-hand side given; x: p = 8 and 7 (2^n - 1),
+    # tridiagonal alpha = 1/3, right-hand side given; x: the default (16
+    # segments of 513 / 497 rows, a warp each) and p = 7 (2^n - 1),
     # y/z: p = 16 (the default: 512-row segments, tiles of 8 strided lines);
     # the three fields share one buffer of random values
     dpx = np.random.default_rng(20).standard_normal(256 * 256 * 8192)
     di = torch.from_numpy(dpx).to(dev)
     do = torch.empty_like(di)
-    for direction, prec, p in ((0, "fp32_refine", 8), (0, "fp32_refine", 7), (0, "fp64", 8),
+    for direction, prec, p in ((0, "fp32_refine", 0), (0, "fp32_refine", 7), (0, "fp64", 0),
                                (1, "fp32_refine", 16), (1, "fp64", 16), (2, "fp32_refine", 16), (2, "fp64", 16)):
         shape = [(256, 256, 8192), (256, 8192, 256), (8192, 256, 256)][direction]  # (nz, ny, nx)
         pl = Plan(shape, direction, lhs=W.LELE6_TRI["lhs"], rhs=None, precision=prec, segments=p)
@@ -366,9 +374,11 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
             lines = np.stack([src[i, j] for i, j in ii])
             ref = oracle.solve_cyclic(oracle.toeplitz_bands(8192, W.LELE6_TRI["lhs"]), lines)
             err = oracle.rel_err(np.stack([got[i, j] for i, j in ii]), ref)
+        info = pl.info()
+        how = "%d segments per line%s" % (info["segments"], ", a warp each" if info["segment_warp"] else "")
         res.append(_entry("256^2 %s-lines of 8192 (the paper's single-GPU workload), cyclic tridiagonal "
-                          "alpha=1/3, right-hand side given, %d segments per line, %s" % ("xyz"[direction], p, prec),
-                          256 * 256 * 8192, ms, 16, hbm, err, segments=p, sampled_lines=8))
+                          "alpha=1/3, right-hand side given, %s, %s" % ("xyz"[direction], how, prec),
+                          256 * 256 * 8192, ms, 16, hbm, err, segments=info["segments"], sampled_lines=8))
         pl.close()
     del di, do, dpx
 
@@ -485,8 +495,8 @@ def profile_other(args, dev, stream, rank):
         di = torch.from_numpy(d.reshape(1, lines, n)).to(dev)
         do = torch.empty((1, lines, n), dtype=torch.float64, device=dev)
         prec = args.precision
-        pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=1024, precision=prec,
-                  sweeps=2 if prec == "fp32_refine" else 1, in_dtype=torch.float32)
+        pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, precision=prec, sweeps=1,
+                  in_dtype=torch.float32)
         for _ in range(args.warmup + args.steps):
             pl.solve(di, do, stream)
         info = pl.info()

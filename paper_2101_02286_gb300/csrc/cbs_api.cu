@@ -29,7 +29,11 @@ size_t batch_smem(size_t tile_bytes);
 cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitems, const void* const* ins,
                          void* const* outs, int count, int grid, size_t smem, cudaStream_t s);
 size_t batch_problem_bytes();
-void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant);
+void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant, int user);
+void batch_fill_long(void* dst, const LongArgs& la, const DevLineTables& inner, const LongWarpArgs& wa, int R,
+                     int MODE, int user);
+int batch_long_variant_host(int R, int MODE);
+size_t batch_long_bytes(int R, int K);
 constexpr int kBatchMax = 256;
 bool tma_eligible(int mode, int KS, bool staggered, bool in64, bool out64, const LineArgs& a, const DevLineTables& t);
 cudaError_t launch_tma(int mode, int KS, const LineArgs& a, const DevLineTables& t, int tile_lines, int fault,
@@ -1212,7 +1216,8 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   cbs_batch* B = new (std::nothrow) cbs_batch();
   if (!B) return fail(CBS_ERR_NO_MEMORY, "host allocation failed");
   const size_t pb = batch_problem_bytes();
-  std::vector<unsigned char> probs(pb * count);
+  std::vector<unsigned char> probs;  // one entry per on-chip problem, one per segment size of a long line
+  int nent = 0;
   std::vector<int4> items;
   std::vector<double> cost;
   for (int k = 0; k < count; k++) {
@@ -1231,11 +1236,39 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       return fail(st, msg);
     }
     B->plans.push_back(P);
-    if (P->kind != 0) {
-      cbs_batch_destroy(B);
-      return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": lines too long for one warp");
-    }
     const int mode = d.precision == CBS_FP64 ? kModeF64 : kModeRefine;
+    if (P->kind != 0) {
+      // long lines: the x-lines of a warp-per-segment plan, an entry per
+      // segment size, an item per (chunk of kLongWarps segments, line)
+      if (!(P->long_warp && P->variant == 0) || batch_long_variant_host(P->r, mode) < 0) {
+        cbs_batch_destroy(B);
+        return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) +
+                                             ": long lines are batched as x-lines of a warp per segment "
+                                             "(segments of 32 x 16 + r rows, decoupled interface system)");
+      }
+      const LongArgs& la = P->largs;
+      for (int part = 0; part < 2; part++) {
+        LongWarpArgs wa = P->lwargs;
+        wa.ifc = P->lwifc[part];
+        wa.seg0 = part == 0 ? 0 : la.cbig;
+        wa.nseg = part == 0 ? la.cbig : la.p - la.cbig;
+        if (wa.nseg <= 0) continue;
+        wa.nchunks = (wa.nseg + kLongWarps - 1) / kLongWarps;
+        probs.resize(pb * (nent + 1));
+        batch_fill_long(probs.data() + pb * nent, la, part == 0 ? P->dev_inner : P->dev_inner_small, wa, P->r, mode,
+                        k);
+        B->smem = std::max(B->smem, batch_long_bytes(P->r, la.K));
+        const double c = (double)kLongWarps * la.m * (mode == kModeRefine ? 2.0 : 1.0);
+        for (int64_t line = 0; line < la.lines; line++)
+          for (int ch = 0; ch < wa.nchunks; ch++) {
+            items.push_back(make_int4(nent, ch, (int)line, 0));
+            cost.push_back(c);
+          }
+        nent++;
+      }
+      B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
+      continue;
+    }
     const bool full = P->dev.count_big == P->dev.p && P->dev.rows_big == 16 && P->M == 16;
     int variant = full ? batch_variant_host(P->r, P->ks, P->M, mode, true) : -1;
     if (variant < 0) variant = batch_variant_host(P->r, P->ks, P->M, mode, false);
@@ -1243,17 +1276,19 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       cbs_batch_destroy(B);
       return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": tile variant not compiled");
     }
-    batch_fill_problem(probs.data() + pb * k, P->args, P->dev, variant);
+    probs.resize(pb * (nent + 1));
+    batch_fill_problem(probs.data() + pb * nent, P->args, P->dev, variant, k);
     const int TL = kLineThreads / P->dev.pw;
     B->smem = std::max(B->smem, (size_t)TL * P->dev.lsz * sizeof(double));
     const dim3 g = tile_grid(d.dims[0], d.dims[1], d.dims[2], P->nlines, d.direction, TL);
     const double c = (double)TL * P->n * (mode == kModeRefine ? 2.0 : 1.0);
     for (unsigned ty = 0; ty < g.y; ty++)
       for (unsigned tx = 0; tx < g.x; tx++) {
-        items.push_back(make_int4(k, (int)tx, (int)ty, 0));
+        items.push_back(make_int4(nent, (int)tx, (int)ty, 0));
         cost.push_back(c);
       }
     B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
+    nent++;
   }
   // most expensive tiles first, so the static stride ends with small tiles
   std::vector<size_t> order(items.size());

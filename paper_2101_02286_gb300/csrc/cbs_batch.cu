@@ -9,14 +9,23 @@
 // by value in the kernel parameters, so a solve is exactly one launch with
 // no allocation, copy or host synchronisation, and can be captured in a CUDA
 // graph.
+#include <cstring>
+
 #include "cbs_line_launch.cuh"
+#include "cbs_long_warp.cuh"
 
 namespace cbs {
 
+// One entry of the batch: an on-chip problem (line tiles: args, tab) or one
+// segment size of a long-line problem (warp per segment: largs, lwa, tab =
+// the inner tables of that size).  `user` indexes the caller's in/out arrays.
 struct alignas(16) BatchProblem {
   LineArgs args;
   DevLineTables tab;
+  LongArgs largs;
+  LongWarpArgs lwa;
   int variant;
+  int user;
 };
 
 constexpr int kMaxBatch = 256;
@@ -39,16 +48,39 @@ __host__ __device__ constexpr int batch_variant(int R, int KS, int M, int MODE, 
   const int mo = (MODE == kModeF64) ? 0 : (MODE == kModeRefine) ? 1 : -1;
   return (rk < 0 || mi < 0 || mo < 0) ? -1 : (rk * 3 + mi) * 2 + mo;
 }
+// Long-line entries (x-lines, a warp per segment; FP64 in and out): after
+// the tile variants.
+constexpr int kBatchLong = 24;
+__host__ __device__ constexpr int batch_long_variant(int R, int MODE) {
+  return (R < 1 || R > 2 || (MODE != kModeF64 && MODE != kModeRefine)) ? -1
+                                                                       : kBatchLong + (R - 1) * 2 + (MODE == kModeRefine);
+}
 
 #define CBS_BV(R, KS, M, MODE)                                                                   \
   case batch_variant(R, KS, M, MODE):                                                            \
-    line_tile<R, M, MODE, KS, double, double>(P.args, P.tab, bp.in[w.x], bp.out[w.x], w.y, w.z, \
+    line_tile<R, M, MODE, KS, double, double>(P.args, P.tab, bp.in[P.user], bp.out[P.user], w.y, w.z, \
                                               tile_smem);                                        \
     break;
 #define CBS_BVF(R, KS, MODE)                                                                               \
   case batch_variant(R, KS, 16, MODE, true):                                                               \
-    line_tile<R, 16, MODE, KS, double, double, true>(P.args, P.tab, bp.in[w.x], bp.out[w.x], w.y, w.z,   \
+    line_tile<R, 16, MODE, KS, double, double, true>(P.args, P.tab, bp.in[P.user], bp.out[P.user], w.y, w.z, \
                                                      tile_smem);                                           \
+    break;
+
+// Long-line entry: item (entry, chunk, line); the chunk's kLongWarps
+// segments of the line, in the tile's shared memory.  A separate function
+// (not inlined), so that its register allocation stays its own.
+template <int R, int MODE>
+__device__ __noinline__ void batch_long_item(const BatchProblem& P, const void* in, void* out, int chunk, int line,
+                                             unsigned char* smem) {
+  LongArgs la = P.largs;
+  la.in = in;
+  la.out = out;
+  long_warp_item<R, MODE, double, double>(la, P.tab, P.lwa, chunk, (int64_t)line, smem);
+}
+#define CBS_BL(R, MODE)                                                                          \
+  case batch_long_variant(R, MODE):                                                              \
+    batch_long_item<R, MODE>(P, bp.in[P.user], bp.out[P.user], w.y, w.z, tile_smem);             \
     break;
 
 // Shared memory: the current problem's BatchProblem (its tables are read by
@@ -96,6 +128,10 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
       CBS_BVF(1, 0, kModeRefine)
       CBS_BVF(2, 0, kModeF64)
       CBS_BVF(2, 0, kModeRefine)
+      CBS_BL(1, kModeF64)
+      CBS_BL(1, kModeRefine)
+      CBS_BL(2, kModeF64)
+      CBS_BL(2, kModeRefine)
       default:
         break;
     }
@@ -104,6 +140,7 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
 }
 #undef CBS_BV
 #undef CBS_BVF
+#undef CBS_BL
 
 int batch_variant_host(int R, int KS, int M, int MODE, bool full) { return batch_variant(R, KS, M, MODE, full); }
 
@@ -135,11 +172,29 @@ cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitem
 
 size_t batch_problem_bytes() { return sizeof(BatchProblem); }
 
-void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant) {
+void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, int variant, int user) {
   BatchProblem* p = static_cast<BatchProblem*>(dst);
+  std::memset(p, 0, sizeof(*p));
   p->args = a;
   p->tab = t;
   p->variant = variant;
+  p->user = user;
 }
+
+void batch_fill_long(void* dst, const LongArgs& la, const DevLineTables& inner, const LongWarpArgs& wa, int R,
+                     int MODE, int user) {
+  BatchProblem* p = static_cast<BatchProblem*>(dst);
+  std::memset(p, 0, sizeof(*p));
+  p->largs = la;
+  p->tab = inner;
+  p->lwa = wa;
+  p->variant = batch_long_variant(R, MODE);
+  p->user = user;
+}
+
+int batch_long_variant_host(int R, int MODE) { return batch_long_variant(R, MODE); }
+
+// Shared memory of a long-line entry (truncation length K, FP64 input).
+size_t batch_long_bytes(int R, int K) { return R == 1 ? lw_bytes<1>(K, 8) : lw_bytes<2>(K, 8); }
 
 }  // namespace cbs

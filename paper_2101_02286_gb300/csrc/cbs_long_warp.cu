@@ -1,382 +1,15 @@
-// cbs_long_warp.cu -- long x-lines with one warp per segment and one launch
-// per segment size (no separate end-row and interface passes).
-//
-// Segments have r interface rows and a bulk of 32 (or 31) inner partitions
-// of 16 rows, one per lane.  The path applies when the outer interface
-// system is decoupled to FP64 rounding: its coupling blocks L-hat, U-hat are
-// below 2^-60 of the diagonal blocks D-hat (they shrink like the corner
-// entries of D_i^{-1}, i.e. geometrically in the 512 bulk rows), so every
-// PCR stage reduces to a local product and x~_i = D-hat^{-1} b-hat_i.  b-hat_i
-// (Eq. 21) needs the last r rows of y_{i-1} and the first r rows of y_i, each
-// a truncated dot product of K input rows with rows of D^{-1} (the long-line
-// reading of Sec. 4: only those rows cross segments).
-//
-// A CTA takes kLongWarps consecutive segments of one line.  Each warp stages
-// its bulk rows in shared memory (lane i's row k at slot k * 33 + i), forms
-// the end rows of its own y_i from them, and the CTA's first and last warps
-// also those of the neighbouring segments outside the CTA (halo rows read
-// from global memory).  One barrier shares the ends; each warp then forms
-// x~_i and x~_{i+1}, moves their couplings to the right-hand side of its bulk
-// rows (Eq. 9) and runs the inner partition solve (FP32 + refinement with an
-// FP64-accurate residual, or FP64 / FP32) in registers with shuffled
-// messages.  The results leave through the same slots, one row per lane per
-// store instruction.
-#include "cbs_line.cuh"
-#include "cbs_long.cuh"
+// cbs_long_warp.cu -- launch of the warp-per-segment long-line item
+// (cbs_long_warp.cuh): one CTA per chunk of kLongWarps segments of a line.
+#include "cbs_long_warp.cuh"
 
 namespace cbs {
-
-namespace {
-
-constexpr int kWarpM = 16;         // rows per lane
-constexpr int kSlot = 33;          // padded row stride of a warp's slots
-constexpr int kSlotsPerWarp = kWarpM * kSlot;
-
-// Dot products of one CTA: a left and a right end (R rows each) for each of
-// the kLongWarps + 1 segment boundaries, each spread over kTpd<R> threads.
-template <int R> constexpr int kNdot = (kLongWarps + 1) * 2 * R;
-template <int R> constexpr int kTpd = kLongWarps * 32 / kNdot<R>;
-
-// acc += g b in double-float, g = gh + gl and b an input element (exact FP32,
-// or an FP64 value split into two floats).
-template <typename TIn>
-__device__ __forceinline__ void df_madd(float& ah, float& al, float gh, float gl, TIn b) {
-  const f2 bs = split_in(b);
-  const float p = __fmul_rn(gh, bs.hi);
-  const float pe = __fmaf_rn(gh, bs.hi, -p);
-  const f2 s = two_sum(ah, p);
-  ah = s.hi;
-  al += (s.lo + pe) + (gl * bs.hi + gh * bs.lo);
-}
-
-// a2-a4 for the lane's inner partition of 16 rows (whole-size, acyclic inner
-// system of P <= 32 partitions; lanes >= P hold zeros and zero blocks): on
-// entry v holds the partition's right-hand side, on exit its solution.  Bulk
-// in T, interface in TI through the compact stage list `f`.
-template <typename T, int R, typename TI>
-__device__ __forceinline__ void lw_solve(T (&v)[kWarpM], const int lane, const int P, const DevLineTables& t,
-                                         const LwIface& f) {
-  constexpr int M = kWarpM, NB = M - R, F = 2 * R + 1, rr = R * R;
-  // a2: y = D_i^{-1} b (pre-factorised LU of the bulk block, Eq. 17)
-#pragma unroll
-  for (int j = 0; j < NB; j++) {
-    T s = v[R + j];
-#pragma unroll
-    for (int q = 1; q <= R; q++)
-      if (j - q >= 0) s -= Tab<T>::fac(t, j * F + q - 1) * v[R + j - q];
-    v[R + j] = s;
-  }
-#pragma unroll
-  for (int j = NB - 1; j >= 0; j--) {
-    T s = Tab<T>::fac(t, j * F + R) * v[R + j];
-#pragma unroll
-    for (int q = 1; q <= R; q++)
-      if (j + q < NB) s -= Tab<T>::fac(t, j * F + R + q) * v[R + j + q];
-    v[R + j] = s;
-  }
-  // a3: b-hat_i = b~_i - L~ y_{i-1}[last r] - U~ y_i[first r]   (Eq. 21)
-  TI xt[R];
-#pragma unroll
-  for (int q = 0; q < R; q++) xt[q] = (TI)v[q];
-#pragma unroll
-  for (int e = 0; e < R; e++) {
-    const T yp = __shfl_sync(kFull, v[M - R + e], lane > 0 ? lane - 1 : 0);
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-      if (lane > 0) xt[q] -= ITab<TI>::Lt(t, q, e) * (TI)yp;
-      xt[q] -= ITab<TI>::Ut(t, q, e) * (TI)v[R + e];
-    }
-  }
-  // a3: the acting stages of block PCR (acyclic, Sec. 4), per-lane blocks;
-  // a stage's messages carry the values from before the stage
-  const TI* tab = static_cast<const TI*>(f.tab) + lane;
-#pragma unroll 1
-  for (int en = 0; en < f.ne; en++) {
-    const TI* b = tab + f.off[en] * 32;
-    const int fl = f.flags[en];
-    TI xm[R], xp[R], nx[R];
-    if (fl & 1) {
-      const int s = f.s[en];
-#pragma unroll
-      for (int q = 0; q < R; q++) {  // out-of-range partners carry zero blocks
-        xm[q] = __shfl_sync(kFull, xt[q], lane >= s ? lane - s : lane);
-        xp[q] = __shfl_sync(kFull, xt[q], lane + s < 32 ? lane + s : lane);
-      }
-    }
-    int o = 0;
-    if (fl & 2) {
-#pragma unroll
-      for (int q = 0; q < R; q++) {
-        TI acc = TI(0);
-#pragma unroll
-        for (int e = 0; e < R; e++) acc += __ldg(b + (q * R + e) * 32) * xt[e];
-        nx[q] = acc;
-      }
-      o = rr;
-    } else {
-#pragma unroll
-      for (int q = 0; q < R; q++) nx[q] = xt[q];
-    }
-    if (fl & 1) {
-#pragma unroll
-      for (int q = 0; q < R; q++)
-#pragma unroll
-        for (int e = 0; e < R; e++)
-          nx[q] -= __ldg(b + (o + q * R + e) * 32) * xm[e] + __ldg(b + (o + rr + q * R + e) * 32) * xp[e];
-    }
-#pragma unroll
-    for (int q = 0; q < R; q++) xt[q] = nx[q];
-  }
-  // a4: back-substitution x_i = y_i - S x~_i - R x~_{i+1} (Eq. 22); the last
-  // partition has no next interface
-  T xa[R], xb[R];
-#pragma unroll
-  for (int q = 0; q < R; q++) {
-    const TI xn = __shfl_sync(kFull, xt[q], lane + 1 < 32 ? lane + 1 : lane);
-    xa[q] = (T)xt[q];
-    xb[q] = lane + 1 < P ? (T)xn : T(0);
-  }
-#pragma unroll
-  for (int j = 0; j < NB; j++) {
-    T s = v[R + j];
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-      s -= Tab<T>::sr(t, true, j * 2 * R + q) * xa[q];
-      s -= Tab<T>::sr(t, true, j * 2 * R + R + q) * xb[q];
-    }
-    v[R + j] = s;
-  }
-#pragma unroll
-  for (int q = 0; q < R; q++) v[q] = xa[q];
-}
-
-}  // namespace
-
-// Shared memory of one CTA for truncation length K and input element size.
-__host__ __device__ constexpr size_t lw_off_halo() { return (size_t)kLongWarps * kSlotsPerWarp * 8; }
-template <int R>
-__host__ __device__ constexpr size_t lw_bytes(int K, int in_size) {
-  return lw_off_halo() + (size_t)(2 * K * in_size + 15) / 16 * 16 + (size_t)kNdot<R> * kTpd<R> * 8 +
-         (size_t)(kLongWarps + 1) * R * 8 * 4;
-}
 
 template <int R, int MODE, typename TIn, typename TOut>
 __global__ void __launch_bounds__(kLongWarps * 32, 2)
     long_warp_kernel(const LongArgs a, const DevLineTables tin, const LongWarpArgs wa) {
-  constexpr int W = kLongWarps, ND = kNdot<R>, TPD = kTpd<R>;
   extern __shared__ __align__(16) unsigned char smem[];
-  // [W][kSlotsPerWarp] 8-byte slots (a warp's input rows as TIn, then its
-  // results as TOut) | halo rows: K before the chunk, K after | dot-product
-  // partials [ND][TPD] (float pairs) | per boundary k = 0..W: b~_k, x~_k, the
-  // coupling terms of segment k's first bulk rows and of segment k-1's last
-  // (R doubles each)
-  const int K = a.K;
-  TIn* Hp = reinterpret_cast<TIn*>(smem + lw_off_halo());
-  TIn* Hn = Hp + K;
-  float2* Pp = reinterpret_cast<float2*>(smem + lw_off_halo() + (size_t)(2 * K * sizeof(TIn) + 15) / 16 * 16);
-  double* Bt = reinterpret_cast<double*>(Pp + ND * TPD);
-  double* Xt = Bt + (W + 1) * R;
-  double* CF = Xt + (W + 1) * R;
-  double* CL = CF + (W + 1) * R;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto slots = [&](int k) { return reinterpret_cast<TIn*>(smem + (size_t)k * kSlotsPerWarp * 8); };
-
-  const int chunk = (int)(blockIdx.x % (unsigned)wa.nchunks);
-  const int64_t line = blockIdx.x / (unsigned)wa.nchunks;
-  const int sfirst = wa.seg0 + chunk * W;
-  const int nv = min(W, wa.seg0 + wa.nseg - sfirst);  // segments of this CTA
-  const bool valid = w < nv;
-  const int N = seg_rows(a, sfirst) - R;  // bulk rows, the same for every segment of a launch
-  const TIn* bl = (const TIn*)a.in + line * a.n;
-  TOut* xl = (TOut*)a.out + line * a.n;
-  const int64_t S0 = seg_start(a, sfirst);
-  const int64_t s0 = S0 + (int64_t)w * (N + R);
-
-  // A: every warp stages its segment's bulk rows and b~; warp 0 the last K
-  // bulk rows of the segment before the CTA, warp W - 1 the interface rows
-  // and first K bulk rows of the segment after it (both cyclic)
-  // lane l moves bulk rows l + 32 t (coalesced): slot (l & 15) * 33 + (l >> 4) + 2 t
-  const int sb = (lane & 15) * kSlot + (lane >> 4);
-  if (valid) {
-    TIn* S = slots(w) + sb;
-    const TIn* bb = bl + s0 + R + lane;
-#pragma unroll
-    for (int t = 0; t < kWarpM; t++)
-      if (lane + 32 * t < N) S[2 * t] = __ldg(bb + 32 * t);
-    if (lane < R) Bt[w * R + lane] = (double)__ldg(bl + s0 + lane);
-  }
-  if (w == 0) {
-    const int64_t e = (S0 == 0 ? a.n : S0) - 1;  // last bulk row of the segment before
-    for (int j = lane; j < K; j += 32) Hp[j] = __ldg(bl + e - j);
-  } else if (w == W - 1) {
-    const int sn = sfirst + nv;
-    const int64_t s1 = sn == a.p ? 0 : S0 + (int64_t)nv * (N + R);  // the segment after
-    for (int j = lane; j < K; j += 32) Hn[j] = __ldg(bl + s1 + R + j);
-    if (lane < R) Bt[nv * R + lane] = (double)__ldg(bl + s1 + lane);
-  }
-  __syncthreads();
-
-  // B: the end rows of y for every boundary k = 0..nv (Sec. 4: only these
-  // cross segments): left end y_{k-1}[N - R + e] and right end y_k[e], each
-  // a truncated dot product of K rows with a row of D^{-1} (persymmetric:
-  // row R - 1 - e serves the last rows), in double-float
-  {
-    const int d = threadIdx.x / TPD, part = threadIdx.x % TPD;
-    const int k = d / (2 * R), e = d % (2 * R);
-    if (d < ND && k <= nv) {
-      float ah = 0.f, al = 0.f;
-      const bool left = e < R;
-      const int g = left ? R - 1 - e : e - R;
-      const float* Gh = wa.Gh + g * K;
-      const float* Gl = wa.Gl + g * K;
-      if (left) {
-        const TIn* S = k > 0 ? slots(k - 1) : nullptr;
-        for (int j = part; j < K; j += TPD) {
-          const int row = N - 1 - j;
-          const TIn b = k > 0 ? S[(row & 15) * kSlot + (row >> 4)] : Hp[j];
-          df_madd(ah, al, __ldg(Gh + j), __ldg(Gl + j), b);
-        }
-      } else {
-        const TIn* S = k < nv ? slots(k) : nullptr;
-        for (int j = part; j < K; j += TPD) {
-          const TIn b = k < nv ? S[(j & 15) * kSlot + (j >> 4)] : Hn[j];
-          df_madd(ah, al, __ldg(Gh + j), __ldg(Gl + j), b);
-        }
-      }
-      Pp[d * TPD + part] = make_float2(ah, al);
-    }
-  }
-  __syncthreads();
-
-  // C: one lane per boundary: x~_k = D-hat^{-1} (b~_k - L~ y_{k-1}[last] -
-  // U~ y_k[first]) (Eq. 21, the decoupled outer system) and the Eq. 9
-  // couplings of the bulk rows next to it
-  if (w == 0 && lane <= nv) {
-    const int k = lane;
-    double y[2 * R];
-#pragma unroll
-    for (int e = 0; e < 2 * R; e++) {
-      float h = 0.f, l = 0.f;
-      for (int q = 0; q < TPD; q++) {
-        const float2 v = Pp[(k * 2 * R + e) * TPD + q];
-        const f2 s = two_sum(h, v.x);
-        h = s.hi;
-        l += s.lo + v.y;
-      }
-      y[e] = f32_to_f64(h) + f32_to_f64(l);
-    }
-    double bh[R], xt[R];
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-      double v = Bt[k * R + q];
-#pragma unroll
-      for (int e = 0; e < R; e++) v -= wa.Lt[q * R + e] * y[e] + wa.Ut[q * R + e] * y[R + e];
-      bh[q] = v;
-    }
-#pragma unroll
-    for (int q = 0; q < R; q++) {
-      double v = 0.0;
-#pragma unroll
-      for (int e = 0; e < R; e++) v += wa.Dinv[q * R + e] * bh[e];
-      xt[q] = v;
-      Xt[k * R + q] = v;
-    }
-    // bulk row j < R of segment k couples to x~_k[q] at band offset q - R - j;
-    // bulk row N - R + j of segment k - 1 at offset q + R - j
-#pragma unroll
-    for (int j = 0; j < R; j++) {
-      double c = 0.0, dd = 0.0;
-#pragma unroll
-      for (int q = 0; q < R; q++) {
-        if (q >= j) c += a.band[q - j] * xt[q];
-        if (q <= j) dd += a.band[q - j + 2 * R] * xt[q];
-      }
-      CF[k * R + j] = c;
-      CL[k * R + j] = dd;
-    }
-  }
-  __syncthreads();
-  if (!valid) return;  // no barrier below
-
-  // D: the segment's bulk: D_i x_i = b_i - (couplings) (Eq. 9), the inner
-  // partition method in registers, a lane per partition
-  const int P = tin.p;  // 32 or 31 inner partitions
-  const bool lane_ok = lane < P;
-  double cF[R], cL[R];
-#pragma unroll
-  for (int j = 0; j < R; j++) {
-    cF[j] = lane == 0 ? CF[w * R + j] : 0.0;
-    cL[j] = lane == P - 1 ? CL[(w + 1) * R + j] : 0.0;
-  }
-  TIn* S = slots(w);
-  TOut* O = reinterpret_cast<TOut*>(S);
-  WarpXchg xch{32};
-  using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;
-  bool bad = false;
-  if constexpr (!refine_mode(MODE)) {
-    using T = typename std::conditional<MODE == kModeF64, double, float>::type;
-    T v[kWarpM];
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
-      T val = lane_ok ? conv<T>(S[k * kSlot + lane]) : T(0);
-      if (k < R) val -= conv<T>(cF[k]);
-      if (k >= kWarpM - R) val -= conv<T>(cL[k - (kWarpM - R)]);
-      v[k] = val;
-    }
-    lw_solve<T, R, T>(v, lane, P, tin, wa.ifc);
-    __syncwarp();  // every lane has read its input slots
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) O[k * kSlot + lane] = conv<TOut>(v[k]);
-  } else {
-    float bh[kWarpM], blo[kWarpM], xh[kWarpM], xlo[kWarpM], v[kWarpM];
-    f2 sF[R], sL[R];
-#pragma unroll
-    for (int e = 0; e < R; e++) {
-      sF[e] = split_f64(cF[e]);
-      sL[e] = split_f64(cL[e]);
-    }
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
-      const f2 sv = lane_ok ? split_in(S[k * kSlot + lane]) : f2{0.f, 0.f};
-      f2 c = {0.f, 0.f};
-      if (k < R) c = sF[k];
-      if (k >= kWarpM - R) c = sL[k - (kWarpM - R)];
-      const f2 dd = two_sum(sv.hi, -c.hi);  // subtract the coupling exactly
-      bh[k] = dd.hi;
-      blo[k] = dd.lo + (sv.lo - c.lo);
-      v[k] = dd.hi;
-    }
-    lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
-      xh[k] = v[k];
-      xlo[k] = 0.f;
-    }
-    for (int sw = 0; sw < a.sweeps; sw++) {
-      if (sw == 0) residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
-      else residual_sym2<R, kWarpM, true>(bh, blo, xh, xlo, v, lane, tin, xch);
-      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
-#pragma unroll
-      for (int k = 0; k < kWarpM; k++) {
-        const f2 t = two_sum(xh[k], v[k]);
-        xh[k] = t.hi;
-        xlo[k] = xlo[k] + t.lo;
-      }
-    }
-    __syncwarp();  // every lane has read its input slots
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
-      bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
-      O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(xlo[k]));
-    }
-  }
-  if (__any_sync(kFull, bad && lane_ok) && lane == 0 && wa.status) atomicExch(wa.status, (int)CBS_ERR_RANGE);
-  __syncwarp();
-  TOut* xb0 = xl + s0 + R + lane;
-#pragma unroll
-  for (int t = 0; t < kWarpM; t++)  // lane l: bulk rows l + 32 t (coalesced)
-    if (lane + 32 * t < N) xb0[32 * t] = O[sb + 2 * t];
-  if (lane < R) xl[s0 + lane] = (TOut)Xt[w * R + lane];  // the segment's interface rows
+  long_warp_item<R, MODE, TIn, TOut>(a, tin, wa, (int)(blockIdx.x % (unsigned)wa.nchunks),
+                                     (int64_t)(blockIdx.x / (unsigned)wa.nchunks), smem);
 }
 
 template <int R, int MODE, typename TIn, typename TOut>

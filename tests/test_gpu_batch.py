@@ -95,3 +95,50 @@ def test_ragged_batch_full_workload_sampled(cuda):
         ref = oracle.derivative(fl[i0, i1], sch["lhs"], sch["rhs"], W.grid_spacing(n))
         assert oracle.rel_err(yl[i0, i1], ref) < 1e-12
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_batch_mixes_long_lines_with_grids(cuda, precision):
+    # one persistent launch over on-chip grids (derivatives) and long x-lines
+    # (right-hand side given, a warp per segment: 8192 = 16 segments in both
+    # sizes, 9 x 513 = 4617: one CTA of 8 segments and one of 1), replayed
+    # from a CUDA graph with new data
+    items = W.ragged_batch(count=6, seed=77, sizes=(32, 64, 96))
+    specs = _specs(items)
+    longs = [((1, 5, 8192), W.PENTA10["lhs"]), ((1, 3, 4617), W.LELE6_TRI["lhs"])]
+    for shape, lhs in longs:
+        specs.append((shape, 0, dict(lhs=lhs, rhs=None, precision=precision, sweeps=1)))
+    b = Batch(specs)
+    rng = np.random.default_rng(9)
+    data = [it.f for it in items] + [rng.standard_normal(shape) for shape, _ in longs]
+    ins = [torch.from_numpy(f).cuda() for f in data]
+    outs = [torch.empty_like(x) for x in ins]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.solve(ins, outs, s)
+    torch.cuda.current_stream().wait_stream(s)
+    assert abi.cbs_last_launch_count() == 1
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.solve(ins, outs)
+    fresh = [rng.uniform(-1, 1, size=f.shape) for f in data]
+    for x, f in zip(ins, fresh):
+        x.copy_(torch.from_numpy(f))
+    g.replay()
+    torch.cuda.synchronize()
+    assert abi.cbs_batch_status_poll(b.handle) == abi.CBS_OK
+    for it, f, y in zip(items, fresh, outs):
+        assert oracle.rel_err(y.cpu().numpy(), _ref(it, f)) < 1e-12
+    for (shape, lhs), f, y in zip(longs, fresh[len(items):], outs[len(items):]):
+        ref = oracle.solve_cyclic(oracle.toeplitz_bands(shape[2], lhs), f[0])
+        assert oracle.rel_err(y.cpu().numpy()[0], ref) < 1e-12
+    b.close()
+
+
+def test_batch_rejects_long_lines_off_the_warp_layout(cuda):
+    # long lines whose segments do not hold 32 x 16 rows stay separate plans
+    from paper_2101_02286_gb300.solver import make_desc
+    d = make_desc((1, 2, 1 << 16), 0, lhs=(1 / 3,), rhs=None, segments=16)
+    with pytest.raises(abi.CbsError):
+        abi.cbs_batch_create([d])
