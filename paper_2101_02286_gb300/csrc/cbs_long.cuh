@@ -45,7 +45,8 @@ struct LongGeom {
 // 32 x 16 + r rows (or 31 x 16 + r), whose outer interface system is
 // decoupled to FP64 rounding.  Launch for segments seg0 .. seg0 + nseg - 1
 // (all of one size), kLongWarps consecutive segments of one line per CTA.
-constexpr int kLongWarps = 8;
+constexpr int kLongWarps = 4;
+constexpr int kLongCtasPerSm = 5;  // register budget of the kernel: 65536 / (5 x 128 threads) -> 96 per thread
 // The inner (segment-level) acyclic interface system of one segment size in
 // compact form: the stages that act, in order.  Entry e has flags bit 0 (a
 // message stage: x~ -= KM x~_{i-s} + KP x~_{i+s}, from the values before the

@@ -5,7 +5,7 @@
 namespace cbs {
 
 template <int R, int MODE, typename TIn, typename TOut>
-__global__ void __launch_bounds__(kLongWarps * 32, 2)
+__global__ void __launch_bounds__(kLongWarps * 32, kLongCtasPerSm)
     long_warp_kernel(const LongArgs a, const DevLineTables tin, const LongWarpArgs wa) {
   extern __shared__ __align__(16) unsigned char smem[];
   long_warp_item<R, MODE, TIn, TOut>(a, tin, wa, (int)(blockIdx.x % (unsigned)wa.nchunks),

@@ -339,13 +339,16 @@ __device__ __forceinline__ void long_warp_item(const LongArgs& a, const DevLineT
 #pragma unroll
     for (int k = 0; k < kWarpM; k++) {
       const f2 sv = lane_ok ? split_in(S[k * kSlot + lane]) : f2{0.f, 0.f};
-      f2 c = {0.f, 0.f};
-      if (k < R) c = sF[k];
-      if (k >= kWarpM - R) c = sL[k - (kWarpM - R)];
-      const f2 dd = two_sum(sv.hi, -c.hi);  // subtract the coupling exactly
-      bh[k] = dd.hi;
-      blo[k] = dd.lo + (sv.lo - c.lo);
-      v[k] = dd.hi;
+      if (k < R || k >= kWarpM - R) {  // the rows that carry a coupling term
+        const f2 c = k < R ? sF[k] : sL[k - (kWarpM - R)];
+        const f2 dd = two_sum(sv.hi, -c.hi);  // subtract the coupling exactly
+        bh[k] = dd.hi;
+        blo[k] = dd.lo + (sv.lo - c.lo);
+      } else {  // FP32 input: the low part is the constant zero
+        bh[k] = sv.hi;
+        blo[k] = sv.lo;
+      }
+      v[k] = bh[k];
     }
     lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
 #pragma unroll
