@@ -46,7 +46,10 @@ struct LongGeom {
 // decoupled to FP64 rounding.  Launch for segments seg0 .. seg0 + nseg - 1
 // (all of one size), kLongWarps consecutive segments of one line per CTA.
 constexpr int kLongWarps = 4;
-constexpr int kLongCtasPerSm = 5;  // register budget of the kernel: 65536 / (5 x 128 threads) -> 96 per thread
+// Register budget of the kernel as CTAs per SM (65536 / (CTAs x 128 threads)
+// registers per thread): 8 (64 registers) for the FP64 / FP32 modes and the
+// one-sweep refinement, 5 (96) for more sweeps, which keep x0 as a float pair.
+constexpr int long_ctas_per_sm(bool light) { return light ? 8 : 5; }
 // The inner (segment-level) acyclic interface system of one segment size in
 // compact form: the stages that act, in order.  Entry e has flags bit 0 (a
 // message stage: x~ -= KM x~_{i-s} + KP x~_{i+s}, from the values before the

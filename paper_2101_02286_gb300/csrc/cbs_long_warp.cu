@@ -4,19 +4,20 @@
 
 namespace cbs {
 
-template <int R, int MODE, typename TIn, typename TOut>
-__global__ void __launch_bounds__(kLongWarps * 32, kLongCtasPerSm)
+template <int R, int MODE, typename TIn, typename TOut, bool SW1>
+__global__ void __launch_bounds__(kLongWarps * 32, long_ctas_per_sm(SW1 || !refine_mode(MODE)))
     long_warp_kernel(const LongArgs a, const DevLineTables tin, const LongWarpArgs wa) {
   extern __shared__ __align__(16) unsigned char smem[];
-  long_warp_item<R, MODE, TIn, TOut>(a, tin, wa, (int)(blockIdx.x % (unsigned)wa.nchunks),
-                                     (int64_t)(blockIdx.x / (unsigned)wa.nchunks), smem);
+  long_warp_item<R, MODE, TIn, TOut, SW1>(a, tin, wa, (int)(blockIdx.x % (unsigned)wa.nchunks),
+                                          (int64_t)(blockIdx.x / (unsigned)wa.nchunks), smem);
 }
 
 template <int R, int MODE, typename TIn, typename TOut>
 cudaError_t launch_long_warp_t(const LongArgs& a, const DevLineTables& tin, const LongWarpArgs& wa, cudaStream_t s) {
   const size_t smem = lw_bytes<R>(a.K, (int)sizeof(TIn));  // <= 48 KB for K <= 496: no opt-in needed
   if (a.K > 16 * 31 || smem > 48 * 1024) return cudaErrorInvalidValue;
-  auto kern = long_warp_kernel<R, MODE, TIn, TOut>;
+  auto kern = refine_mode(MODE) && a.sweeps == 1 ? long_warp_kernel<R, MODE, TIn, TOut, refine_mode(MODE)>
+                                                   : long_warp_kernel<R, MODE, TIn, TOut, false>;
   const int64_t blocks = a.lines * wa.nchunks;
   if (blocks > 0x7fffffff || wa.nchunks < 1) return cudaErrorInvalidValue;
   kern<<<(unsigned)blocks, kLongWarps * 32, smem, s>>>(a, tin, wa);

@@ -164,7 +164,9 @@ __host__ __device__ constexpr size_t lw_bytes(int K, int in_size) {
 // One CTA's work: segments seg0 + chunk * kLongWarps .. of `line`, shared
 // memory at smem (lw_bytes<R>(K, sizeof(TIn)) bytes, 16-byte aligned).  All
 // threads of the CTA (kLongWarps warps) call it; it ends without a barrier.
-template <int R, int MODE, typename TIn, typename TOut>
+// SW1: the plan runs one refinement sweep (compiled apart: the sum x0 +
+// delta then needs no extra registers across the second solve).
+template <int R, int MODE, typename TIn, typename TOut, bool SW1 = false>
 __device__ __forceinline__ void long_warp_item(const LongArgs& a, const DevLineTables& tin, const LongWarpArgs& wa,
                                                const int chunk, const int64_t line, unsigned char* smem) {
   constexpr int W = kLongWarps, ND = kNdot<R>, TPD = kTpd<R>;
@@ -356,7 +358,17 @@ __device__ __forceinline__ void long_warp_item(const LongArgs& a, const DevLineT
       xh[k] = v[k];
       xlo[k] = 0.f;
     }
-    for (int sw = 0; sw < a.sweeps; sw++) {
+    if constexpr (SW1) {  // one sweep: x = x0 + delta, added in FP64 at the output
+      residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
+      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
+      __syncwarp();  // every lane has read its input slots
+#pragma unroll
+      for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
+        bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
+        O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(v[k]));
+      }
+    }
+    for (int sw = 0; sw < (SW1 ? 0 : a.sweeps); sw++) {
       if (sw == 0) residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
       else residual_sym2<R, kWarpM, true>(bh, blo, xh, xlo, v, lane, tin, xch);
       lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
@@ -367,11 +379,13 @@ __device__ __forceinline__ void long_warp_item(const LongArgs& a, const DevLineT
         xlo[k] = xlo[k] + t.lo;
       }
     }
-    __syncwarp();  // every lane has read its input slots
+    if constexpr (!SW1) {
+      __syncwarp();  // every lane has read its input slots
 #pragma unroll
-    for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
-      bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
-      O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(xlo[k]));
+      for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
+        bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
+        O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(xlo[k]));
+      }
     }
   }
   if (__any_sync(kFull, bad && lane_ok) && lane == 0 && wa.status) atomicExch(wa.status, (int)CBS_ERR_RANGE);
