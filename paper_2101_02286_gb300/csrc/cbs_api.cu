@@ -33,6 +33,7 @@ void batch_fill_problem(void* dst, const LineArgs& a, const DevLineTables& t, in
 void batch_fill_long(void* dst, const LongArgs& la, const DevLineTables& inner, const LongWarpArgs& wa, int R,
                      int MODE, int user);
 int batch_long_variant_host(int R, int MODE);
+int batch_f32_variant_host(int R, int KS, int M);
 size_t batch_long_bytes(int R, int K);
 constexpr int kBatchMax = 256;
 bool tma_eligible(int mode, int KS, bool staggered, bool in64, bool out64, const LineArgs& a, const DevLineTables& t);
@@ -1222,11 +1223,14 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   std::vector<double> cost;
   for (int k = 0; k < count; k++) {
     const cbs_desc& d = descs[k];
-    if (d.lhs_kind != CBS_LHS_TOEPLITZ || d.in_dtype != CBS_DTYPE_F64 || d.out_dtype != CBS_DTYPE_F64 ||
-        (d.precision != CBS_FP64 && d.precision != CBS_FP32_REFINE) || is_staggered(&d) || d.closure_rows) {
+    const bool f32 = d.precision == CBS_FP32 && d.in_dtype == CBS_DTYPE_F32 && d.out_dtype == CBS_DTYPE_F32;
+    const bool f64io = d.in_dtype == CBS_DTYPE_F64 && d.out_dtype == CBS_DTYPE_F64 &&
+                       (d.precision == CBS_FP64 || d.precision == CBS_FP32_REFINE);
+    if (d.lhs_kind != CBS_LHS_TOEPLITZ || !(f32 || f64io) || is_staggered(&d) || d.closure_rows || d.bandwidth > 5) {
       cbs_batch_destroy(B);
       return fail(CBS_ERR_UNSUPPORTED,
-                  "batch problems: Toeplitz, FP64 in/out, FP64 or FP32_REFINE, no staggered stencil or closures");
+                  "batch problems: Toeplitz bands of width 3 or 5; FP64 or FP32_REFINE with FP64 in/out, or FP32 "
+                  "with FP32 in/out; no staggered stencil or closures");
     }
     cbs_plan* P = nullptr;
     cbs_status st = cbs_plan_create(&P, &d);
@@ -1236,7 +1240,7 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       return fail(st, msg);
     }
     B->plans.push_back(P);
-    const int mode = d.precision == CBS_FP64 ? kModeF64 : kModeRefine;
+    const int mode = d.precision == CBS_FP64 ? kModeF64 : d.precision == CBS_FP32 ? kModeF32 : kModeRefine;
     if (P->kind != 0) {
       // long lines: the x-lines of a warp-per-segment plan, an entry per
       // segment size, an item per (chunk of kLongWarps segments, line)
@@ -1270,8 +1274,13 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       continue;
     }
     const bool full = P->dev.count_big == P->dev.p && P->dev.rows_big == 16 && P->M == 16;
-    int variant = full ? batch_variant_host(P->r, P->ks, P->M, mode, true) : -1;
-    if (variant < 0) variant = batch_variant_host(P->r, P->ks, P->M, mode, false);
+    int variant = -1;
+    if (mode == kModeF32) {
+      variant = batch_f32_variant_host(P->r, P->ks, P->M);
+    } else {
+      variant = full ? batch_variant_host(P->r, P->ks, P->M, mode, true) : -1;
+      if (variant < 0) variant = batch_variant_host(P->r, P->ks, P->M, mode, false);
+    }
     if (variant < 0) {
       cbs_batch_destroy(B);
       return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": tile variant not compiled");
@@ -1290,7 +1299,18 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
     B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
     nent++;
   }
-  // most expensive tiles first, so the static stride ends with small tiles
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cbs_batch_destroy(B);
+    return cuda_fail(e, "batch setup");
+  }
+  const int grid = (int)std::min<size_t>(items.size(), 2 * (size_t)sms);
+  // most expensive tiles first, so the static stride (CTA b takes positions
+  // b, b + grid, ...) ends with small tiles; FP64 and other tiles stay mixed
+  // on every SM (FP64 tiles on CTAs of their own measured 6.38 against 4.54
+  // ms on the 48-grid batch: the FP64 pipe then idles on half of the SMs)
   std::vector<size_t> order(items.size());
   for (size_t q = 0; q < order.size(); q++) order[q] = q;
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
@@ -1299,19 +1319,16 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   B->nitems = (int)sorted.size();
   B->count = count;
   B->smem = batch_smem(B->smem);  // + the current problem's tables
-  cudaError_t e = batch_configure(B->smem);
+  e = batch_configure(B->smem);
   if (e == cudaSuccess) e = cudaMalloc(&B->dprobs, probs.size());
   if (e == cudaSuccess) e = cudaMalloc(&B->ditems, sorted.size() * sizeof(int4));
   if (e == cudaSuccess) e = cudaMemcpy(B->dprobs, probs.data(), probs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(B->ditems, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice);
-  int dev = 0, sms = 0;
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) {
     cbs_batch_destroy(B);
     return cuda_fail(e, "batch setup");
   }
-  B->grid = std::min(B->nitems, 2 * sms);
+  B->grid = grid;
   *out = B;
   return CBS_OK;
 }

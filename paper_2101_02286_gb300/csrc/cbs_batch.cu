@@ -41,7 +41,8 @@ struct BatchParams {
 // The tile variants compiled into the persistent kernel: (R, KS) in
 // {(1,2), (2,3), (1,0), (2,0)} x M in {8, 16} x {FP64, FP32 + refinement},
 // plus whole-size 16-row partitions (FULL: compile-time sizes) of the same
-// (R, KS, mode); FP64 input and output.
+// (R, KS, mode), FP64 input and output; the same (R, KS) x M in the FP32
+// mode with FP32 input and output.
 __host__ __device__ constexpr int batch_variant(int R, int KS, int M, int MODE, bool FULL = false) {
   const int rk = (R == 1 && KS == 2) ? 0 : (R == 2 && KS == 3) ? 1 : (R == 1 && KS == 0) ? 2 : (R == 2 && KS == 0) ? 3 : -1;
   const int mi = FULL ? (M == 16 ? 2 : -1) : (M == 8) ? 0 : (M == 16) ? 1 : -1;
@@ -55,6 +56,20 @@ __host__ __device__ constexpr int batch_long_variant(int R, int MODE) {
   return (R < 1 || R > 2 || (MODE != kModeF64 && MODE != kModeRefine)) ? -1
                                                                        : kBatchLong + (R - 1) * 2 + (MODE == kModeRefine);
 }
+
+// FP32 problems (FP32 in and out, the FP32 mode): after the long-line entries.
+constexpr int kBatchF32 = 28;
+__host__ __device__ constexpr int batch_f32_variant(int R, int KS, int M) {
+  const int rk = (R == 1 && KS == 2) ? 0 : (R == 2 && KS == 3) ? 1 : (R == 1 && KS == 0) ? 2 : (R == 2 && KS == 0) ? 3 : -1;
+  const int mi = (M == 8) ? 0 : (M == 16) ? 1 : -1;
+  return (rk < 0 || mi < 0) ? -1 : kBatchF32 + rk * 2 + mi;
+}
+
+#define CBS_BV32(R, KS, M)                                                                       \
+  case batch_f32_variant(R, KS, M):                                                              \
+    line_tile<R, M, kModeF32, KS, float, float>(P.args, P.tab, bp.in[P.user], bp.out[P.user], w.y, w.z, \
+                                                tile_smem);                                      \
+    break;
 
 #define CBS_BV(R, KS, M, MODE)                                                                   \
   case batch_variant(R, KS, M, MODE):                                                            \
@@ -132,6 +147,14 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
       CBS_BL(1, kModeRefine)
       CBS_BL(2, kModeF64)
       CBS_BL(2, kModeRefine)
+      CBS_BV32(1, 2, 8)
+      CBS_BV32(1, 2, 16)
+      CBS_BV32(2, 3, 8)
+      CBS_BV32(2, 3, 16)
+      CBS_BV32(1, 0, 8)
+      CBS_BV32(1, 0, 16)
+      CBS_BV32(2, 0, 8)
+      CBS_BV32(2, 0, 16)
       default:
         break;
     }
@@ -141,6 +164,7 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ B
 #undef CBS_BV
 #undef CBS_BVF
 #undef CBS_BL
+#undef CBS_BV32
 
 int batch_variant_host(int R, int KS, int M, int MODE, bool full) { return batch_variant(R, KS, M, MODE, full); }
 
@@ -193,6 +217,7 @@ void batch_fill_long(void* dst, const LongArgs& la, const DevLineTables& inner, 
 }
 
 int batch_long_variant_host(int R, int MODE) { return batch_long_variant(R, MODE); }
+int batch_f32_variant_host(int R, int KS, int M) { return batch_f32_variant(R, KS, M); }
 
 // Shared memory of a long-line entry (truncation length K, FP64 input).
 size_t batch_long_bytes(int R, int K) { return R == 1 ? lw_bytes<1>(K, 8) : lw_bytes<2>(K, 8); }

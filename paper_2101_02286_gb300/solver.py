@@ -135,21 +135,25 @@ class Plan:
 class Batch:
     """A ragged batch of independent problems solved by one persistent launch.
 
-    specs: list of (shape_zyx, direction, kwargs for make_desc).  FP64 input
-    and output, Toeplitz bands, precision "fp64" or "fp32_refine".
+    specs: list of (shape_zyx, direction, kwargs for make_desc).  Toeplitz
+    bands; precision "fp64" or "fp32_refine" with FP64 input and output, or
+    "fp32" with FP32 input and output (in_dtype=torch.float32); long x-lines
+    whose plan runs a warp per segment.
     """
 
     def __init__(self, specs):
         self.shapes = [tuple(int(v) for v in sh) for sh, _, _ in specs]
+        self.dtypes = [kw.get("in_dtype", torch.float64) for _, _, kw in specs]
         descs = [make_desc(sh, d, **kw) for sh, d, kw in specs]
         self.handle = abi.cbs_batch_create(descs)
 
     def solve(self, ins, outs=None, stream: torch.cuda.Stream | None = None):
         if outs is None:
             outs = [torch.empty_like(x) for x in ins]
-        for x, y, sh in zip(ins, outs, self.shapes):
-            if x.shape != sh or y.shape != sh or x.dtype != torch.float64 or not x.is_contiguous():
-                raise ValueError("batch inputs/outputs must be contiguous FP64 tensors of the planned shapes")
+        for x, y, sh, dt in zip(ins, outs, self.shapes, self.dtypes):
+            if x.shape != sh or y.shape != sh or x.dtype != dt or y.dtype != dt or not x.is_contiguous() \
+                    or not y.is_contiguous():
+                raise ValueError("batch inputs/outputs must be contiguous tensors of the planned shapes and dtypes")
         s = stream if stream is not None else torch.cuda.current_stream(ins[0].device)
         abi.cbs_batch_solve(self.handle, [x.data_ptr() for x in ins], [y.data_ptr() for y in outs], s.cuda_stream)
         return outs

@@ -70,9 +70,11 @@ def test_ragged_batch_cuda_graph(cuda):
 
 def test_batch_rejects_unsupported(cuda):
     from paper_2101_02286_gb300.solver import make_desc
-    d = make_desc((4, 4, 64), 0, lhs=(1 / 3,), precision="fp32", in_dtype=torch.float32)
-    with pytest.raises(abi.CbsError):
-        abi.cbs_batch_create([d])
+    # heptadiagonal bands and FP32 input with an FP64 result stay single plans
+    for d in (make_desc((4, 4, 64), 0, lhs=W.HEPTA12["lhs"]),
+              make_desc((4, 4, 64), 0, lhs=(1 / 3,), precision="fp32_refine", in_dtype=torch.float32)):
+        with pytest.raises(abi.CbsError):
+            abi.cbs_batch_create([d])
 
 
 @pytest.mark.slow
@@ -142,3 +144,34 @@ def test_batch_rejects_long_lines_off_the_warp_layout(cuda):
     d = make_desc((1, 2, 1 << 16), 0, lhs=(1 / 3,), rhs=None, segments=16)
     with pytest.raises(abi.CbsError):
         abi.cbs_batch_create([d])
+
+
+def test_batch_fp32_problems_with_fp64_ones(cuda):
+    # FP32 problems (FP32 in and out, no refinement) in the same launch as
+    # FP64 and refinement problems; tolerance 2e-5 for the FP32 ones
+    items = W.ragged_batch(count=6, seed=91, sizes=(32, 48, 64, 96))
+    specs = _specs(items)
+    f32 = []
+    for k, (shape, direction, scheme) in enumerate([((8, 12, 64), 0, "tri6"), ((16, 96, 8), 1, "penta10"),
+                                                    ((48, 8, 8), 2, "tri6")]):
+        n = shape[2 - direction]
+        sch = SCH[scheme]
+        specs.append((shape, direction, dict(lhs=sch["lhs"], rhs=sch["rhs"], h=W.grid_spacing(n), precision="fp32",
+                                             in_dtype=torch.float32)))
+        f32.append((shape, direction, scheme))
+    b = Batch(specs)
+    rng = np.random.default_rng(4)
+    data = [it.f for it in items] + [rng.uniform(-1, 1, size=sh).astype(np.float32) for sh, _, _ in f32]
+    ins = [torch.from_numpy(f).cuda() for f in data]
+    outs = b.solve(ins)
+    torch.cuda.synchronize()
+    assert abi.cbs_last_launch_count() == 1
+    for it, y in zip(items, outs):
+        assert oracle.rel_err(y.cpu().numpy(), _ref(it, it.f)) < 1e-12
+    for (shape, direction, scheme), f, y in zip(f32, data[len(items):], outs[len(items):]):
+        assert y.dtype == torch.float32
+        n = shape[2 - direction]
+        sch = SCH[scheme]
+        ref = oracle.derivative(f.astype(np.float64), sch["lhs"], sch["rhs"], W.grid_spacing(n), axis=2 - direction)
+        assert oracle.rel_err(y.double().cpu().numpy(), ref) < 2e-5
+    b.close()
