@@ -318,9 +318,9 @@ cbs_status cbs_interface_model(const cbs_desc* desc, int32_t p, double* dhat, do
 /* Ragged batch: up to `count` (<= 256) independent problems (each its own
  * cbs_desc, in and out arrays) solved by one persistent launch per call.
  * The batch pre-builds every problem's plan tables and a work table of line
- * tiles.  Problems: Toeplitz bands of bandwidth 3 or 5, FP64 in and out,
- * CBS_FP64 or CBS_FP32_REFINE, the central stencil or the right-hand side
- * given; lines that fit one warp (on-chip plans), and long x-lines whose
+ * tiles.  Problems: Toeplitz bands of bandwidth 3 or 5; CBS_FP64 or
+ * CBS_FP32_REFINE with FP64 in and out, or CBS_FP32 with FP32 in and out;
+ * the central stencil or the right-hand side given; lines that fit one warp (on-chip plans), and long x-lines whose
  * plan runs a warp per segment (cbs_plan_info.segment_warp = 1: right-hand
  * side given, segments of 32 x 16 + r rows), which enter the work table as
  * (chunk of 8 segments, line) items.  Allocates device memory at creation,
