@@ -294,8 +294,8 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     lines, n = d.shape
     di = torch.from_numpy(d.reshape(1, lines, n)).to(dev)
     do = torch.empty((1, lines, n), dtype=torch.float64, device=dev)
-    # default segments: 8168 of 514 / 498 rows, a warp per segment and 8
-    # segments per CTA (1021 thread blocks per line); p = 1024: the end-row /
+    # default segments: 8168 of 514 / 498 rows, a warp per segment and 4
+    # segments per CTA (2042 thread blocks per line); p = 1024: the end-row /
     # interface / segment launches (segments of ~4096 rows, a CTA each)
     for prec, sweeps, seg in (("fp32_refine", 1, 0), ("fp32_refine", 2, 1024), ("fp64", 1, 0)):
         pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, segments=seg, precision=prec,
@@ -307,7 +307,7 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
             k = int(rng.integers(0, lines))
             ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d[k:k + 1].astype(np.float64))
             err = oracle.rel_err(do[0, k:k + 1].cpu().numpy(), ref)
-        how = ("%d segments, a warp each, %d per thread block" % (info["segments"], 8) if info["segment_warp"]
+        how = ("%d segments, a warp each, 4 per thread block" % info["segments"] if info["segment_warp"]
                else "%d segments across CTAs" % info["segments"])
         res.append(_entry("32 x 2^22 cyclic penta (1/20,1/2,1,1/2,1/20), N(0,1) rhs stored FP32, FP64 out, "
                           "%s, %s sweeps=%d" % (how, prec, sweeps),
@@ -355,7 +355,8 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     # (fields 8192 x 256 x 256, 256 x 8192 x 256, 256 x 256 x 8192), cyclic
     # tridiagonal alpha = 1/3, right-hand side given; x: the default (16
     # segments of 513 / 497 rows, a warp each) and p = 7 (2^n - 1),
-    # y/z: p = 16 (the default: 512-row segments, tiles of 8 strided lines);
+    # y/z: p = 16 (the default: segments of 513 / 497 rows, a warp each, one
+    # segment of 4 adjacent lines per CTA);
     # the three fields share one buffer of random values
     dpx = np.random.default_rng(20).standard_normal(256 * 256 * 8192)
     di = torch.from_numpy(dpx).to(dev)

@@ -520,7 +520,7 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   const bool tiled = d->direction != 0;
   const int max_inner = tiled ? 1024 / kLongLines : 512;
   int p = d->segments;
-  if (!p && !tiled) p = warp_layout_segments(n, r);  // x-lines: a warp per segment where it applies
+  if (!p) p = warp_layout_segments(n, r);  // a warp per segment where it applies
   if (!p) {  // segments of about 512 rows (y/z: tiles of 8 lines x 32 inner partitions), 1024 (x, n <= 2^16),
              // 4096 (longer x-lines)
     p = tiled ? (n + 511) / 512 : n <= 65536 ? (n + 1023) / 1024 : (n + 4095) / 4096;
@@ -598,8 +598,9 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
   // x-lines whose segments have 32 (31) whole 16-row inner partitions and
   // whose outer system is decoupled: a warp per segment (cbs_long_warp.cu)
   double Dinv[kMaxR * kMaxR] = {};
-  P->long_warp = !tiled && full && m == 16 * 32 + r && (sizes[0] == p || sizes[2] == 16 * 31 + r) && p >= 2 &&
-                 K <= 16 * 31 && outer_decoupled(P->host, r, Dinv);
+  P->long_warp = full && m == 16 * 32 + r && (sizes[0] == p || sizes[2] == 16 * 31 + r) && p >= 2 &&
+                 long_warp_fits(r, K, d->in_dtype == CBS_DTYPE_F64 ? 8 : 4, tiled) &&
+                 outer_decoupled(P->host, r, Dinv);
   if (!P->long_warp && 2 * (size_t)p * r * sizeof(double) > 227 * 1024)
     return fail(CBS_ERR_UNSUPPORTED, "long lines: more than 14528 interface unknowns per line (raise the segment size)");
   cbs_status st = fill_dev_tables(P->dev, P->host, A, d, 0, &P->dbuf, false);
@@ -697,6 +698,8 @@ cbs_status create_long(cbs_plan* P, const cbs_desc* d) {
         w.Ut[q * r + e] = P->host.Ut[q][e];
       }
     w.status = P->dstatus;
+    w.gm = P->lgeom;
+    w.ngroups = (int)((P->nlines + kLongWarps - 1) / kLongWarps);
     w.Gh = gf;
     w.Gl = gf + G.size();
   }
@@ -1244,7 +1247,7 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
     if (P->kind != 0) {
       // long lines: the x-lines of a warp-per-segment plan, an entry per
       // segment size, an item per (chunk of kLongWarps segments, line)
-      if (!(P->long_warp && P->variant == 0) || batch_long_variant_host(P->r, mode) < 0) {
+      if (!(P->long_warp && P->variant == 0) || P->lgeom.dir != 0 || batch_long_variant_host(P->r, mode) < 0) {
         cbs_batch_destroy(B);
         return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) +
                                              ": long lines are batched as x-lines of a warp per segment "

@@ -36,16 +36,6 @@ namespace cbs {
 
 
 
-// Element offset of row 0 of a line (row k at + k * es); line < 2^31.
-__device__ __forceinline__ int64_t long_base(const LongArgs& a, const LongGeom& gm, int64_t line) {
-  if (gm.dir == 0) return line * a.n;
-  if (gm.dir == 1) {
-    const unsigned L = (unsigned)line, NX = (unsigned)gm.nx;
-    return (int64_t)(L % NX) + gm.nx * gm.ny * (int64_t)(L / NX);
-  }
-  return line;
-}
-
 // ---------------------------------------------------------------- 1. ends
 // One CTA per (segment, LG lines): x-lines LG = 1; y/z lines LG = kLongLines
 // adjacent lines, thread = (j, line) with the line fastest, so each row of

@@ -41,10 +41,21 @@ struct LongGeom {
   int dir;
 };
 
-// The warp-per-segment path for x-lines (cbs_long_warp.cu): segments of
-// 32 x 16 + r rows (or 31 x 16 + r), whose outer interface system is
-// decoupled to FP64 rounding.  Launch for segments seg0 .. seg0 + nseg - 1
-// (all of one size), kLongWarps consecutive segments of one line per CTA.
+// Element offset of row 0 of a line (row k at + k * es); line < 2^31.
+__device__ __forceinline__ int64_t long_base(const LongArgs& a, const LongGeom& gm, int64_t line) {
+  if (gm.dir == 0) return line * a.n;
+  if (gm.dir == 1) {
+    const unsigned L = (unsigned)line, NX = (unsigned)gm.nx;
+    return (int64_t)(L % NX) + gm.nx * gm.ny * (int64_t)(L / NX);
+  }
+  return line;
+}
+
+// The warp-per-segment path (cbs_long_warp.cu): segments of 32 x 16 + r rows
+// (or 31 x 16 + r), whose outer interface system is decoupled to FP64
+// rounding.  Launch for segments seg0 .. seg0 + nseg - 1 (all of one size);
+// x-lines: kLongWarps consecutive segments of one line per CTA; y/z lines:
+// one segment of kLongWarps adjacent lines per CTA.
 constexpr int kLongWarps = 4;
 // Register budget of the kernel as CTAs per SM (65536 / (CTAs x 128 threads)
 // registers per thread): 8 (64 registers) for the FP64 / FP32 modes and the
@@ -69,6 +80,8 @@ struct LongWarpArgs {
   const float* Gh;                       // [r][K] leading entries of D^{-1}'s first rows as
   const float* Gl;                       //   float pairs (G = Gh + Gl)
   LwIface ifc;                           // inner system of this launch's segment size
+  LongGeom gm;                           // line geometry (y/z lines: a CTA per group of adjacent lines)
+  int ngroups;                           // y/z lines: groups of kLongWarps adjacent lines
   int seg0, nseg, nchunks;               // nchunks = ceil(nseg / kLongWarps)
   int* status;                           // device status word
 };

@@ -4,24 +4,41 @@
 
 namespace cbs {
 
-template <int R, int MODE, typename TIn, typename TOut, bool SW1>
+template <int R, int MODE, typename TIn, typename TOut, bool SW1, bool YZ>
 __global__ void __launch_bounds__(kLongWarps * 32, long_ctas_per_sm(SW1 || !refine_mode(MODE)))
     long_warp_kernel(const LongArgs a, const DevLineTables tin, const LongWarpArgs wa) {
   extern __shared__ __align__(16) unsigned char smem[];
-  long_warp_item<R, MODE, TIn, TOut, SW1>(a, tin, wa, (int)(blockIdx.x % (unsigned)wa.nchunks),
-                                          (int64_t)(blockIdx.x / (unsigned)wa.nchunks), smem);
+  if constexpr (YZ)  // groups fastest: CTAs in flight read the same rows (z-planes) of adjacent groups
+    long_warp_item_yz<R, MODE, TIn, TOut, SW1>(a, tin, wa, wa.seg0 + (int)(blockIdx.x / (unsigned)wa.ngroups),
+                                               (int64_t)(blockIdx.x % (unsigned)wa.ngroups) * kLongWarps, smem);
+  else
+    long_warp_item<R, MODE, TIn, TOut, SW1>(a, tin, wa, (int)(blockIdx.x % (unsigned)wa.nchunks),
+                                            (int64_t)(blockIdx.x / (unsigned)wa.nchunks), smem);
 }
 
+// The launch of one segment size.
 template <int R, int MODE, typename TIn, typename TOut>
 cudaError_t launch_long_warp_t(const LongArgs& a, const DevLineTables& tin, const LongWarpArgs& wa, cudaStream_t s) {
-  const size_t smem = lw_bytes<R>(a.K, (int)sizeof(TIn));  // <= 48 KB for K <= 496: no opt-in needed
-  if (a.K > 16 * 31 || smem > 48 * 1024) return cudaErrorInvalidValue;
-  auto kern = refine_mode(MODE) && a.sweeps == 1 ? long_warp_kernel<R, MODE, TIn, TOut, refine_mode(MODE)>
-                                                   : long_warp_kernel<R, MODE, TIn, TOut, false>;
-  const int64_t blocks = a.lines * wa.nchunks;
-  if (blocks > 0x7fffffff || wa.nchunks < 1) return cudaErrorInvalidValue;
+  const bool yz = wa.gm.dir != 0;
+  const size_t smem = yz ? lwyz_bytes<R>(a.K, (int)sizeof(TIn)) : lw_bytes<R>(a.K, (int)sizeof(TIn));
+  if (a.K > 16 * 31 || smem > 48 * 1024) return cudaErrorInvalidValue;  // no opt-in above 48 KB
+  const bool sw1 = refine_mode(MODE) && a.sweeps == 1;
+  auto kern = yz ? (sw1 ? long_warp_kernel<R, MODE, TIn, TOut, refine_mode(MODE), true>
+                        : long_warp_kernel<R, MODE, TIn, TOut, false, true>)
+                 : (sw1 ? long_warp_kernel<R, MODE, TIn, TOut, refine_mode(MODE), false>
+                        : long_warp_kernel<R, MODE, TIn, TOut, false, false>);
+  const int64_t blocks = yz ? (int64_t)wa.ngroups * wa.nseg : a.lines * wa.nchunks;
+  if (blocks > 0x7fffffff || blocks < 1) return cudaErrorInvalidValue;
   kern<<<(unsigned)blocks, kLongWarps * 32, smem, s>>>(a, tin, wa);
   return cudaGetLastError();
+}
+
+// Whether the shared memory of one CTA stays within 48 KB (no opt-in).
+bool long_warp_fits(int R, int K, int in_size, bool yz) {
+  if (K < 1 || K > 16 * 31) return false;
+  const size_t b = yz ? (R == 1 ? lwyz_bytes<1>(K, in_size) : lwyz_bytes<2>(K, in_size))
+                      : (R == 1 ? lw_bytes<1>(K, in_size) : lw_bytes<2>(K, in_size));
+  return b <= 48 * 1024;
 }
 
 // Element types per mode: FP64 in and out for every mode; FP32 in and out

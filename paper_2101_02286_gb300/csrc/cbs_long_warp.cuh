@@ -161,6 +161,102 @@ __host__ __device__ constexpr size_t lw_bytes(int K, int in_size) {
          (size_t)(kLongWarps + 1) * R * 8 * 4;
 }
 
+// Phase D of a segment, for one warp: D_i x_i = b_i - couplings (Eq. 9) by
+// the inner partition method in registers (a lane per partition), the rows
+// read from the warp's slots S (lane i's row k at k * 33 + i) and the results
+// written back to them as TOut.  cF0 / cL0: the coupling terms of the first
+// and last R bulk rows (FP64).  Returns whether this lane's result left the
+// FP32 range (refinement modes).
+template <int R, int MODE, typename TIn, typename TOut, bool SW1>
+__device__ __forceinline__ bool lw_segment_solve(TIn* S, const double* cF0, const double* cL0, const int lane,
+                                                 const LongArgs& a, const DevLineTables& tin, const LongWarpArgs& wa) {
+  const int P = tin.p;  // 32 or 31 inner partitions
+  const bool lane_ok = lane < P;
+  double cF[R], cL[R];
+#pragma unroll
+  for (int j = 0; j < R; j++) {
+    cF[j] = lane == 0 ? cF0[j] : 0.0;
+    cL[j] = lane == P - 1 ? cL0[j] : 0.0;
+  }
+  TOut* O = reinterpret_cast<TOut*>(S);
+  WarpXchg xch{32};
+  using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;
+  bool bad = false;
+  if constexpr (!refine_mode(MODE)) {
+    using T = typename std::conditional<MODE == kModeF64, double, float>::type;
+    T v[kWarpM];
+#pragma unroll
+    for (int k = 0; k < kWarpM; k++) {
+      T val = lane_ok ? conv<T>(S[k * kSlot + lane]) : T(0);
+      if (k < R) val -= conv<T>(cF[k]);
+      if (k >= kWarpM - R) val -= conv<T>(cL[k - (kWarpM - R)]);
+      v[k] = val;
+    }
+    lw_solve<T, R, T>(v, lane, P, tin, wa.ifc);
+    __syncwarp();  // every lane has read its input slots
+#pragma unroll
+    for (int k = 0; k < kWarpM; k++) O[k * kSlot + lane] = conv<TOut>(v[k]);
+  } else {
+    float bh[kWarpM], blo[kWarpM], xh[kWarpM], xlo[kWarpM], v[kWarpM];
+    f2 sF[R], sL[R];
+#pragma unroll
+    for (int e = 0; e < R; e++) {
+      sF[e] = split_f64(cF[e]);
+      sL[e] = split_f64(cL[e]);
+    }
+#pragma unroll
+    for (int k = 0; k < kWarpM; k++) {
+      const f2 sv = lane_ok ? split_in(S[k * kSlot + lane]) : f2{0.f, 0.f};
+      if (k < R || k >= kWarpM - R) {  // the rows that carry a coupling term
+        const f2 c = k < R ? sF[k] : sL[k - (kWarpM - R)];
+        const f2 dd = two_sum(sv.hi, -c.hi);  // subtract the coupling exactly
+        bh[k] = dd.hi;
+        blo[k] = dd.lo + (sv.lo - c.lo);
+      } else {  // FP32 input: the low part is the constant zero
+        bh[k] = sv.hi;
+        blo[k] = sv.lo;
+      }
+      v[k] = bh[k];
+    }
+    lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
+#pragma unroll
+    for (int k = 0; k < kWarpM; k++) {
+      xh[k] = v[k];
+      xlo[k] = 0.f;
+    }
+    if constexpr (SW1) {  // one sweep: x = x0 + delta, added in FP64 at the output
+      residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
+      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
+      __syncwarp();  // every lane has read its input slots
+#pragma unroll
+      for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
+        bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
+        O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(v[k]));
+      }
+    }
+    for (int sw = 0; sw < (SW1 ? 0 : a.sweeps); sw++) {
+      if (sw == 0) residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
+      else residual_sym2<R, kWarpM, true>(bh, blo, xh, xlo, v, lane, tin, xch);
+      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
+#pragma unroll
+      for (int k = 0; k < kWarpM; k++) {
+        const f2 t = two_sum(xh[k], v[k]);
+        xh[k] = t.hi;
+        xlo[k] = xlo[k] + t.lo;
+      }
+    }
+    if constexpr (!SW1) {
+      __syncwarp();  // every lane has read its input slots
+#pragma unroll
+      for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
+        bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
+        O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(xlo[k]));
+      }
+    }
+  }
+  return bad && lane_ok;
+}
+
 // One CTA's work: segments seg0 + chunk * kLongWarps .. of `line`, shared
 // memory at smem (lw_bytes<R>(K, sizeof(TIn)) bytes, 16-byte aligned).  All
 // threads of the CTA (kLongWarps warps) call it; it ends without a barrier.
@@ -303,98 +399,183 @@ __device__ __forceinline__ void long_warp_item(const LongArgs& a, const DevLineT
 
   // D: the segment's bulk: D_i x_i = b_i - (couplings) (Eq. 9), the inner
   // partition method in registers, a lane per partition
-  const int P = tin.p;  // 32 or 31 inner partitions
-  const bool lane_ok = lane < P;
-  double cF[R], cL[R];
-#pragma unroll
-  for (int j = 0; j < R; j++) {
-    cF[j] = lane == 0 ? CF[w * R + j] : 0.0;
-    cL[j] = lane == P - 1 ? CL[(w + 1) * R + j] : 0.0;
-  }
-  TIn* S = slots(w);
-  TOut* O = reinterpret_cast<TOut*>(S);
-  WarpXchg xch{32};
-  using TIR = typename std::conditional<MODE == kModeRefineI64, double, float>::type;
-  bool bad = false;
-  if constexpr (!refine_mode(MODE)) {
-    using T = typename std::conditional<MODE == kModeF64, double, float>::type;
-    T v[kWarpM];
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
-      T val = lane_ok ? conv<T>(S[k * kSlot + lane]) : T(0);
-      if (k < R) val -= conv<T>(cF[k]);
-      if (k >= kWarpM - R) val -= conv<T>(cL[k - (kWarpM - R)]);
-      v[k] = val;
-    }
-    lw_solve<T, R, T>(v, lane, P, tin, wa.ifc);
-    __syncwarp();  // every lane has read its input slots
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) O[k * kSlot + lane] = conv<TOut>(v[k]);
-  } else {
-    float bh[kWarpM], blo[kWarpM], xh[kWarpM], xlo[kWarpM], v[kWarpM];
-    f2 sF[R], sL[R];
-#pragma unroll
-    for (int e = 0; e < R; e++) {
-      sF[e] = split_f64(cF[e]);
-      sL[e] = split_f64(cL[e]);
-    }
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
-      const f2 sv = lane_ok ? split_in(S[k * kSlot + lane]) : f2{0.f, 0.f};
-      if (k < R || k >= kWarpM - R) {  // the rows that carry a coupling term
-        const f2 c = k < R ? sF[k] : sL[k - (kWarpM - R)];
-        const f2 dd = two_sum(sv.hi, -c.hi);  // subtract the coupling exactly
-        bh[k] = dd.hi;
-        blo[k] = dd.lo + (sv.lo - c.lo);
-      } else {  // FP32 input: the low part is the constant zero
-        bh[k] = sv.hi;
-        blo[k] = sv.lo;
-      }
-      v[k] = bh[k];
-    }
-    lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
-#pragma unroll
-    for (int k = 0; k < kWarpM; k++) {
-      xh[k] = v[k];
-      xlo[k] = 0.f;
-    }
-    if constexpr (SW1) {  // one sweep: x = x0 + delta, added in FP64 at the output
-      residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
-      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
-      __syncwarp();  // every lane has read its input slots
-#pragma unroll
-      for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
-        bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
-        O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(v[k]));
-      }
-    }
-    for (int sw = 0; sw < (SW1 ? 0 : a.sweeps); sw++) {
-      if (sw == 0) residual_sym2<R, kWarpM, false>(bh, blo, xh, xlo, v, lane, tin, xch);
-      else residual_sym2<R, kWarpM, true>(bh, blo, xh, xlo, v, lane, tin, xch);
-      lw_solve<float, R, TIR>(v, lane, P, tin, wa.ifc);
-#pragma unroll
-      for (int k = 0; k < kWarpM; k++) {
-        const f2 t = two_sum(xh[k], v[k]);
-        xh[k] = t.hi;
-        xlo[k] = xlo[k] + t.lo;
-      }
-    }
-    if constexpr (!SW1) {
-      __syncwarp();  // every lane has read its input slots
-#pragma unroll
-      for (int k = 0; k < kWarpM; k++) {  // values in the FP32 range: normal or zero (below 2^-126: flushed)
-        bad |= !(fabsf(xh[k]) <= 3.4e38f);  // inf or nan (the FP32 range was left)
-        O[k * kSlot + lane] = (TOut)(f32_to_f64_nz(xh[k]) + f32_to_f64_nz(xlo[k]));
-      }
-    }
-  }
-  if (__any_sync(kFull, bad && lane_ok) && lane == 0 && wa.status) atomicExch(wa.status, (int)CBS_ERR_RANGE);
+  const bool bad = lw_segment_solve<R, MODE, TIn, TOut, SW1>(slots(w), CF + w * R, CL + (w + 1) * R, lane, a, tin, wa);
+  TOut* O = reinterpret_cast<TOut*>(slots(w));
+  if (__any_sync(kFull, bad) && lane == 0 && wa.status) atomicExch(wa.status, (int)CBS_ERR_RANGE);
   __syncwarp();
   TOut* xb0 = xl + s0 + R + lane;
 #pragma unroll
   for (int t = 0; t < kWarpM; t++)  // lane l: bulk rows l + 32 t (coalesced)
     if (lane + 32 * t < N) xb0[32 * t] = O[sb + 2 * t];
   if (lane < R) xl[s0 + lane] = (TOut)Xt[w * R + lane];  // the segment's interface rows
+  }
+}
+
+// ---------------------------------------------------------------- y/z lines
+// Dot products of one y/z CTA: per line, the left and right ends of its two
+// boundaries (b~_s side: y_{s-1}[last], y_s[first]; b~_{s+1} side: y_s[last],
+// y_{s+1}[first]), R rows each.
+template <int R> constexpr int kNdotYZ = kLongWarps * 4 * R;
+template <int R> constexpr int kTpdYZ = kLongWarps * 32 / kNdotYZ<R>;
+
+// Shared memory of a y/z CTA: slots, halos [2][W][K] TIn, partials, and per
+// line b~ and x~ of both boundaries and the coupling terms (R doubles each).
+template <int R>
+__host__ __device__ constexpr size_t lwyz_off_part(int K, int in_size) {
+  return lw_off_halo() + (size_t)(2 * kLongWarps * K * in_size + 15) / 16 * 16;
+}
+template <int R>
+__host__ __device__ constexpr size_t lwyz_bytes(int K, int in_size) {
+  return lwyz_off_part<R>(K, in_size) + (size_t)kNdotYZ<R> * kTpdYZ<R> * 8 + (size_t)kLongWarps * R * 8 * 6;
+}
+
+// One y/z CTA: segment s of the lines line0 .. line0 + kLongWarps - 1
+// (consecutive line indices: adjacent in x), a warp per line.  Rows of the
+// group are moved cooperatively, thread t taking line t % kLongWarps of rows
+// t / kLongWarps + 32 m, so that a warp's access covers 8 rows of 4 adjacent
+// lines (32-byte runs for FP64); the halo rows of the neighbouring segments
+// are read the same way.  Then as for x-lines: double-float end rows spread
+// over the CTA, x~ of every (line, boundary) by one lane, each warp's
+// segment solve, results out through the slots.
+template <int R, int MODE, typename TIn, typename TOut, bool SW1 = false>
+__device__ __forceinline__ void long_warp_item_yz(const LongArgs& a, const DevLineTables& tin, const LongWarpArgs& wa,
+                                                  const int s, const int64_t line0, unsigned char* smem) {
+  constexpr int W = kLongWarps, ND = kNdotYZ<R>, TPD = kTpdYZ<R>;
+  static_assert(W == 4, "cooperative moves: 8 rows x 4 lines per warp access");
+  const int K = a.K;
+  TIn* Hp = reinterpret_cast<TIn*>(smem + lw_off_halo());  // [W][K]
+  TIn* Hn = Hp + W * K;
+  float2* Pp = reinterpret_cast<float2*>(smem + lwyz_off_part<R>(K, (int)sizeof(TIn)));
+  double* Bt = reinterpret_cast<double*>(Pp + ND * TPD);  // [W][2][R]
+  double* Xt = Bt + W * 2 * R;                            // [W][2][R]
+  double* CF = Xt + W * 2 * R;                            // [W][R]
+  double* CL = CF + W * R;                                // [W][R]
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  auto slots = [&](int k) { return reinterpret_cast<TIn*>(smem + (size_t)k * kSlotsPerWarp * 8); };
+  const LongGeom& gm = wa.gm;
+  const int64_t es = gm.es;
+
+  const int N = seg_rows(a, s) - R;
+  const int64_t s0 = seg_start(a, s);
+  const int64_t s1 = s + 1 == a.p ? 0 : s0 + N + R;  // the next segment (cyclic)
+  const int64_t pe = (s0 == 0 ? a.n : s0) - 1;       // last bulk row of the previous one
+  // A: this thread's line of the group and its rows
+  {
+    const int g = t & (W - 1), r0 = t >> 2;
+    const int64_t line = line0 + g;
+    if (line < a.lines) {
+      const TIn* b = (const TIn*)a.in + long_base(a, gm, line);
+      TIn* S = slots(g);
+#pragma unroll 4
+      for (int m = 0; m < kWarpM; m++) {
+        const int j = r0 + 32 * m;
+        if (j < N) S[(j & 15) * kSlot + (j >> 4)] = __ldg(b + (s0 + R + j) * es);
+      }
+      for (int j = r0; j < K; j += 32) {
+        Hp[g * K + j] = __ldg(b + (pe - j) * es);
+        Hn[g * K + j] = __ldg(b + (s1 + R + j) * es);
+      }
+      if (r0 < R) {
+        Bt[(g * 2 + 0) * R + r0] = (double)__ldg(b + (s0 + r0) * es);
+        Bt[(g * 2 + 1) * R + r0] = (double)__ldg(b + (s1 + r0) * es);
+      }
+    }
+  }
+  __syncthreads();
+
+  // B: the four end rows of y of every line (double-float dot products)
+  {
+    const int d = t / TPD, part = t % TPD;
+    const int g = d / (4 * R), e = d % (4 * R);
+    if (d < ND && line0 + g < a.lines) {
+      const int kind = e / R, q = e % R;  // 0: y_{s-1} last, 1: y_s first, 2: y_s last, 3: y_{s+1} first
+      const bool last = kind == 0 || kind == 2;
+      const int grow = last ? R - 1 - q : q;
+      const float* Gh = wa.Gh + grow * K;
+      const float* Gl = wa.Gl + grow * K;
+      const TIn* S = slots(g);
+      float ah = 0.f, al = 0.f;
+      for (int j = part; j < K; j += TPD) {
+        TIn b;
+        if (kind == 0) b = Hp[g * K + j];
+        else if (kind == 3) b = Hn[g * K + j];
+        else {
+          const int row = kind == 1 ? j : N - 1 - j;
+          b = S[(row & 15) * kSlot + (row >> 4)];
+        }
+        df_madd(ah, al, __ldg(Gh + j), __ldg(Gl + j), b);
+      }
+      Pp[d * TPD + part] = make_float2(ah, al);
+    }
+  }
+  __syncthreads();
+
+  // C: one lane per (line, boundary): x~ = D-hat^{-1} (b~ - L~ y_left - U~
+  // y_right) (Eq. 21, the decoupled outer system) and the Eq. 9 couplings
+  if (w == 0 && lane < 2 * W && line0 + (lane >> 1) < a.lines) {
+    const int g = lane >> 1, bd = lane & 1;
+    double y[2 * R];
+#pragma unroll
+    for (int e = 0; e < 2 * R; e++) {
+      float h = 0.f, l = 0.f;
+      const int d = g * 4 * R + bd * 2 * R + e;
+      for (int q = 0; q < TPD; q++) {
+        const float2 v = Pp[d * TPD + q];
+        const f2 u = two_sum(h, v.x);
+        h = u.hi;
+        l += u.lo + v.y;
+      }
+      y[e] = f32_to_f64(h) + f32_to_f64(l);
+    }
+    double bh[R], xt[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      double v = Bt[(g * 2 + bd) * R + q];
+#pragma unroll
+      for (int e = 0; e < R; e++) v -= wa.Lt[q * R + e] * y[e] + wa.Ut[q * R + e] * y[R + e];
+      bh[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      double v = 0.0;
+#pragma unroll
+      for (int e = 0; e < R; e++) v += wa.Dinv[q * R + e] * bh[e];
+      xt[q] = v;
+      Xt[(g * 2 + bd) * R + q] = v;
+    }
+    // boundary s: the segment's first bulk rows (offset q - R - j); boundary
+    // s + 1: its last bulk rows (offset q + R - j)
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      double c = 0.0;
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        if (bd == 0 && q >= j) c += a.band[q - j] * xt[q];
+        if (bd == 1 && q <= j) c += a.band[q - j + 2 * R] * xt[q];
+      }
+      (bd == 0 ? CF : CL)[g * R + j] = c;
+    }
+  }
+  __syncthreads();
+
+  // D: each warp's segment
+  bool bad = false;
+  if (line0 + w < a.lines) bad = lw_segment_solve<R, MODE, TIn, TOut, SW1>(slots(w), CF + w * R, CL + w * R, lane, a, tin, wa);
+  if (__any_sync(kFull, bad) && lane == 0 && wa.status) atomicExch(wa.status, (int)CBS_ERR_RANGE);
+  __syncthreads();  // the results of every warp, out cooperatively
+  {
+    const int g = t & (W - 1), r0 = t >> 2;
+    const int64_t line = line0 + g;
+    if (line < a.lines) {
+      TOut* x = (TOut*)a.out + long_base(a, gm, line);
+      const TOut* O = reinterpret_cast<const TOut*>(slots(g));
+#pragma unroll 4
+      for (int m = 0; m < kWarpM; m++) {
+        const int j = r0 + 32 * m;
+        if (j < N) x[(s0 + R + j) * es] = O[(j & 15) * kSlot + (j >> 4)];
+      }
+      if (r0 < R) x[(s0 + r0) * es] = (TOut)Xt[(g * 2 + 0) * R + r0];  // the segment's interface rows
+    }
   }
 }
 

@@ -69,6 +69,7 @@ cbs_status set_error(cbs_status s, const std::string& msg);
 void set_launch_count(int n);
 // inner_small: tables of the msmall-row segments (whole-16-row layout), or
 // null when every segment uses `inner`.
+bool long_warp_fits(int R, int K, int in_size, bool yz);
 cudaError_t launch_long_warp(int mode, int R, bool in64, bool out64, const LongArgs& a, const DevLineTables& inner,
                              const DevLineTables* inner_small, const LongWarpArgs& wa, const LwIface* ifc,
                              cudaStream_t s, int* launches);

@@ -123,3 +123,48 @@ def test_config3_full_size_sampled(cuda):
     for l in (0, 13, 31):
         ref = oracle.solve_cyclic(oracle.toeplitz_bands(n, W.PENTA10["lhs"]), d[l:l + 1].astype(np.float64))
         assert oracle.rel_err(x[0, l].cpu().numpy(), ref[0]) < 1e-12
+
+
+def _yz_field(direction, n, a, b, seed, f32=False):
+    shape = [(a, b, n), (a, n, b), (n, a, b)][direction]
+    d = np.random.default_rng(seed).standard_normal(shape)
+    return d.astype(np.float32).astype(np.float64) if f32 else d
+
+
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp64", "fp32"])
+@pytest.mark.parametrize("scheme", ["tri6", "penta10"])
+@pytest.mark.parametrize("direction", [1, 2])
+def test_yz_lines_warp_per_segment(cuda, direction, scheme, precision):
+    # y/z lines of 8192: a CTA per (segment, group of 4 lines adjacent in x);
+    # 7 x 3 lines: groups that end mid-row and a ragged last group
+    d = _yz_field(direction, 8192, 3, 7, 40 + direction, f32=precision == "fp32")
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    lhs = LHS[scheme]
+    plan = Plan(d.shape, direction, lhs=lhs, rhs=None, precision=precision, sweeps=1, in_dtype=dt)
+    info = plan.info()
+    y = plan.solve(torch.from_numpy(d).to("cuda", dt))
+    torch.cuda.synchronize()
+    st = plan.status()
+    plan.close()
+    assert info["segment_warp"] == 1 and info["segments"] == 16 and st == 0
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(8192, lhs), d, axis=2 - direction)
+    assert oracle.rel_err(y.double().cpu().numpy(), ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("direction", [1, 2])
+def test_yz_agrees_with_three_launch_path(cuda, direction):
+    # 2^16-point lines (both segment sizes), FP32 right-hand side, 5 x 2 lines
+    d = _yz_field(direction, 1 << 16, 2, 5, 77 + direction, f32=True)
+    ref = oracle.solve_cyclic(oracle.toeplitz_bands(1 << 16, LHS["penta10"]), d, axis=2 - direction)
+    outs = []
+    for variant in (0, 1):
+        plan = Plan(d.shape, direction, lhs=LHS["penta10"], rhs=None, precision="fp32_refine", sweeps=2,
+                    in_dtype=torch.float32)
+        abi.cbs_plan_set_variant(plan.handle, variant, 0)
+        assert plan.info()["segment_warp"] == 1 - variant
+        y = plan.solve(torch.from_numpy(d).to("cuda", torch.float32))
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        plan.close()
+        outs.append(y.cpu().numpy())
+    assert oracle.rel_err(outs[0], ref) < 1e-12 and oracle.rel_err(outs[1], ref) < 1e-12
