@@ -349,8 +349,9 @@ cbs_status cbs_batch_status_poll(cbs_batch* batch, int32_t* device_status);
  * The first call on a device looks up the array's device address (with that
  * device current), so make it before any stream capture.  All calls share
  * the array: calls whose launches may overlap on the GPU race with each
- * other, so order them (one stream, or events).  in / out / stream as for
- * cbs_solve. */
+ * other, so order them (one stream, or events).  Plans that run a warp per
+ * segment (cbs_plan_info.segment_warp = 1) use no scratch: the call then
+ * runs that path for any plan size.  in / out / stream as for cbs_solve. */
 cbs_status cbs_solve_noalloc(cbs_plan* plan, const void* in, void* out, void* stream);
 
 /* Measurement support for rooflines (not part of the method): the current
