@@ -544,7 +544,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2101_02286_gb300 import workloads as W
-    from paper_2101_02286_gb300.solver import Plan
+    from paper_2101_02286_gb300.solver import Pipe, Plan
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -656,54 +656,32 @@ def main():
                 e = max(e, oracle.rel_err(got, ref))
             err[prec] = e
 
-    # end to end through the public API: every step uploads the field from
-    # pinned host memory, runs the three solves and reads the three results
-    # back into pinned host memory.  Uploads, solves and downloads run on three
-    # streams with two device buffers each, so step k+1's upload and step k's
-    # downloads overlap the solves (as a user streaming fields would run them).
+    # end to end through the C-ABI with host buffers (cbs_pipe_solve): every
+    # step uploads the field from pinned host memory, runs the three solves and
+    # reads the three results back into pinned host memory, all inside the
+    # call; the pipe alternates two sets of device buffers, so step k+1's
+    # upload overlaps step k's downloads on the other copy engine.
     out_pin = [torch.empty(f.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
-    f_dev = [f, torch.empty_like(f)]
-    o_dev = [outs, [torch.empty_like(f) for _ in range(3)]]
-    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    pipe = Pipe([plans["fp32_refine"][d] for d in range(3)])
     e2e_steps = max(4, args.steps // 2)
 
-    def e2e_run(ps, steps):
-        free_in = [None, None]    # solves that read f_dev[b] are done
-        free_out = [None, None]   # downloads of o_dev[b] are done
-        for k in range(steps):
-            b = k % 2
-            with torch.cuda.stream(s_up):
-                if free_in[b] is not None:
-                    s_up.wait_event(free_in[b])
-                f_dev[b].copy_(f_pin, non_blocking=True)
-                up = torch.cuda.Event()
-                up.record(s_up)
-            stream.wait_event(up)
-            if free_out[b] is not None:
-                stream.wait_event(free_out[b])
-            solved = []
-            for d in range(3):
-                ps[d].solve(f_dev[b], o_dev[b][d], stream)
-                ev = torch.cuda.Event()
-                ev.record(stream)
-                solved.append(ev)
-            free_in[b] = solved[-1]
-            with torch.cuda.stream(s_down):
-                for d in range(3):
-                    s_down.wait_event(solved[d])
-                    out_pin[d].copy_(o_dev[b][d], non_blocking=True)
-                down = torch.cuda.Event()
-                down.record(s_down)
-            free_out[b] = down
+    def e2e_run(steps):
+        for _ in range(steps):
+            pipe.solve(f_pin, out_pin, stream)
+        stream.synchronize()
 
-    e2e_run(plans["fp32_refine"], 2)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_run(plans["fp32_refine"], e2e_steps)
-    barrier()
-    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
-    e2e_ms = max_over_ranks(e2e_ms, dev)
-    del f_dev, o_dev
+    e2e_run(4)
+    # three timed windows; the host link of a shared box shows bursts of
+    # contention, so the median window is reported (all three are listed)
+    e2e_windows = []
+    for _ in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        e2e_run(e2e_steps)
+        barrier()
+        e2e_windows.append(max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, dev))
+    e2e_ms = sorted(e2e_windows)[1]
+    pipe.close()
 
     if rank == 0:
         peaks = {}
@@ -771,8 +749,9 @@ def main():
             "speedup_refine_vs_fp64": ms_64 / ms_ref,
             "e2e": {"value": job_throughput(units, world, e2e_ms), "unit": "Gunknowns/s",
                     "h2d_bytes_per_step": 8 * n ** 3, "d2h_bytes_per_step": 3 * 8 * n ** 3,
-                    "ms_per_step": e2e_ms, "steps": e2e_steps,
-                    "overlap": "upload, solves and downloads on three streams, two device buffers"},
+                    "ms_per_step": e2e_ms, "steps": e2e_steps, "window_ms": e2e_windows,
+                    "api": "cbs_pipe_solve (C-ABI, pinned host buffers, copies inside the call)",
+                    "overlap": "upload, solves and downloads on three streams, two device buffer sets"},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "cpu_baseline": {"value": cpu_v, "unit": "Gunknowns/s", "cores": cores, "kind": "oracle",

@@ -354,6 +354,27 @@ cbs_status cbs_batch_status_poll(cbs_batch* batch, int32_t* device_status);
  * runs that path for any plan size.  in / out / stream as for cbs_solve. */
 cbs_status cbs_solve_noalloc(cbs_plan* plan, const void* in, void* out, void* stream);
 
+/* Solves from host memory.  A pipe holds plans that read the same field
+ * (same dims and input type: say the x, y and z derivatives of one field)
+ * and, on the device, two input buffers and two output buffers per plan,
+ * allocated by cbs_pipe_create (count 1..64; NO_MEMORY / CUDA on failure);
+ * cbs_pipe_solve allocates nothing.  Each call copies host_in (the field,
+ * host memory; page-locked for the copies to run asynchronously) to the
+ * device on an internal upload stream, runs every plan's solve on `stream`,
+ * and copies result k to host_outs[k] (host arrays of each plan's output
+ * size and type) on an internal download stream as soon as solve k is done;
+ * `stream` then waits for the downloads, so work issued on it after the call
+ * -- or a synchronize of it -- sees the results in host memory.  Successive
+ * calls alternate the device buffers: the upload of one call overlaps the
+ * downloads of the previous one.  Call with the device current that the
+ * pipe was created on.  Host buffers must stay valid until `stream` passes
+ * the call.  The paper has no counterpart (its data live on the device). */
+typedef struct cbs_pipe cbs_pipe;
+cbs_status cbs_pipe_create(cbs_pipe** out, cbs_plan* const* plans, int32_t count);
+cbs_status cbs_pipe_solve(cbs_pipe* pipe, const void* host_in, void* const* host_outs, void* stream);
+/* Synchronises the device, then frees the pipe's buffers (not its plans). */
+cbs_status cbs_pipe_destroy(cbs_pipe* pipe);
+
 /* Measurement support for rooflines (not part of the method): the current
  * device's FP64 fused multiply-add throughput, timed with CUDA events on a
  * register-resident kernel of independent fma chains (4 CTAs of 256

@@ -30,7 +30,8 @@ EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transp
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
            "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
            "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune",
-           "cbs_plan_set_variant", "cbs_plan_inject_fault", "cbs_probe_fp64_peak")
+           "cbs_plan_set_variant", "cbs_plan_inject_fault", "cbs_probe_fp64_peak", "cbs_pipe_create",
+           "cbs_pipe_solve", "cbs_pipe_destroy")
 
 
 class CbsError(RuntimeError):
@@ -110,6 +111,9 @@ def _load():
         "cbs_plan_set_variant": ([vp, i32, i32], st),
         "cbs_plan_inject_fault": ([vp, i32], st),
         "cbs_probe_fp64_peak": ([P(ctypes.c_double)], st),
+        "cbs_pipe_create": ([P(vp), P(vp), i32], st),
+        "cbs_pipe_solve": ([vp, vp, P(vp), vp], st),
+        "cbs_pipe_destroy": ([vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -225,6 +229,22 @@ def cbs_batch_create(descs: list[cbs_desc]) -> int:
     h = ctypes.c_void_p()
     _check(_lib.cbs_batch_create(ctypes.byref(h), arr, len(descs)))
     return h.value
+
+
+def cbs_pipe_create(plans: list[int]) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = ctypes.c_void_p()
+    _check(_lib.cbs_pipe_create(ctypes.byref(h), arr, len(plans)))
+    return h.value
+
+
+def cbs_pipe_solve(pipe: int, host_in: int, host_outs: list[int], stream: int = 0) -> None:
+    outs = (ctypes.c_void_p * len(host_outs))(*host_outs)
+    _check(_lib.cbs_pipe_solve(pipe, host_in, outs, stream))
+
+
+def cbs_pipe_destroy(pipe: int) -> None:
+    _check(_lib.cbs_pipe_destroy(pipe))
 
 
 def cbs_batch_destroy(batch: int) -> None:

@@ -168,3 +168,37 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Pipe:
+    """Plans over one field, solved from host memory (cbs_pipe_*): each
+    solve() uploads the field, runs every plan and downloads every result
+    inside the call; `stream` then covers the downloads.  Host tensors should
+    be pinned (torch.empty(..., pin_memory=True))."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.handle = abi.cbs_pipe_create([p.handle for p in self.plans])
+
+    def solve(self, host_in: torch.Tensor, host_outs, stream: torch.cuda.Stream | None = None):
+        for p, y in zip(self.plans, host_outs):
+            if y.device.type != "cpu" or y.shape != p.shape or y.dtype != p.out_dtype or not y.is_contiguous():
+                raise ValueError("host outputs: contiguous CPU tensors of each plan's shape and output type")
+        p0 = self.plans[0]
+        if host_in.device.type != "cpu" or host_in.shape != p0.shape or host_in.dtype != p0.in_dtype \
+                or not host_in.is_contiguous():
+            raise ValueError("host input: a contiguous CPU tensor of the plans' shape and input type")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        abi.cbs_pipe_solve(self.handle, host_in.data_ptr(), [y.data_ptr() for y in host_outs], s.cuda_stream)
+        return host_outs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.cbs_pipe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
