@@ -339,18 +339,16 @@ cbs_status cbs_batch_status_poll(cbs_batch* batch, int32_t* device_status);
 
 /* Allocation-free variant of cbs_solve for long-line plans (cbs_plan_info
  * kernel == 1).  The paper has no counterpart: this serves callers that must
- * not call cudaMalloc when they solve -- code running while a stream capture
- * is active (allocation is refused then), applications that hand all device
+ * not call cudaMalloc when they solve -- applications that hand all device
  * memory to their own allocator at start-up, and loops with a fixed memory
  * footprint.  The solve's scratch (5 r doubles per segment of every line) is
  * one fixed 4 MiB array inside the library's device image instead of the
  * plan's buffer; lines x segments x 5 r above 524288 is rejected with
- * CBS_ERR_INVALID_ARG.  No cudaMalloc / cudaFree or other allocating call.
- * The first call on a device looks up the array's device address (with that
- * device current), so make it before any stream capture.  All calls share
- * the array: calls whose launches may overlap on the GPU race with each
- * other, so order them (one stream, or events).  Plans that run a warp per
- * segment (cbs_plan_info.segment_warp = 1) use no scratch: the call then
+ * CBS_ERR_INVALID_ARG.  No cudaMalloc / cudaFree or other allocating call;
+ * each call looks up the array's address in the current context.  All calls
+ * share the array: calls whose launches may overlap on the GPU race with
+ * each other, so order them (one stream, or events).  Plans that run a warp
+ * per segment (cbs_plan_info.segment_warp = 1) use no scratch: the call then
  * runs that path for any plan size.  in / out / stream as for cbs_solve. */
 cbs_status cbs_solve_noalloc(cbs_plan* plan, const void* in, void* out, void* stream);
 

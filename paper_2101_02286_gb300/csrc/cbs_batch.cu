@@ -171,13 +171,8 @@ int batch_variant_host(int R, int KS, int M, int MODE, bool full) { return batch
 size_t batch_smem(size_t tile_bytes) { return kBatchProblemBytes + tile_bytes; }
 
 cudaError_t batch_configure(size_t smem) {
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  return cudaSuccess;
+  static SmemOptIn opt;
+  return opt.ensure(batch_kernel, smem);
 }
 
 cudaError_t batch_launch(const BatchProblem* probs, const int4* items, int nitems, const void* const* ins,

@@ -8,18 +8,68 @@ namespace cbs {
 
 constexpr int kLineThreads = 256;
 
-// Streaming multiprocessors of the current device (cached per process).
+constexpr int kMaxDevices = 64;
+
+// Streaming multiprocessors of the current device (cached per device).
 inline int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      n = v;
-    else
-      return 152;
+  static int n[kMaxDevices] = {};
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 152;
+  if (n[dev] == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 152;
+    n[dev] = v;
   }
-  return n;
+  return n[dev];
 }
+
+// Opt-in to more than 48 KB of dynamic shared memory for one kernel: the
+// attribute belongs to the device, so the largest size set so far is kept
+// per device (one instance per kernel, a static at the call site).
+struct SmemOptIn {
+  std::mutex mu;
+  size_t done[kMaxDevices] = {};
+  template <typename K>
+  cudaError_t ensure(K kern, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done[dev] = smem;
+    return e;
+  }
+};
+
+// Resident blocks per SM of one kernel at the last (device, threads, shared
+// memory) it was launched with (one instance per kernel, a static at the
+// call site).
+struct OccupancyCache {
+  std::mutex mu;
+  size_t smem = 0;
+  int threads = 0, dev = -1, per_sm = 0;
+  template <typename K>
+  cudaError_t get(K kern, int nthreads, size_t nsmem, int* out) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev != d || smem != nsmem || threads != nthreads) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, nsmem);
+      if (e != cudaSuccess) {
+        dev = -1;
+        return e;
+      }
+      dev = d;
+      smem = nsmem;
+      threads = nthreads;
+    }
+    *out = per_sm;
+    return cudaSuccess;
+  }
+};
 
 // Launch grid of the tile kernels: x-lines are tiled along the line index;
 // y/z lines along x (grid.x) and the remaining coordinate (grid.y).
@@ -46,13 +96,9 @@ cudaError_t launch_one(const LineArgs& a, const DevLineTables& t, cudaStream_t s
   // staged: the tile; direct strided: the message buffer
   const size_t smem = LAYOUT == kStaged ? (size_t)lines_per_cta * t.lsz * sizeof(TT)
                       : LAYOUT == kDirectStrided ? (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) : 0;
-  static size_t configured = 0;  // per instantiation
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  static SmemOptIn opt;  // per instantiation
+  cudaError_t e = opt.ensure(line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT, ST>, smem);
+  if (e != cudaSuccess) return e;
   line_kernel<R, M, MODE, KS, TIn, TOut, FULL, LAYOUT, ST><<<grid, threads, smem, s>>>(a, t);
   return cudaGetLastError();
 }
@@ -72,29 +118,15 @@ cudaError_t launch_pipe(const LineArgs& a, const DevLineTables& t, cudaStream_t 
                       2 * (size_t)pipe_buf_elems<M, KS, TIn, LAYOUT>(threads, t.pw, t.p) * sizeof(TIn);
   (void)NS;
   auto kern = line_kernel_pipe<R, M, MODE, KS, TIn, TOut, LAYOUT, ST>;
-  // per instantiation: the largest dynamic shared memory configured so far
-  // and the occupancy of the last (threads, smem) launched (both depend on
-  // the plan's lanes per line, not only on the instantiation)
-  static std::mutex mu;
-  static size_t attr_smem = 0, occ_smem = 0;
-  static int occ_threads = 0, per_sm = 0;
+  // per instantiation: the shared-memory opt-in and the occupancy (both
+  // depend on the plan's lanes per line, not only on the instantiation)
+  static SmemOptIn opt;
+  cudaError_t e = opt.ensure(kern, smem);
+  if (e != cudaSuccess) return e;
+  static OccupancyCache occ;
   int blocks_per_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024 && smem > attr_smem) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr_smem = smem;
-    }
-    if (occ_smem != smem || occ_threads != threads) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-      if (e != cudaSuccess) return e;
-      occ_smem = smem;
-      occ_threads = threads;
-    }
-    blocks_per_sm = per_sm;
-  }
+  e = occ.get(kern, threads, smem, &blocks_per_sm);
+  if (e != cudaSuccess) return e;
   if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
   const int per_sm_now = blocks_per_sm;
   const int64_t want = (int64_t)per_sm_now * sm_count();

@@ -391,28 +391,14 @@ cudaError_t launch_seg_pipe(const LongArgs& a, const DevLineTables& tin, int seg
   if (items > 0x7fffffff || threads > 256) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kCtaXchgSlots * threads * sizeof(unsigned long long) + 2 * (size_t)M * threads * sizeof(TIn);
   auto kern = long_seg_pipe_kernel<R, M, MODE, TIn, TOut, FULL, LG>;
-  // per instantiation: largest dynamic shared memory configured, and the
-  // occupancy of the last (threads, smem) launched
-  static std::mutex mu;
-  static size_t attr_smem = 0, occ_smem = 0;
-  static int occ_threads = 0, per_sm = 0;
+  // per instantiation: the shared-memory opt-in and the occupancy
+  static SmemOptIn opt;
+  cudaError_t e = opt.ensure(kern, smem);
+  if (e != cudaSuccess) return e;
+  static OccupancyCache occ;
   int blocks_per_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    cudaError_t e;
-    if (smem > 48 * 1024 && smem > attr_smem) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr_smem = smem;
-    }
-    if (occ_smem != smem || occ_threads != threads) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-      if (e != cudaSuccess) return e;
-      occ_smem = smem;
-      occ_threads = threads;
-    }
-    blocks_per_sm = per_sm;
-  }
+  e = occ.get(kern, threads, smem, &blocks_per_sm);
+  if (e != cudaSuccess) return e;
   if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t want = (int64_t)blocks_per_sm * sm_count();
   const unsigned blocks = (unsigned)(items < want ? items : want);
@@ -460,18 +446,12 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
   if (e != cudaSuccess) return e;
   const int ithreads = a.p < 1024 ? ((a.p + 31) / 32) * 32 : 1024;
   const size_t ismem = 2 * (size_t)a.p * a.r * sizeof(double);
-  static std::mutex imu;
-  static size_t iconf = 0;
-  if (ismem > 48 * 1024) {
-    std::lock_guard<std::mutex> lock(imu);
-    if (ismem > iconf) {
-      const void* ks[4] = {(const void*)long_iface_kernel<double, false>, (const void*)long_iface_kernel<float, false>,
-                           (const void*)long_iface_kernel<double, true>, (const void*)long_iface_kernel<float, true>};
-      for (int k = 0; k < 4 && e == cudaSuccess; k++)
-        e = cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-      if (e != cudaSuccess) return e;
-      iconf = ismem;
-    }
+  {
+    static SmemOptIn opt[4];  // one per interface kernel
+    const void* ks[4] = {(const void*)long_iface_kernel<double, false>, (const void*)long_iface_kernel<float, false>,
+                         (const void*)long_iface_kernel<double, true>, (const void*)long_iface_kernel<float, true>};
+    for (int k = 0; k < 4 && e == cudaSuccess; k++) e = opt[k].ensure(ks[k], ismem);
+    if (e != cudaSuccess) return e;
   }
   const unsigned nl = (unsigned)a.lines;
   if (tiled) {
@@ -541,24 +521,23 @@ cudaError_t launch_long(int mode, int R, bool in64, bool out64, const LongArgs& 
 // ---------------------------------------------------------------- no-alloc entry
 // Long-line solve whose per-solve scratch (yb, cc, xt) is one library-wide
 // array in the device image instead of the plan's own buffer.  It exists for
-// callers that must not call cudaMalloc when they solve: code running while
-// a stream capture is active (allocation is refused then), applications that
+// callers that must not call cudaMalloc when they solve: applications that
 // hand all device memory to their own allocator at start-up, and loops with a
-// fixed memory footprint where a late allocation could fail.
+// fixed memory footprint where a late allocation could fail.  Plans that run
+// a warp per segment need no scratch at all.
 //
 // The array is a host-side stand-in in host code: the device address comes
-// from cudaGetSymbolAddress, fetched once per device (with that device
-// current) by the first call made on it.  Every call shares the array and
-// the previous call's contents stay in it; nothing needs to start at zero
-// because every slot is written before it is read within a solve.  Calls
-// whose launches overlap on the GPU (different streams, or the same plan from
-// several host threads without ordering) race on the array.
+// from cudaGetSymbolAddress in the current context, on every call.  Every
+// call shares the array and the previous call's contents stay in it; nothing
+// needs to start at zero because every slot is written before it is read
+// within a solve.  Calls whose launches overlap on the GPU (different
+// streams, or the same plan from several host threads without ordering) race
+// on the array.
 }  // namespace cbs
 
 namespace {
 
 constexpr size_t kNoAllocScratchDoubles = (size_t)1 << 19;  // 4 MiB
-constexpr int kNoAllocMaxDevices = 64;
 
 }  // namespace
 
@@ -566,24 +545,15 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 
 namespace {
 
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the array on the current device (set-up on first use).
+// Device address of the array in the current context.  Looked up on every
+// call rather than cached: after a device reset the new context maps the
+// array at a new address.
 cbs_status noalloc_scratch(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cbs::set_error(CBS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return cbs::set_error(CBS_ERR_UNSUPPORTED, "device index above 63");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      return cbs::set_error(CBS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess)
+    return cbs::set_error(CBS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+  *out = static_cast<double*>(p);
   return CBS_OK;
 }
 

@@ -12,13 +12,9 @@ static cudaError_t launch_var_one(const VarArgs& a, const DevLineTables& t, cuda
   if (a.nlines <= 0) return cudaSuccess;
   const dim3 grid = tile_grid(a.nx, a.ny, a.nz, a.nlines, a.dir, lines_per_cta);
   const size_t smem = 3 * (size_t)lines_per_cta * t.lsz * sizeof(TG);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(var_kernel<M, KS, ADJ, T, TG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  static SmemOptIn opt;  // per instantiation
+  cudaError_t e = opt.ensure(var_kernel<M, KS, ADJ, T, TG>, smem);
+  if (e != cudaSuccess) return e;
   var_kernel<M, KS, ADJ, T, TG><<<grid, threads, smem, s>>>(a, t);
   return cudaGetLastError();
 }

@@ -1,8 +1,7 @@
 """The allocation-free long-line entry point (cbs_solve_noalloc).
 
 It is meant for callers that cannot allocate device memory while they solve
-(inside a stream capture, under an application-owned allocator, with a fixed
-memory footprint): it runs the same kernels as cbs_solve on a fixed scratch
+(under an application-owned allocator, with a fixed memory footprint): it runs the same kernels as cbs_solve on a fixed scratch
 array in the library instead of the plan's buffer.  Checked through the
 C-ABI against cbs_solve on two calls in a row, plus the size limit.  This
 file is collected last on purpose.
@@ -62,3 +61,29 @@ def test_noalloc_rejects_oversize_and_on_chip_plans(cuda):
         abi.cbs_solve_noalloc(small.handle, a.data_ptr(), torch.empty_like(a).data_ptr(), 0)
     assert e.value.status == abi.CBS_ERR_UNSUPPORTED
     small.close()
+
+
+@pytest.mark.parametrize("dims,direction,lhs", [
+    ((1, 3, 8191), 0, W.PENTA10["lhs"]),   # 8191 = 16 x 511 + 15: two segment sizes
+    ((2, 8191, 4), 1, W.LELE6_TRI["lhs"]),  # y-lines, strided
+])
+def test_noalloc_ragged_segments(cuda, dims, direction, lhs):
+    # the three-launch path on the fixed scratch with segments of two sizes
+    # (the last one shorter), FP64 in and out, against the oracle directly
+    plan = Plan(dims, direction, lhs=lhs, rhs=None, segments=16, precision="fp64")
+    abi.cbs_plan_set_variant(plan.handle, 1, 0)
+    assert plan.info()["kernel"] == 1 and plan.info()["segment_warp"] == 0
+    rng = np.random.default_rng(77)
+    axis = 2 - direction
+    n = dims[axis]
+    for call in range(2):
+        d = rng.standard_normal(dims)
+        x = torch.from_numpy(d).cuda()
+        out = torch.full_like(x, float("nan"))
+        abi.cbs_solve_noalloc(plan.handle, x.data_ptr(), out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        exact = oracle.solve_cyclic(oracle.toeplitz_bands(n, lhs), d, axis=axis)
+        assert oracle.rel_err(got, exact) < 1e-12, call
+    plan.close()
