@@ -65,21 +65,30 @@ __host__ __device__ constexpr int batch_f32_variant(int R, int KS, int M) {
   return (rk < 0 || mi < 0) ? -1 : kBatchF32 + rk * 2 + mi;
 }
 
-#define CBS_BV32(R, KS, M)                                                                       \
-  case batch_f32_variant(R, KS, M):                                                              \
-    line_tile<R, M, kModeF32, KS, float, float>(P.args, P.tab, bp.in[P.user], bp.out[P.user], w.y, w.z, \
-                                                tile_smem);                                      \
+// One tile of an on-chip problem.  A separate function per variant (not
+// inlined), so that each variant's register allocation stays its own instead
+// of the largest one's pressure spilling in all of them.
+template <int R, int M, int MODE, int KS, typename T, bool FULL>
+__device__ __noinline__ void batch_tile_item(const BatchProblem& P, const void* in, void* out, int tx, int ty,
+                                             unsigned char* smem) {
+  line_tile<R, M, MODE, KS, T, T, FULL>(P.args, P.tab, in, out, tx, ty, smem);
+}
+
+#define CBS_BV32(R, KS, M)                                                                        \
+  case batch_f32_variant(R, KS, M):                                                               \
+    batch_tile_item<R, M, kModeF32, KS, float, false>(P, bp.in[P.user], bp.out[P.user], w.y, w.z, \
+                                                      tile_smem);                                 \
     break;
 
-#define CBS_BV(R, KS, M, MODE)                                                                   \
-  case batch_variant(R, KS, M, MODE):                                                            \
-    line_tile<R, M, MODE, KS, double, double>(P.args, P.tab, bp.in[P.user], bp.out[P.user], w.y, w.z, \
-                                              tile_smem);                                        \
+#define CBS_BV(R, KS, M, MODE)                                                                  \
+  case batch_variant(R, KS, M, MODE):                                                           \
+    batch_tile_item<R, M, MODE, KS, double, false>(P, bp.in[P.user], bp.out[P.user], w.y, w.z, \
+                                                   tile_smem);                                  \
     break;
-#define CBS_BVF(R, KS, MODE)                                                                               \
-  case batch_variant(R, KS, 16, MODE, true):                                                               \
-    line_tile<R, 16, MODE, KS, double, double, true>(P.args, P.tab, bp.in[P.user], bp.out[P.user], w.y, w.z, \
-                                                     tile_smem);                                           \
+#define CBS_BVF(R, KS, MODE)                                                                   \
+  case batch_variant(R, KS, 16, MODE, true):                                                   \
+    batch_tile_item<R, 16, MODE, KS, double, true>(P, bp.in[P.user], bp.out[P.user], w.y, w.z, \
+                                                   tile_smem);                                 \
     break;
 
 // Long-line entry: item (entry, chunk, line); the chunk's kLongWarps
