@@ -316,40 +316,46 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
         pl.close()
     del di, do, d
 
-    # ragged batch: 48 grids, one persistent launch replayed from a CUDA graph
+    # ragged batch: 48 grids replayed from a CUDA graph, in the default mode
+    # (each problem's own kernels, FP64 problems on a forked stream) and as
+    # one persistent launch
     items = W.ragged_batch()
-    b = Batch(batch_specs(items))
     ins = [torch.from_numpy(it.f).to(dev) for it in items]
-    outs = [torch.empty_like(x) for x in ins]
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(stream)
-    b.solve(ins, outs, side)
-    stream.wait_stream(side)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=side):
-        b.solve(ins, outs, side)
     unk = sum(int(np.prod(it.shape_zyx)) for it in items)
-    ms = time_ms(g.replay, stream, steps)
-    err = None
-    if check:
-        err = 0.0
-        for it, y in zip(items, outs):
-            ax = 2 - it.direction
-            sc = W.LELE6_TRI if it.scheme == "tri6" else W.PENTA10
-            nn = it.shape_zyx[ax]
-            fl = np.moveaxis(it.f, ax, -1)
-            other = fl.shape[:2]
-            idx = [(int(rng.integers(0, other[0])), int(rng.integers(0, other[1]))) for _ in range(4)]
-            sel = np.stack([fl[i, j] for i, j in idx])
-            ref = oracle.derivative(sel, sc["lhs"], sc["rhs"], W.grid_spacing(nn))
-            yl = np.moveaxis(y.cpu().numpy(), ax, -1)
-            err = max(err, oracle.rel_err(np.stack([yl[i, j] for i, j in idx]), ref))
-    res.append(_entry("ragged batch of 48 grids (sizes from {32..384} per axis, seed 3), mixed tri/penta, "
-                      "fp64/fp32_refine, one persistent launch under a CUDA graph", unk, ms, 16, hbm, err,
-                      problems=len(items), launches_per_step=abi.cbs_last_launch_count(), sampled_lines=4 * len(items)))
-    b.close()
-    del ins, outs, items, g
+    for mode, how in (("auto", "each problem's own kernels, FP64 problems on a second stream"),
+                      ("persistent", "one persistent launch")):
+        b = Batch(batch_specs(items), mode=mode)
+        outs = [torch.empty_like(x) for x in ins]
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        b.solve(ins, outs, side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            b.solve(ins, outs, side)
+        launches = abi.cbs_last_launch_count()
+        ms = time_ms(g.replay, stream, steps)
+        err = None
+        if check:
+            err = 0.0
+            for it, y in zip(items, outs):
+                ax = 2 - it.direction
+                sc = W.LELE6_TRI if it.scheme == "tri6" else W.PENTA10
+                nn = it.shape_zyx[ax]
+                fl = np.moveaxis(it.f, ax, -1)
+                other = fl.shape[:2]
+                idx = [(int(rng.integers(0, other[0])), int(rng.integers(0, other[1]))) for _ in range(4)]
+                sel = np.stack([fl[i, j] for i, j in idx])
+                ref = oracle.derivative(sel, sc["lhs"], sc["rhs"], W.grid_spacing(nn))
+                yl = np.moveaxis(y.cpu().numpy(), ax, -1)
+                err = max(err, oracle.rel_err(np.stack([yl[i, j] for i, j in idx]), ref))
+        res.append(_entry("ragged batch of 48 grids (sizes from {32..384} per axis, seed 3), mixed tri/penta, "
+                          "fp64/fp32_refine, %s, under a CUDA graph" % how, unk, ms, 16, hbm, err,
+                          problems=len(items), mode=mode, launches_per_step=launches, sampled_lines=4 * len(items)))
+        b.close()
+        del outs, g
+    del ins, items
 
     # the paper's single-GPU workload: 256^2 lines of 8192 along x, y and z
     # (fields 8192 x 256 x 256, 256 x 8192 x 256, 256 x 256 x 8192), cyclic

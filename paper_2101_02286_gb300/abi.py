@@ -21,6 +21,7 @@ CBS_FP64, CBS_FP32, CBS_FP32_REFINE, CBS_FP32_REFINE_I64 = 0, 1, 2, 3
 CBS_DTYPE_F64, CBS_DTYPE_F32 = 0, 1
 CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE = 0, 1
 CBS_RHS_NONE, CBS_RHS_CENTRAL, CBS_RHS_STAGGERED, CBS_RHS_MIDPOINT = 0, 1, 2, 3
+CBS_BATCH_AUTO, CBS_BATCH_PERSISTENT, CBS_BATCH_PER_PROBLEM = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA",
                 6: "NO_MEMORY", 7: "RANGE"}
@@ -28,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "SINGULAR", 4: "
 # every entry point declared in include/cbs.h
 EXPORTS = ("cbs_plan_create", "cbs_plan_destroy", "cbs_solve", "cbs_solve_transpose", "cbs_band_grad",
            "cbs_status_poll", "cbs_plan_info_get", "cbs_schedule", "cbs_batch_create", "cbs_batch_destroy",
-           "cbs_batch_solve", "cbs_batch_status_poll", "cbs_last_launch_count", "cbs_last_error_string",
+           "cbs_batch_solve", "cbs_batch_status_poll", "cbs_batch_set_mode", "cbs_last_launch_count", "cbs_last_error_string",
            "cbs_version", "cbs_interface_model", "cbs_plan_set_bands", "cbs_solve_noalloc", "cbs_autotune",
            "cbs_plan_set_variant", "cbs_plan_inject_fault", "cbs_probe_fp64_peak", "cbs_pipe_create",
            "cbs_pipe_solve", "cbs_pipe_destroy")
@@ -101,6 +102,7 @@ def _load():
         "cbs_batch_destroy": ([vp], st),
         "cbs_batch_solve": ([vp, P(vp), P(vp), vp], st),
         "cbs_batch_status_poll": ([vp, P(i32)], st),
+        "cbs_batch_set_mode": ([vp, i32], st),
         "cbs_last_launch_count": ([], i32),
         "cbs_last_error_string": ([], ctypes.c_char_p),
         "cbs_version": ([], i32),
@@ -256,6 +258,10 @@ def cbs_batch_solve(batch: int, ins: list[int], outs: list[int], stream: int = 0
     a = (ctypes.c_void_p * n)(*ins)
     b = (ctypes.c_void_p * n)(*outs)
     _check(_lib.cbs_batch_solve(batch, a, b, stream))
+
+
+def cbs_batch_set_mode(batch: int, mode: int) -> None:
+    _check(_lib.cbs_batch_set_mode(batch, mode))
 
 
 def cbs_batch_status_poll(batch: int) -> int:

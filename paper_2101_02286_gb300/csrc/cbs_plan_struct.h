@@ -26,6 +26,12 @@ struct cbs_batch {
   int nitems = 0, count = 0, grid = 1;
   size_t smem = 0;
   int64_t unknowns = 0;
+  int mode = 0;                   // cbs_batch_set_mode
+  int device = -1;                // device current at creation
+  std::vector<int> order_fp64;    // per-problem launches: FP64 problems, largest first
+  std::vector<int> order_other;   // the others, largest first
+  cudaStream_t side = nullptr;    // per-problem launches: the FP64 problems' stream
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 struct cbs_plan {

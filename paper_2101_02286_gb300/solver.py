@@ -133,19 +133,28 @@ class Plan:
 
 
 class Batch:
-    """A ragged batch of independent problems solved by one persistent launch.
+    """A ragged batch of independent problems solved together.
 
     specs: list of (shape_zyx, direction, kwargs for make_desc).  Toeplitz
     bands; precision "fp64" or "fp32_refine" with FP64 input and output, or
     "fp32" with FP32 input and output (in_dtype=torch.float32); long x-lines
-    whose plan runs a warp per segment.
+    whose plan runs a warp per segment.  mode: "auto", "persistent" (one
+    launch over a work table of line tiles) or "per_problem" (each problem's
+    own kernels, FP64 problems on a stream of their own).
     """
 
-    def __init__(self, specs):
+    MODES = {"auto": abi.CBS_BATCH_AUTO, "persistent": abi.CBS_BATCH_PERSISTENT,
+             "per_problem": abi.CBS_BATCH_PER_PROBLEM}
+
+    def __init__(self, specs, mode: str = "auto"):
         self.shapes = [tuple(int(v) for v in sh) for sh, _, _ in specs]
         self.dtypes = [kw.get("in_dtype", torch.float64) for _, _, kw in specs]
         descs = [make_desc(sh, d, **kw) for sh, d, kw in specs]
         self.handle = abi.cbs_batch_create(descs)
+        if mode not in self.MODES:
+            self.close()
+            raise ValueError("mode must be one of %s" % sorted(self.MODES))
+        abi.cbs_batch_set_mode(self.handle, self.MODES[mode])
 
     def solve(self, ins, outs=None, stream: torch.cuda.Stream | None = None):
         if outs is None:

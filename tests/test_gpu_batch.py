@@ -1,5 +1,6 @@
-"""GPU parity of the ragged batch (one persistent launch) and its CUDA-graph
-capture, against the FP64 oracle problem by problem."""
+"""GPU parity of the ragged batch, in both modes (one persistent launch; each
+problem's own launches with the FP64 problems on a forked stream), and its
+CUDA-graph capture, against the FP64 oracle problem by problem."""
 import numpy as np
 import pytest
 import torch
@@ -11,6 +12,12 @@ from paper_2101_02286_gb300.solver import Batch
 
 pytestmark = pytest.mark.gpu
 SCH = {"tri6": W.LELE6_TRI, "penta10": W.PENTA10}
+MODES = ["persistent", "per_problem"]
+
+
+def _launches_ok(mode, count):
+    n = abi.cbs_last_launch_count()
+    return n == 1 if mode == "persistent" else n >= count
 
 
 def _specs(items):
@@ -30,21 +37,23 @@ def _ref(it, f):
     return oracle.derivative(f, sch["lhs"], sch["rhs"], W.grid_spacing(n), axis=2 - it.direction)
 
 
-def test_ragged_batch_small(cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_ragged_batch_small(cuda, mode):
     items = W.ragged_batch(count=24, seed=123, sizes=(32, 48, 64, 96))
-    b = Batch(_specs(items))
+    b = Batch(_specs(items), mode=mode)
     ins = [torch.from_numpy(it.f).cuda() for it in items]
     outs = b.solve(ins)
-    assert abi.cbs_last_launch_count() == 1
+    assert _launches_ok(mode, len(items))
     torch.cuda.synchronize()
     for it, y in zip(items, outs):
         assert oracle.rel_err(y.cpu().numpy(), _ref(it, it.f)) < 1e-12, it
     b.close()
 
 
-def test_ragged_batch_cuda_graph(cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_ragged_batch_cuda_graph(cuda, mode):
     items = W.ragged_batch(count=16, seed=321, sizes=(32, 64, 128))
-    b = Batch(_specs(items))
+    b = Batch(_specs(items), mode=mode)
     ins = [torch.from_numpy(it.f).cuda() for it in items]
     outs = [torch.empty_like(x) for x in ins]
     s = torch.cuda.Stream()
@@ -78,10 +87,11 @@ def test_batch_rejects_unsupported(cuda):
 
 
 @pytest.mark.slow
-def test_ragged_batch_full_workload_sampled(cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_ragged_batch_full_workload_sampled(cuda, mode):
     # the 48-grid ragged batch (sizes up to 384 per axis), sampled lines
     items = W.ragged_batch()
-    b = Batch(_specs(items))
+    b = Batch(_specs(items), mode=mode)
     ins = [torch.from_numpy(it.f).cuda() for it in items]
     outs = b.solve(ins)
     torch.cuda.synchronize()
@@ -99,8 +109,9 @@ def test_ragged_batch_full_workload_sampled(cuda):
     b.close()
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-def test_batch_mixes_long_lines_with_grids(cuda, precision):
+def test_batch_mixes_long_lines_with_grids(cuda, precision, mode):
     # one persistent launch over on-chip grids (derivatives) and long x-lines
     # (right-hand side given, a warp per segment: 8192 = 16 segments in both
     # sizes, 9 x 513 = 4617: one CTA of 8 segments and one of 1), replayed
@@ -110,7 +121,7 @@ def test_batch_mixes_long_lines_with_grids(cuda, precision):
     longs = [((1, 5, 8192), W.PENTA10["lhs"]), ((1, 3, 4617), W.LELE6_TRI["lhs"])]
     for shape, lhs in longs:
         specs.append((shape, 0, dict(lhs=lhs, rhs=None, precision=precision, sweeps=1)))
-    b = Batch(specs)
+    b = Batch(specs, mode=mode)
     rng = np.random.default_rng(9)
     data = [it.f for it in items] + [rng.standard_normal(shape) for shape, _ in longs]
     ins = [torch.from_numpy(f).cuda() for f in data]
@@ -120,7 +131,7 @@ def test_batch_mixes_long_lines_with_grids(cuda, precision):
     with torch.cuda.stream(s):
         b.solve(ins, outs, s)
     torch.cuda.current_stream().wait_stream(s)
-    assert abi.cbs_last_launch_count() == 1
+    assert _launches_ok(mode, len(specs))
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         b.solve(ins, outs)
@@ -146,7 +157,8 @@ def test_batch_rejects_long_lines_off_the_warp_layout(cuda):
         abi.cbs_batch_create([d])
 
 
-def test_batch_fp32_problems_with_fp64_ones(cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_fp32_problems_with_fp64_ones(cuda, mode):
     # FP32 problems (FP32 in and out, no refinement) in the same launch as
     # FP64 and refinement problems; tolerance 2e-5 for the FP32 ones
     items = W.ragged_batch(count=6, seed=91, sizes=(32, 48, 64, 96))
@@ -159,13 +171,13 @@ def test_batch_fp32_problems_with_fp64_ones(cuda):
         specs.append((shape, direction, dict(lhs=sch["lhs"], rhs=sch["rhs"], h=W.grid_spacing(n), precision="fp32",
                                              in_dtype=torch.float32)))
         f32.append((shape, direction, scheme))
-    b = Batch(specs)
+    b = Batch(specs, mode=mode)
     rng = np.random.default_rng(4)
     data = [it.f for it in items] + [rng.uniform(-1, 1, size=sh).astype(np.float32) for sh, _, _ in f32]
     ins = [torch.from_numpy(f).cuda() for f in data]
     outs = b.solve(ins)
     torch.cuda.synchronize()
-    assert abi.cbs_last_launch_count() == 1
+    assert _launches_ok(mode, len(specs))
     for it, y in zip(items, outs):
         assert oracle.rel_err(y.cpu().numpy(), _ref(it, it.f)) < 1e-12
     for (shape, direction, scheme), f, y in zip(f32, data[len(items):], outs[len(items):]):
@@ -175,3 +187,37 @@ def test_batch_fp32_problems_with_fp64_ones(cuda):
         ref = oracle.derivative(f.astype(np.float64), sch["lhs"], sch["rhs"], W.grid_spacing(n), axis=2 - direction)
         assert oracle.rel_err(y.double().cpu().numpy(), ref) < 2e-5
     b.close()
+
+
+def test_batch_modes_agree_and_auto_picks_by_size(cuda):
+    # the two modes give the same results element by element up to the
+    # kernels' rounding; auto takes per-problem launches from 2^20 unknowns
+    # per problem on average, the persistent launch below
+    big = [((64, 128, 128), 0, "fp64", "tri6"), ((128, 64, 128), 1, "fp32_refine", "penta10"),
+           ((128, 128, 64), 2, "fp64", "penta10")]
+    specs = []
+    for shape, direction, prec, scheme in big:
+        n = shape[2 - direction]
+        sch = SCH[scheme]
+        specs.append((shape, direction, dict(lhs=sch["lhs"], rhs=sch["rhs"], h=W.grid_spacing(n), precision=prec)))
+    rng = np.random.default_rng(12)
+    ins = [torch.from_numpy(rng.uniform(-1, 1, size=sh)).cuda() for sh, _, _ in specs]
+    got = {}
+    for mode in ("persistent", "per_problem", "auto"):
+        b = Batch(specs, mode=mode)
+        got[mode] = [y.cpu().numpy() for y in b.solve(ins)]
+        torch.cuda.synchronize()
+        got[mode + "_launches"] = abi.cbs_last_launch_count()
+        b.close()
+    assert got["persistent_launches"] == 1 and got["per_problem_launches"] >= 3
+    assert got["auto_launches"] == got["per_problem_launches"]  # 2^20 unknowns each
+    for a, c in zip(got["persistent"], got["per_problem"]):
+        assert oracle.rel_err(a, c) < 1e-12
+    small = Batch(specs[:1] + [((4, 8, 32), 0, dict(lhs=(1 / 3,), rhs=(14 / 9, 1 / 9), h=0.2))])
+    x2 = torch.zeros((4, 8, 32), dtype=torch.float64, device="cuda")
+    small.solve([ins[0], x2])
+    # (64 * 128 * 128 + 1024) / 2 unknowns on average: below 2^20 -> one launch
+    assert abi.cbs_last_launch_count() == 1
+    small.close()
+    with pytest.raises(ValueError):
+        Batch(specs, mode="bogus")
