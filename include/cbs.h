@@ -85,8 +85,10 @@ enum { CBS_DTYPE_F64 = 0, CBS_DTYPE_F32 = 1 };
 /* Left-hand side. */
 enum {
     CBS_LHS_TOEPLITZ = 0,    /* constant bands: (beta,) alpha, 1, alpha (, beta)      */
-    CBS_LHS_VARIABLE = 1     /* tridiagonal, row-wise alpha_i read from cbs_desc.bands:
+    CBS_LHS_VARIABLE = 1,    /* tridiagonal, row-wise alpha_i read from cbs_desc.bands:
                                 A[i,i-1] = A[i,i+1] = alpha_i, A[i,i] = 1            */
+    CBS_LHS_BLOCK = 2        /* block-tridiagonal with 2 x 2 block entries (Sec. 1),
+                                see cbs_desc.block_size / blocks                     */
 };
 
 /* Right-hand side.  The staggered kinds (App. A.2; Eq. 2) map a field on one
@@ -149,6 +151,20 @@ typedef struct cbs_desc {
     int32_t closure_rows;   /* 0..4                                                */
     int32_t closure_width;  /* 1..16                                               */
     const double* closure;  /* host array, 2 * closure_width doubles per row      */
+    /* CBS_LHS_BLOCK: a line of n = dims[direction] unknowns is n / b points of
+     * b = block_size unknowns each, point-major (unknown c of point m is
+     * element m b + c along the line), and point m couples to points m - 1, m
+     * and m + 1 through the b x b blocks L, D, U (the same for every point):
+     *     L x_{m-1} + D x_m + U x_{m+1} = d_m   (cyclic: point indices mod n/b).
+     * `blocks` is a host array of 3 b^2 doubles, L, D, U row-major, read by
+     * cbs_plan_create (not kept).  b = 2 (the flattened system has half
+     * bandwidth 2b - 1 = 3: set bandwidth = 7); n even; right-hand side given
+     * (CBS_RHS_NONE); CBS_FP64 or CBS_FP32; on-chip lines (partitions of at
+     * most 32 rows, made of whole points); cyclic or acyclic; no batches,
+     * closures or transposes.  Partitions are counted in whole points (the
+     * `segments` partitions split the n / b points as evenly as possible). */
+    int32_t block_size;     /* b: 2 for CBS_LHS_BLOCK; ignored otherwise          */
+    const double* blocks;   /* CBS_LHS_BLOCK: host array L | D | U (3 b^2 doubles) */
 } cbs_desc;
 
 typedef struct cbs_plan cbs_plan;
@@ -280,7 +296,8 @@ cbs_status cbs_solve_transpose(cbs_plan* plan, const void* g, const void* x,
 
 /* grad_bands_i = -lambda_i (x_{i-1} + x_{i+1}) along the plan's lines
  * (periodic), the gradient of <g, x> with respect to row-wise alpha_i when
- * lambda = A^{-T} g.  Device arrays of the plan's dims, in_dtype. */
+ * lambda = A^{-T} g.  Device arrays of the plan's dims, in_dtype.
+ * UNSUPPORTED for CBS_LHS_BLOCK plans. */
 cbs_status cbs_band_grad(cbs_plan* plan, const void* lambda, const void* x,
                          void* grad_bands, void* stream);
 
@@ -311,7 +328,9 @@ cbs_status cbs_schedule(int32_t p, int32_t cyclic, int32_t* stages, int32_t cap,
  *   - when bhat and xt are non-NULL, applies the pre-factorised stage
  *     coefficients (Algorithms 2-4) to b-hat (p*r doubles) and writes
  *     x~ = A-hat^{-1} b-hat to xt, exactly as the device kernels do.
- * Toeplitz LHS only.  Errors: INVALID_ARG, UNSUPPORTED, SINGULAR. */
+ * Toeplitz or block-entry LHS (CBS_LHS_BLOCK: partitions of whole points,
+ * as cbs_plan_create makes them).  Errors: INVALID_ARG, UNSUPPORTED,
+ * SINGULAR. */
 cbs_status cbs_interface_model(const cbs_desc* desc, int32_t p, double* dhat, double* lhat,
                                double* uhat, const double* bhat, double* xt);
 

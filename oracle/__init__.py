@@ -31,6 +31,11 @@ What the oracle computes is the plain definition of the method's result:
                        paper prints no closure; the rows are inputs.
 * ``dense_matrix`` / ``acyclic_dense_matrix`` / ``dense_solve``  brute force
                        for tiny n (partial pivoting).
+* ``block_tridiagonal_bands`` / ``block_dense_matrix``  block entries (Sec. 1):
+                       the block-tridiagonal matrix with b x b blocks as the
+                       banded matrix of half bandwidth 2b - 1 that the solves
+                       above take, and assembled block by block for dense
+                       checks.
 * ``adjoint_variable_tri``  gradients of L = <g, x> for x = A(alpha)^{-1} S f:
                        lambda = A^{-T} g, grad_f = S^T lambda,
                        grad_alpha_i = -lambda_i (x_{i-1} + x_{i+1}).  The paper
@@ -181,6 +186,51 @@ def toeplitz_bands(n, lhs):
         b[r - q] = lhs[q - 1]
         b[r + q] = lhs[q - 1]
     return b
+
+
+def block_tridiagonal_bands(npts, L, D, U):
+    """Bands (2r+1, n) of a block-tridiagonal matrix with b x b blocks.
+
+    Sec. 1 names block entries (compact schemes for shock capturing couple
+    several unknowns per grid point).  A line of npts points with b unknowns
+    each, point-major (unknown c of point m is row m b + c), where point m
+    couples to points m-1, m, m+1 through L, D, U (the same for every point),
+    is a banded matrix: row m b + c holds L[c][j] in column (m-1) b + j, D[c][j]
+    in column m b + j and U[c][j] in column (m+1) b + j, i.e. at offsets
+    j - c - b, j - c and j - c + b, so its half bandwidth is r = 2b - 1.
+    Column indices wrap (cyclic); solve_acyclic drops the wrapped corners.
+    """
+    L, D, U = (np.asarray(a, dtype=np.float64) for a in (L, D, U))
+    b = D.shape[0]
+    r = 2 * b - 1
+    n = npts * b
+    bands = np.zeros((2 * r + 1, n))
+    for m in range(npts):
+        for c in range(b):
+            i = m * b + c
+            for j in range(b):
+                bands[r + j - c - b, i] += L[c, j]
+                bands[r + j - c, i] += D[c, j]
+                bands[r + j - c + b, i] += U[c, j]
+    return bands
+
+
+def block_dense_matrix(npts, L, D, U, cyclic=True):
+    """Dense (npts b) x (npts b) block-tridiagonal matrix, assembled block by
+    block: block (m, m-1) = L, (m, m) = D, (m, m+1) = U; cyclic wraps the
+    corner blocks (m = 0 gets L at the last point, the last point U at 0)."""
+    L, D, U = (np.asarray(a, dtype=np.float64) for a in (L, D, U))
+    b = D.shape[0]
+    A = np.zeros((npts * b, npts * b))
+    for m in range(npts):
+        A[m * b:(m + 1) * b, m * b:(m + 1) * b] += D
+        if m > 0 or cyclic:
+            mm = (m - 1) % npts
+            A[m * b:(m + 1) * b, mm * b:(mm + 1) * b] += L
+        if m < npts - 1 or cyclic:
+            mp = (m + 1) % npts
+            A[m * b:(m + 1) * b, mp * b:(mp + 1) * b] += U
+    return A
 
 
 def variable_alpha_bands(alpha_lines):
@@ -391,15 +441,17 @@ def adjoint_variable_tri(f, alpha, g, coefs, h, axis=-1):
 
 
 # ---------------------------------------------------------------- interface system
-def partition_bounds(n, p):
-    """Partition starts/sizes: the first n mod p partitions get ceil(n/p) rows."""
-    base, extra = divmod(n, p)
-    sizes = [base + (1 if i < extra else 0) for i in range(p)]
+def partition_bounds(n, p, unit=1):
+    """Partition starts/sizes: the first (n/unit) mod p partitions get
+    ceil(n/(unit p)) units of `unit` rows (unit = b: whole points of a
+    block-entry line)."""
+    base, extra = divmod(n // unit, p)
+    sizes = [unit * (base + (1 if i < extra else 0)) for i in range(p)]
     starts = np.cumsum([0] + sizes[:-1]).tolist()
     return starts, sizes
 
 
-def reduced_system_dense(bands, p):
+def reduced_system_dense(bands, p, unit=1):
     """Interface system A-hat of Sec. 3 as a dense Schur complement.
 
     The interface unknowns are the first r rows of each partition (Fig. 3);
@@ -411,7 +463,7 @@ def reduced_system_dense(bands, p):
     A = dense_matrix(bands)
     n = A.shape[0]
     r = (bands.shape[0] - 1) // 2
-    starts, sizes = partition_bounds(n, p)
+    starts, sizes = partition_bounds(n, p, unit)
     iface = [s + q for s in starts for q in range(r)]
     bulk = [j for j in range(n) if j not in set(iface)]
     A_II = A[np.ix_(iface, iface)]

@@ -19,7 +19,7 @@ CBS_OK, CBS_ERR_INVALID_ARG, CBS_ERR_UNSUPPORTED, CBS_ERR_SINGULAR, CBS_ERR_TIME
     CBS_ERR_NO_MEMORY, CBS_ERR_RANGE = range(8)
 CBS_FP64, CBS_FP32, CBS_FP32_REFINE, CBS_FP32_REFINE_I64 = 0, 1, 2, 3
 CBS_DTYPE_F64, CBS_DTYPE_F32 = 0, 1
-CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE = 0, 1
+CBS_LHS_TOEPLITZ, CBS_LHS_VARIABLE, CBS_LHS_BLOCK = 0, 1, 2
 CBS_RHS_NONE, CBS_RHS_CENTRAL, CBS_RHS_STAGGERED, CBS_RHS_MIDPOINT = 0, 1, 2, 3
 CBS_BATCH_AUTO, CBS_BATCH_PERSISTENT, CBS_BATCH_PER_PROBLEM = 0, 1, 2
 
@@ -65,6 +65,8 @@ class cbs_desc(ctypes.Structure):
         ("closure_rows", ctypes.c_int32),
         ("closure_width", ctypes.c_int32),
         ("closure", ctypes.c_void_p),
+        ("block_size", ctypes.c_int32),
+        ("blocks", ctypes.c_void_p),
     ]
 
 

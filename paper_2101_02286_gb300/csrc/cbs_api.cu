@@ -12,6 +12,7 @@
 #include <new>
 #include <string>
 
+#include "cbs_bands.h"
 #include "cbs_line_launch.cuh"
 #include "cbs_plan_struct.h"
 
@@ -129,6 +130,24 @@ Bands desc_bands(const cbs_desc* d, int r, double alpha) {
   return A;
 }
 
+// Block-entry plans (CBS_LHS_BLOCK): the periodic bands of the flattened
+// block-tridiagonal matrix, and partition sizes in whole points (the n / b
+// points split as evenly as possible over p partitions).  false when p
+// exceeds the points.
+PBands desc_block_bands(const cbs_desc* d) {
+  const int b = d->block_size;
+  return block_bands(b, d->blocks, d->blocks + b * b, d->blocks + 2 * b * b);
+}
+bool block_sizes(int n, int b, int p, int sizes[3]) {
+  const int npts = n / b;
+  if (p < 1 || p > npts) return false;
+  const int small = npts / p, extra = npts % p;
+  sizes[0] = extra ? extra : p;
+  sizes[1] = (small + (extra ? 1 : 0)) * b;
+  sizes[2] = small * b;
+  return true;
+}
+
 bool is_staggered(const cbs_desc* d) { return d->rhs_kind == CBS_RHS_STAGGERED || d->rhs_kind == CBS_RHS_MIDPOINT; }
 
 cbs_status validate(const cbs_desc* d) {
@@ -139,8 +158,20 @@ cbs_status validate(const cbs_desc* d) {
   if (d->bandwidth != 3 && d->bandwidth != 5 && d->bandwidth != 7)
     return fail(CBS_ERR_INVALID_ARG, "bandwidth must be 3, 5 or 7");
   if (d->cyclic != 0 && d->cyclic != 1) return fail(CBS_ERR_INVALID_ARG, "cyclic must be 0 or 1");
-  if (d->lhs_kind != CBS_LHS_TOEPLITZ && d->lhs_kind != CBS_LHS_VARIABLE)
+  if (d->lhs_kind != CBS_LHS_TOEPLITZ && d->lhs_kind != CBS_LHS_VARIABLE && d->lhs_kind != CBS_LHS_BLOCK)
     return fail(CBS_ERR_INVALID_ARG, "bad lhs_kind");
+  if (d->lhs_kind == CBS_LHS_BLOCK) {
+    if (d->block_size != 2) return fail(CBS_ERR_UNSUPPORTED, "block entries: block_size 2");
+    if (d->bandwidth != 7) return fail(CBS_ERR_INVALID_ARG, "block entries of size 2: bandwidth 7 (half bandwidth 3)");
+    if (!d->blocks) return fail(CBS_ERR_INVALID_ARG, "block entries need the host array of L, D, U");
+    for (int k = 0; k < 3 * d->block_size * d->block_size; k++)
+      if (!std::isfinite(d->blocks[k])) return fail(CBS_ERR_INVALID_ARG, "non-finite block entries");
+    if (d->dims[d->direction] % d->block_size != 0)
+      return fail(CBS_ERR_INVALID_ARG, "block entries: the line length must be a multiple of block_size");
+    if (d->rhs_kind != CBS_RHS_NONE) return fail(CBS_ERR_UNSUPPORTED, "block entries: right-hand side given (no stencil)");
+    if (d->precision != CBS_FP64 && d->precision != CBS_FP32)
+      return fail(CBS_ERR_UNSUPPORTED, "block entries: FP64 or FP32 (the refinement residual is for Toeplitz bands)");
+  }
   if (d->rhs_kind < CBS_RHS_NONE || d->rhs_kind > CBS_RHS_MIDPOINT) return fail(CBS_ERR_INVALID_ARG, "bad rhs_kind");
   if (d->rhs_kind == CBS_RHS_CENTRAL) {
     if (d->rhs_terms < 1 || d->rhs_terms > 3) return fail(CBS_ERR_INVALID_ARG, "rhs_terms must be 1..3");
@@ -752,13 +783,19 @@ cbs_status cbs_interface_model(const cbs_desc* d, int32_t p, double* dhat, doubl
                                const double* bhat, double* xt) {
   cbs_status st = validate(d);
   if (st) return st;
-  if (d->lhs_kind != CBS_LHS_TOEPLITZ) return fail(CBS_ERR_UNSUPPORTED, "Toeplitz LHS only");
+  if (d->lhs_kind == CBS_LHS_VARIABLE) return fail(CBS_ERR_UNSUPPORTED, "Toeplitz or block-entry LHS only");
   const int r = (d->bandwidth - 1) / 2, n = (int)d->dims[d->direction];
   if (p < 1 || n < 2 * r * p) return fail(CBS_ERR_INVALID_ARG, "need 1 <= p and n >= 2 r p");
-  const Bands A = desc_bands(d, r, d->alpha);
   LineTables T;
   bool singular = false;
-  std::string msg = build_line_tables(T, n, A, p, d->cyclic != 0, &singular, /*max_lanes=*/1 << 30);
+  std::string msg;
+  if (d->lhs_kind == CBS_LHS_BLOCK) {
+    int sizes[3];
+    if (!block_sizes(n, d->block_size, p, sizes)) return fail(CBS_ERR_INVALID_ARG, "more partitions than points");
+    msg = build_line_tables_periodic(T, n, desc_block_bands(d), p, d->cyclic != 0, &singular, 1 << 30, sizes);
+  } else {
+    msg = build_line_tables(T, n, desc_bands(d, r, d->alpha), p, d->cyclic != 0, &singular, /*max_lanes=*/1 << 30);
+  }
   if (!msg.empty()) return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
   const size_t nb = (size_t)p * r * r;
   if (dhat) std::memcpy(dhat, T.Dhat.data(), nb * sizeof(double));
@@ -879,6 +916,10 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
     // a line whose partitions do not fit one lane's registers goes to the
     // segment-per-CTA path
     const bool use_long = !P->var && (d->segments > kMaxLanes || p < 1 || (P->n + p - 1) / p > maxM0);
+    if (use_long && d->lhs_kind == CBS_LHS_BLOCK) {
+      delete P;
+      return fail(CBS_ERR_UNSUPPORTED, "block entries: on-chip lines only (at most 32 partitions of at most 32 rows)");
+    }
     if (use_long) {
       st = create_long(P, d);
       if (st) {
@@ -909,7 +950,18 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
   }
   const Bands A = desc_bands(d, P->r, P->var ? 0.25 : d->alpha);  // variable: geometry only
   bool singular = false;
-  std::string msg = build_line_tables(P->host, P->n, A, p, d->cyclic != 0, &singular, kMaxLanes);
+  std::string msg;
+  if (d->lhs_kind == CBS_LHS_BLOCK) {
+    int sizes[3];
+    if (!block_sizes(P->n, d->block_size, p, sizes)) {
+      delete P;
+      return fail(CBS_ERR_INVALID_ARG, "block entries: more partitions than points");
+    }
+    msg = build_line_tables_periodic(P->host, P->n, desc_block_bands(d), p, d->cyclic != 0, &singular, kMaxLanes,
+                                     sizes);
+  } else {
+    msg = build_line_tables(P->host, P->n, A, p, d->cyclic != 0, &singular, kMaxLanes);
+  }
   if (!msg.empty()) {
     delete P;
     return fail(singular ? CBS_ERR_SINGULAR : CBS_ERR_UNSUPPORTED, msg);
@@ -989,7 +1041,8 @@ cbs_status cbs_plan_create(cbs_plan** out, const cbs_desc* d) {
       return st;
     }
   }
-  P->desc.closure = nullptr;  // the caller's host array is not kept
+  P->desc.closure = nullptr;  // the caller's host arrays are not kept
+  P->desc.blocks = nullptr;
   *out = P;
   return CBS_OK;
 }
@@ -1150,6 +1203,7 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
     return CBS_OK;
   }
   if (P->kind != 0) return fail(CBS_ERR_UNSUPPORTED, "transpose solve of long-line plans");
+  if (d.lhs_kind == CBS_LHS_BLOCK) return fail(CBS_ERR_UNSUPPORTED, "transpose solve of block-entry plans");
   // Toeplitz: A is symmetric, and on a periodic grid A^{-1} and the stencil S
   // are both circulant, so S^T A^{-T} g = A^{-1} (S^T g), with S^T = -S for the
   // central stencil: the same line kernel with transposed stencil weights.
@@ -1197,6 +1251,7 @@ cbs_status cbs_solve_transpose(cbs_plan* P, const void* g, const void* x, void* 
 cbs_status cbs_band_grad(cbs_plan* P, const void* lambda, const void* x, void* grad_bands, void* stream) {
   g_launches = 0;
   if (!P || !lambda || !x || !grad_bands) return fail(CBS_ERR_INVALID_ARG, "null argument");
+  if (P->desc.lhs_kind == CBS_LHS_BLOCK) return fail(CBS_ERR_UNSUPPORTED, "band gradient of block-entry plans");
   const cbs_desc& d = P->desc;
   cudaError_t e = launch_band_grad(d.in_dtype == CBS_DTYPE_F64, lambda, x, grad_bands, d.dims[0], d.dims[1],
                                    d.dims[2], d.direction, (cudaStream_t)stream);

@@ -1,7 +1,8 @@
 // cbs_plan.cpp -- host-side pre-factorisation of the partitioned system.
 //
-// For a Toeplitz line matrix A (half bandwidth r, cyclic or not) split into
-// p partitions this computes, in FP64, everything the per-solve kernels need
+// For a Toeplitz line matrix A (half bandwidth r, cyclic or not), or one
+// whose rows repeat with a short period (block entries, cbs_bands.h), split
+// into p partitions this computes, in FP64, everything the per-solve kernels need
 // that does not depend on the right-hand side (paper Sec. 4, last paragraph):
 //   - the banded LU factors of the bulk blocks D_i (Sec. 3, Fig. 3);
 //   - S_i = D_i^{-1} L_i and R_i = D_i^{-1} U_i (Eq. 15-16);
@@ -13,6 +14,7 @@
 #include <cstring>
 #include <utility>
 
+#include "cbs_bands.h"
 #include "cbs_internal.h"
 
 namespace cbs {
@@ -169,8 +171,32 @@ bool inv(const Blk& x, Blk& out, double scale = 0.0) {
 
 }  // namespace
 
+PBands block_bands(int b, const double* L, const double* D, const double* U) {
+  PBands A;
+  A.r = 2 * b - 1;
+  A.period = b;
+  for (int c = 0; c < b; c++)
+    for (int j = 0; j < b; j++) {
+      A.v[c][j - c - b + A.r] = L[c * b + j];
+      A.v[c][j - c + A.r] = D[c * b + j];
+      A.v[c][b + j - c + A.r] = U[c * b + j];
+    }
+  return A;
+}
+
 std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool cyclic,
                               bool* singular, int max_lanes, const int* sizes) {
+  PBands B;
+  B.r = A.r;
+  B.period = 1;
+  for (int t = 0; t < 2 * A.r + 1; t++) B.v[0][t] = A.v[t];
+  return build_line_tables_periodic(T, n, B, p, cyclic, singular, max_lanes, sizes);
+}
+
+// Row indices below are relative to a partition's first row, which is a
+// multiple of the period: interface row q is row q, bulk row j is row r + j.
+std::string build_line_tables_periodic(LineTables& T, int n, const PBands& A, int p, bool cyclic, bool* singular,
+                                       int max_lanes, const int* sizes) {
   *singular = false;
   const int r = A.r;
   T = LineTables();
@@ -194,6 +220,8 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
     if (T.count_big == 0) T.count_big = p;  // all partitions equal
   }
   if (T.rows_small < 2 * r) return "partitions need at least 2r rows (n >= 2 r p)";
+  if (A.period > 1 && (n % A.period || T.rows_big % A.period || T.rows_small % A.period))
+    return "block entries: every partition must hold whole points (sizes multiples of the block size)";
   T.start.resize(p);
   T.size.resize(p);
   int acc = 0;
@@ -211,11 +239,10 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
   // start from D's rows
   std::vector<double> work((size_t)nmax * (2 * r + 1));
   for (int j = 0; j < nmax; j++)
-    for (int t = -r; t <= r; t++) work[(size_t)j * (2 * r + 1) + t + r] = A.at(t);
+    for (int t = -r; t <= r; t++) work[(size_t)j * (2 * r + 1) + t + r] = A.at(r + j, t);
+  const double bscale = A.max_abs();
   for (int j = 0; j < nmax; j++) {
     double piv = work[(size_t)j * (2 * r + 1) + r];
-    double bscale = 0.0;
-    for (int t = -r; t <= r; t++) bscale = std::fmax(bscale, std::fabs(A.at(t)));
     if (!(std::fabs(piv) > 1e-12 * bscale) || !std::isfinite(piv)) {
       *singular = true;
       return "zero pivot in a bulk block D_i";
@@ -264,11 +291,11 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
     Rcl[c].assign((size_t)N * r, 0.0);
     for (int q = 0; q < r; q++) {
       // L_i[:, q]: bulk row j couples to own interface column q at offset q - r - j
-      for (int j = 0; j < N; j++) col[j] = A.at(q - r - j);
+      for (int j = 0; j < N; j++) col[j] = A.at(r + j, q - r - j);
       solveD(N, col.data(), sol.data());
       for (int j = 0; j < N; j++) Scl[c][(size_t)j * r + q] = sol[j];
       // U_i[:, q]: bulk row j couples to next interface column q at offset m + q - r - j
-      for (int j = 0; j < N; j++) col[j] = A.at(m + q - r - j);
+      for (int j = 0; j < N; j++) col[j] = A.at(r + j, m + q - r - j);
       solveD(N, col.data(), sol.data());
       for (int j = 0; j < N; j++) Rcl[c][(size_t)j * r + q] = sol[j];
     }
@@ -294,8 +321,8 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
   // ---- b-hat assembly blocks (Eq. 21) ----
   for (int q = 0; q < r; q++)
     for (int e = 0; e < r; e++) {
-      T.Lt[q][e] = (e >= q) ? A.at(e - r - q) : 0.0;
-      T.Ut[q][e] = (e <= q) ? A.at(r + e - q) : 0.0;
+      T.Lt[q][e] = (e >= q) ? A.at(q, e - r - q) : 0.0;
+      T.Ut[q][e] = (e <= q) ? A.at(q, r + e - q) : 0.0;
     }
 
   // ---- reduced blocks (Eq. 18-20) ----
@@ -306,7 +333,7 @@ std::string build_line_tables(LineTables& T, int n, const Bands& A, int p, bool 
     const int Nm = T.size[im] - r, N = T.size[i] - r;
     Blk Dt(r), LRm(r), USi(r), LSm(r), URi(r);
     for (int q = 0; q < r; q++)
-      for (int qq = 0; qq < r; qq++) Dt(q, qq) = A.at(qq - q);
+      for (int qq = 0; qq < r; qq++) Dt(q, qq) = A.at(q, qq - q);
     for (int q = 0; q < r; q++)
       for (int qq = 0; qq < r; qq++) {
         double a1 = 0, a2 = 0, a3 = 0, a4 = 0;

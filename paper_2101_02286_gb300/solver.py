@@ -20,7 +20,7 @@ _STENCIL = {"central": abi.CBS_RHS_CENTRAL, "staggered": abi.CBS_RHS_STAGGERED, 
 def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 1.0, segments: int = 0,
               precision: str = "fp64", sweeps: int = 1, in_dtype=torch.float64, out_dtype=None,
               cyclic: bool = True, bands_ptr: int | None = None, stencil: str = "central",
-              shift: int = 0, closure=None) -> abi.cbs_desc:
+              shift: int = 0, closure=None, blocks=None) -> abi.cbs_desc:
     """Descriptor for lines along `direction` of a (nz, ny, nx) field.
 
     lhs: (alpha,) tridiagonal, (alpha, beta) pentadiagonal or (alpha, beta,
@@ -32,13 +32,26 @@ def make_desc(shape_zyx, direction: int, lhs=(1.0 / 3.0,), rhs=None, h: float = 
     (shift 0) or nodes to half points (shift 1).  closure: (L, R), two
     equal-shape (rows, width) arrays of one-sided boundary rows for an
     acyclic derivative (row k: sum_j L[k][j] x_j = sum_j R[k][j] f_j / h; the
-    right end is their mirror image, see cbs.h).
+    right end is their mirror image, see cbs.h).  blocks: (L, D, U), three
+    2 x 2 arrays: a block-tridiagonal LHS whose lines hold points of two
+    unknowns each, point-major (lhs is then ignored; right-hand side given).
     """
     nz, ny, nx = (int(s) for s in shape_zyx)
     d = abi.cbs_desc()
     d.dims[0], d.dims[1], d.dims[2] = nx, ny, nz
     d.direction = int(direction)
-    if lhs == "variable":
+    if blocks is not None:
+        import numpy as np
+        L, D, U = (np.asarray(a, dtype=np.float64) for a in blocks)
+        if not (L.shape == D.shape == U.shape == (2, 2)):
+            raise ValueError("blocks: three 2 x 2 arrays (L, D, U)")
+        buf = np.ascontiguousarray(np.concatenate([L.ravel(), D.ravel(), U.ravel()]))
+        d._blocks_buf = buf  # kept alive with the descriptor
+        d.bandwidth = 7
+        d.lhs_kind = abi.CBS_LHS_BLOCK
+        d.block_size = 2
+        d.blocks = buf.ctypes.data
+    elif lhs == "variable":
         d.bandwidth = 3
         d.lhs_kind = abi.CBS_LHS_VARIABLE
         d.bands = bands_ptr

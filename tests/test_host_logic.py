@@ -195,3 +195,60 @@ def test_staggered_descriptors_validated_before_device_work():
     with pytest.raises(abi.CbsError) as e:
         abi.cbs_plan_create(d)
     assert e.value.status == abi.CBS_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- block entries
+BLK = (np.array([[0.21, 0.07], [-0.05, 0.18]]), np.array([[1.0, 0.15], [-0.12, 0.9]]),
+       np.array([[0.24, -0.06], [0.04, 0.2]]))
+
+
+@pytest.mark.parametrize("npts,p", [(8, 1), (12, 2), (13, 3), (24, 4), (40, 5), (64, 16), (100, 31), (96, 32)])
+@pytest.mark.parametrize("cyclic", [True, False])
+def test_block_reduced_system_matches_schur_complement(npts, p, cyclic):
+    # the plan's interface system for 2 x 2 block entries (periodic bands of
+    # half bandwidth 3, partitions of whole points) against the dense Schur
+    # complement of the flattened matrix, and its pre-factorised solve
+    n, r = 2 * npts, 3
+    desc = make_desc((1, 1, n), 0, blocks=BLK, cyclic=cyclic)
+    rng = np.random.default_rng(npts * 7 + p)
+    bhat = rng.standard_normal(p * r)
+    D, L, U, xt = abi.cbs_interface_model(desc, p, bhat)
+    A = oracle.block_dense_matrix(npts, *BLK, cyclic=cyclic)
+    bands = np.zeros((7, n))  # the banded form of A (corners dropped when acyclic)
+    for i in range(n):
+        for k in range(7):
+            bands[k, i] = A[i, (i + k - r) % n] if (cyclic or 0 <= i + k - r < n) else 0.0
+    Ahat, _, _ = oracle.reduced_system_dense(bands, p, unit=2)
+    M = np.zeros((p * r, p * r))
+    for i in range(p):
+        M[i * r:(i + 1) * r, i * r:(i + 1) * r] += D[i]
+        M[i * r:(i + 1) * r, ((i - 1) % p) * r:((i - 1) % p + 1) * r] += L[i]
+        M[i * r:(i + 1) * r, ((i + 1) % p) * r:((i + 1) % p + 1) * r] += U[i]
+    assert np.max(np.abs(M - Ahat)) < 1e-13
+    assert oracle.rel_err(xt, np.linalg.solve(M, bhat)) < 1e-12
+
+
+def test_block_descriptors_validated():
+    from paper_2101_02286_gb300.solver import Plan
+    good = dict(blocks=BLK)
+    for shape, kw, status in [
+            ((1, 1, 63), good, abi.CBS_ERR_INVALID_ARG),                      # odd line length
+            ((1, 1, 64), dict(good, precision="fp32_refine"), abi.CBS_ERR_UNSUPPORTED),
+            ((1, 1, 64), dict(good, rhs=(14 / 9, 1 / 9)), abi.CBS_ERR_UNSUPPORTED)]:
+        with pytest.raises(abi.CbsError) as e:
+            Plan(shape, 0, **kw)
+        assert e.value.status == status, (shape, kw)
+    d = make_desc((1, 1, 64), 0, blocks=BLK)
+    d.block_size = 3
+    with pytest.raises(abi.CbsError) as e:
+        abi.cbs_interface_model(d, 2)
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+    d = make_desc((1, 1, 64), 0, blocks=BLK)
+    d.bandwidth = 5
+    with pytest.raises(abi.CbsError) as e:
+        abi.cbs_interface_model(d, 2)
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG
+    d = make_desc((1, 1, 64), 0, blocks=BLK)
+    with pytest.raises(abi.CbsError) as e:
+        abi.cbs_interface_model(d, 40)  # more partitions than points
+    assert e.value.status == abi.CBS_ERR_INVALID_ARG

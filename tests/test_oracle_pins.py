@@ -483,3 +483,72 @@ def test_closure_convergence_third_order():
         errs.append(np.max(np.abs(got - (3 * np.cos(3 * x) + np.exp(x)))))
     orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(2.9 < o < 4.0 for o in orders), orders
+
+
+# ---------------------------------------------------------------- block entries
+# Block-tridiagonal systems with 2 x 2 blocks (Sec. 1: block entries), as the
+# banded matrices the oracle's solves take.  Blocks: diagonally dominant,
+# neither symmetric nor diagonal, so a transposed block or a swapped L/U
+# changes the answer.
+BL = np.array([[0.21, 0.07], [-0.05, 0.18]])
+BD = np.array([[1.0, 0.15], [-0.12, 0.9]])
+BU = np.array([[0.24, -0.06], [0.04, 0.2]])
+
+
+def test_block_bands_flatten_the_block_matrix():
+    # the banded form, expanded, equals the matrix assembled block by block
+    # (cyclic and acyclic); half bandwidth 2b - 1 = 3
+    for npts in (3, 5, 8):
+        bands = oracle.block_tridiagonal_bands(npts, BL, BD, BU)
+        assert bands.shape == (7, 2 * npts)
+        assert np.array_equal(oracle.dense_matrix(bands), oracle.block_dense_matrix(npts, BL, BD, BU))
+        assert np.array_equal(oracle.acyclic_dense_matrix(bands),
+                              oracle.block_dense_matrix(npts, BL, BD, BU, cyclic=False))
+
+
+@pytest.mark.parametrize("npts", [6, 7, 16, 33])  # the oracle's cyclic banded path needs n >= 4r
+def test_block_solves_match_lapack(npts):
+    rng = np.random.default_rng(npts)
+    d = rng.standard_normal((3, 2 * npts))
+    bands = oracle.block_tridiagonal_bands(npts, BL, BD, BU)
+    for cyclic in (True, False):
+        A = oracle.block_dense_matrix(npts, BL, BD, BU, cyclic=cyclic)
+        ref = np.linalg.solve(A, d.T).T
+        got = oracle.solve_cyclic(bands, d) if cyclic else oracle.solve_acyclic(bands, d)
+        assert oracle.rel_err(got, ref) < 1e-13, cyclic
+
+
+def test_block_diagonal_blocks_decouple():
+    # diagonal blocks: the two unknowns of a point never meet, so the system
+    # is two independent scalar tridiagonal systems (Thomas + Sherman-Morrison)
+    npts = 24
+    L, D, U = np.diag([0.2, 0.3]), np.diag([1.0, 1.1]), np.diag([0.25, 0.15])
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal(2 * npts)
+    got = oracle.solve_cyclic(oracle.block_tridiagonal_bands(npts, L, D, U), d)
+    for c in range(2):
+        tri = np.zeros((3, npts))
+        tri[0], tri[1], tri[2] = L[c, c], D[c, c], U[c, c]
+        ref = oracle.solve_cyclic(tri, d[c::2])
+        assert oracle.rel_err(got[c::2], ref) < 1e-14
+
+
+def test_block_kronecker_closed_form():
+    # L = l K, D = d K, U = u K: A = T (x) K with T = tri(l, d, u) cyclic, so
+    # x (points x unknowns) = T^{-1} B K^{-T}
+    npts = 20
+    K = np.array([[1.0, 0.3], [-0.2, 0.8]])
+    l, dd, u = 0.2, 1.0, 0.3
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((npts, 2))
+    T = np.zeros((npts, npts))
+    for m in range(npts):
+        T[m, m], T[m, (m - 1) % npts], T[m, (m + 1) % npts] = dd, l, u
+    ref = np.linalg.solve(T, B) @ np.linalg.inv(K).T
+    got = oracle.solve_cyclic(oracle.block_tridiagonal_bands(npts, l * K, dd * K, u * K), B.ravel())
+    assert oracle.rel_err(got.reshape(npts, 2), ref) < 1e-13
+
+
+def test_block_partition_bounds_keep_points_whole():
+    starts, sizes = oracle.partition_bounds(26, 4, unit=2)
+    assert sizes == [8, 6, 6, 6] and starts == [0, 8, 14, 20]
