@@ -3,7 +3,8 @@
  *
  * The library solves many independent cyclic (periodic) compact banded linear
  * systems A x = b, tridiagonal (bandwidth w = 3), pentadiagonal (w = 5) or
- * heptadiagonal (w = 7, the generalised bands of Sec. 2, Eq. 3-6), one
+ * heptadiagonal (w = 7, the generalised bands of Sec. 2, Eq. 3-6), or
+ * block-tridiagonal with 2 x 2 block entries (Sec. 1; CBS_LHS_BLOCK), one
  * per grid line of a 3-D field, with the two-level partition method of Song et
  * al., "Scalable Parallel Linear Solver for Compact Banded Systems on
  * Heterogeneous Architectures" (arXiv 2101.02286):
