@@ -338,15 +338,17 @@ cbs_status cbs_interface_model(const cbs_desc* desc, int32_t p, double* dhat, do
 /* Ragged batch: up to `count` (<= 256) independent problems (each its own
  * cbs_desc, in and out arrays) solved together: by one persistent launch
  * over a work table, or by each problem's own launches (cbs_batch_set_mode).
- * The batch pre-builds every problem's plan tables and a work table of line
- * tiles.  Problems: Toeplitz bands of bandwidth 3 or 5; CBS_FP64 or
- * CBS_FP32_REFINE with FP64 in and out, or CBS_FP32 with FP32 in and out;
- * the central stencil or the right-hand side given; lines that fit one warp (on-chip plans), and long x-lines whose
+ * Any problem cbs_plan_create takes can be batched (the batch pre-builds
+ * every problem's plan).  The persistent launch takes: Toeplitz bands of
+ * bandwidth 3 or 5; CBS_FP64 or CBS_FP32_REFINE with FP64 in and out, or
+ * CBS_FP32 with FP32 in and out; the central stencil or the right-hand side
+ * given; lines that fit one warp (on-chip plans), and long x-lines whose
  * plan runs a warp per segment (cbs_plan_info.segment_warp = 1: right-hand
  * side given, segments of 32 x 16 + r rows), which enter the work table as
- * (chunk of 4 segments, line) items.  Allocates device memory, a stream
- * and two events at creation, none per solve.  Errors: UNSUPPORTED for other
- * problems. */
+ * (chunk of 4 segments, line) items.  A batch holding any other problem
+ * runs per problem.  Allocates device memory, a stream and two events at
+ * creation, none per solve.  Errors: those of cbs_plan_create for a
+ * problem (the message names it). */
 cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t count);
 cbs_status cbs_batch_destroy(cbs_batch* batch);
 /* How cbs_batch_solve runs a batch (the results are the same: every problem
@@ -359,8 +361,11 @@ cbs_status cbs_batch_destroy(cbs_batch* batch);
  *     within the call, so that they share the GPU with the others; one launch
  *     or more per problem;
  *   CBS_BATCH_AUTO (the default): per-problem launches when the problems
- *     hold 2^20 unknowns or more on average, else the persistent launch.
- * Errors: INVALID_ARG (NULL, mode not 0..2). */
+ *     hold 2^20 unknowns or more on average or the persistent launch does
+ *     not take one of them, else the persistent launch.
+ * Errors: INVALID_ARG (NULL, mode not 0..2), UNSUPPORTED (persistent
+ * launch asked for a batch holding a problem it does not take; the message
+ * names the first one). */
 enum { CBS_BATCH_AUTO = 0, CBS_BATCH_PERSISTENT = 1, CBS_BATCH_PER_PROBLEM = 2 };
 cbs_status cbs_batch_set_mode(cbs_batch* batch, int32_t mode);
 /* ins[k] / outs[k]: device arrays of problem k (host array of `count`

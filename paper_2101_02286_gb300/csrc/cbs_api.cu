@@ -1282,17 +1282,15 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   int nent = 0;
   std::vector<int4> items;
   std::vector<double> cost;
+  // every problem gets its plan (any problem a plan takes can be batched);
+  // the persistent launch takes the kinds below, and a batch holding any
+  // other problem runs per problem
+  auto not_persistent = [&](int k, const char* why) {
+    if (B->persistent) B->why = "batch problem " + std::to_string(k) + ": " + why;
+    B->persistent = false;
+  };
   for (int k = 0; k < count; k++) {
     const cbs_desc& d = descs[k];
-    const bool f32 = d.precision == CBS_FP32 && d.in_dtype == CBS_DTYPE_F32 && d.out_dtype == CBS_DTYPE_F32;
-    const bool f64io = d.in_dtype == CBS_DTYPE_F64 && d.out_dtype == CBS_DTYPE_F64 &&
-                       (d.precision == CBS_FP64 || d.precision == CBS_FP32_REFINE);
-    if (d.lhs_kind != CBS_LHS_TOEPLITZ || !(f32 || f64io) || is_staggered(&d) || d.closure_rows || d.bandwidth > 5) {
-      cbs_batch_destroy(B);
-      return fail(CBS_ERR_UNSUPPORTED,
-                  "batch problems: Toeplitz bands of width 3 or 5; FP64 or FP32_REFINE with FP64 in/out, or FP32 "
-                  "with FP32 in/out; no staggered stencil or closures");
-    }
     cbs_plan* P = nullptr;
     cbs_status st = cbs_plan_create(&P, &d);
     if (st) {
@@ -1301,15 +1299,23 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       return fail(st, msg);
     }
     B->plans.push_back(P);
+    B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
+    const bool f32 = d.precision == CBS_FP32 && d.in_dtype == CBS_DTYPE_F32 && d.out_dtype == CBS_DTYPE_F32;
+    const bool f64io = d.in_dtype == CBS_DTYPE_F64 && d.out_dtype == CBS_DTYPE_F64 &&
+                       (d.precision == CBS_FP64 || d.precision == CBS_FP32_REFINE);
+    if (d.lhs_kind != CBS_LHS_TOEPLITZ || !(f32 || f64io) || is_staggered(&d) || d.closure_rows || d.bandwidth > 5) {
+      not_persistent(k, "the persistent launch takes Toeplitz bands of width 3 or 5; FP64 or FP32_REFINE with "
+                        "FP64 in/out, or FP32 with FP32 in/out; no staggered stencil or closures");
+      continue;
+    }
     const int mode = d.precision == CBS_FP64 ? kModeF64 : d.precision == CBS_FP32 ? kModeF32 : kModeRefine;
     if (P->kind != 0) {
       // long lines: the x-lines of a warp-per-segment plan, an entry per
       // segment size, an item per (chunk of kLongWarps segments, line)
       if (!(P->long_warp && P->variant == 0) || P->lgeom.dir != 0 || batch_long_variant_host(P->r, mode) < 0) {
-        cbs_batch_destroy(B);
-        return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) +
-                                             ": long lines are batched as x-lines of a warp per segment "
-                                             "(segments of 32 x 16 + r rows, decoupled interface system)");
+        not_persistent(k, "the persistent launch takes long lines as x-lines of a warp per segment (segments of "
+                          "32 x 16 + r rows, decoupled interface system)");
+        continue;
       }
       const LongArgs& la = P->largs;
       for (int part = 0; part < 2; part++) {
@@ -1331,7 +1337,6 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
           }
         nent++;
       }
-      B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
       continue;
     }
     const bool full = P->dev.count_big == P->dev.p && P->dev.rows_big == 16 && P->M == 16;
@@ -1343,8 +1348,8 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
       if (variant < 0) variant = batch_variant_host(P->r, P->ks, P->M, mode, false);
     }
     if (variant < 0) {
-      cbs_batch_destroy(B);
-      return fail(CBS_ERR_UNSUPPORTED, "batch problem " + std::to_string(k) + ": tile variant not compiled");
+      not_persistent(k, "tile variant of the persistent launch not compiled");
+      continue;
     }
     probs.resize(pb * (nent + 1));
     batch_fill_problem(probs.data() + pb * nent, P->args, P->dev, variant, k);
@@ -1357,7 +1362,6 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
         items.push_back(make_int4(nent, (int)tx, (int)ty, 0));
         cost.push_back(c);
       }
-    B->unknowns += d.dims[0] * d.dims[1] * d.dims[2];
     nent++;
   }
   int dev = 0, sms = 0;
@@ -1380,11 +1384,14 @@ cbs_status cbs_batch_create(cbs_batch** out, const cbs_desc* descs, int32_t coun
   B->nitems = (int)sorted.size();
   B->count = count;
   B->smem = batch_smem(B->smem);  // + the current problem's tables
-  e = batch_configure(B->smem);
-  if (e == cudaSuccess) e = cudaMalloc(&B->dprobs, probs.size());
-  if (e == cudaSuccess) e = cudaMalloc(&B->ditems, sorted.size() * sizeof(int4));
-  if (e == cudaSuccess) e = cudaMemcpy(B->dprobs, probs.data(), probs.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(B->ditems, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (B->persistent) {  // the work table of the persistent launch
+    e = batch_configure(B->smem);
+    if (e == cudaSuccess) e = cudaMalloc(&B->dprobs, probs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->ditems, sorted.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMemcpy(B->dprobs, probs.data(), probs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(B->ditems, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cbs_batch_destroy(B);
     return cuda_fail(e, "batch setup");
@@ -1425,6 +1432,7 @@ cbs_status cbs_batch_destroy(cbs_batch* B) {
 cbs_status cbs_batch_set_mode(cbs_batch* B, int32_t mode) {
   if (!B) return fail(CBS_ERR_INVALID_ARG, "null batch");
   if (mode < CBS_BATCH_AUTO || mode > CBS_BATCH_PER_PROBLEM) return fail(CBS_ERR_INVALID_ARG, "batch mode must be 0, 1 or 2");
+  if (mode == CBS_BATCH_PERSISTENT && !B->persistent) return fail(CBS_ERR_UNSUPPORTED, B->why);
   B->mode = mode;
   return CBS_OK;
 }
@@ -1473,7 +1481,7 @@ cbs_status cbs_batch_solve(cbs_batch* B, const void* const* ins, void* const* ou
   if (!B || !ins || !outs) return fail(CBS_ERR_INVALID_ARG, "null argument");
   for (int k = 0; k < B->count; k++)
     if (!ins[k] || !outs[k] || ins[k] == outs[k]) return fail(CBS_ERR_INVALID_ARG, "bad pointer for problem " + std::to_string(k));
-  const bool per_problem = B->mode == CBS_BATCH_PER_PROBLEM ||
+  const bool per_problem = !B->persistent || B->mode == CBS_BATCH_PER_PROBLEM ||
                            (B->mode == CBS_BATCH_AUTO && B->unknowns >= (int64_t)B->count * kBatchPerProblemUnknowns);
   if (per_problem) return batch_solve_per_problem(B, ins, outs, (cudaStream_t)stream);
   cudaError_t e = batch_launch((const BatchProblem*)B->dprobs, (const int4*)B->ditems, B->nitems, ins, outs, B->count,

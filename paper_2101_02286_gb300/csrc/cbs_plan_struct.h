@@ -27,6 +27,8 @@ struct cbs_batch {
   size_t smem = 0;
   int64_t unknowns = 0;
   int mode = 0;                   // cbs_batch_set_mode
+  bool persistent = true;         // every problem fits the persistent launch
+  std::string why;                // else: the first problem that does not, and why
   int device = -1;                // device current at creation
   std::vector<int> order_fp64;    // per-problem launches: FP64 problems, largest first
   std::vector<int> order_other;   // the others, largest first

@@ -148,32 +148,38 @@ class Plan:
 class Batch:
     """A ragged batch of independent problems solved together.
 
-    specs: list of (shape_zyx, direction, kwargs for make_desc).  Toeplitz
-    bands; precision "fp64" or "fp32_refine" with FP64 input and output, or
-    "fp32" with FP32 input and output (in_dtype=torch.float32); long x-lines
-    whose plan runs a warp per segment.  mode: "auto", "persistent" (one
-    launch over a work table of line tiles) or "per_problem" (each problem's
-    own kernels, FP64 problems on a stream of their own).
+    specs: list of (shape_zyx, direction, kwargs for make_desc): any problem
+    a Plan takes.  mode: "auto", "persistent" (one launch over a work table
+    of line tiles: Toeplitz bands of width 3 or 5, precision "fp64" or
+    "fp32_refine" with FP64 input and output or "fp32" with FP32 input and
+    output, long x-lines whose plan runs a warp per segment) or
+    "per_problem" (each problem's own kernels, FP64 problems on a stream of
+    their own).
     """
 
     MODES = {"auto": abi.CBS_BATCH_AUTO, "persistent": abi.CBS_BATCH_PERSISTENT,
              "per_problem": abi.CBS_BATCH_PER_PROBLEM}
 
     def __init__(self, specs, mode: str = "auto"):
+        if mode not in self.MODES:
+            raise ValueError("mode must be one of %s" % sorted(self.MODES))
         self.shapes = [tuple(int(v) for v in sh) for sh, _, _ in specs]
         self.dtypes = [kw.get("in_dtype", torch.float64) for _, _, kw in specs]
+        self.out_dtypes = [kw.get("out_dtype") or (torch.float64 if kw.get("precision", "fp64") != "fp32"
+                                                   else kw.get("in_dtype", torch.float64)) for _, _, kw in specs]
         descs = [make_desc(sh, d, **kw) for sh, d, kw in specs]
         self.handle = abi.cbs_batch_create(descs)
-        if mode not in self.MODES:
+        try:
+            abi.cbs_batch_set_mode(self.handle, self.MODES[mode])
+        except abi.CbsError:
             self.close()
-            raise ValueError("mode must be one of %s" % sorted(self.MODES))
-        abi.cbs_batch_set_mode(self.handle, self.MODES[mode])
+            raise
 
     def solve(self, ins, outs=None, stream: torch.cuda.Stream | None = None):
         if outs is None:
-            outs = [torch.empty_like(x) for x in ins]
-        for x, y, sh, dt in zip(ins, outs, self.shapes, self.dtypes):
-            if x.shape != sh or y.shape != sh or x.dtype != dt or y.dtype != dt or not x.is_contiguous() \
+            outs = [torch.empty(sh, dtype=dt, device=x.device) for x, sh, dt in zip(ins, self.shapes, self.out_dtypes)]
+        for x, y, sh, dt, dto in zip(ins, outs, self.shapes, self.dtypes, self.out_dtypes):
+            if x.shape != sh or y.shape != sh or x.dtype != dt or y.dtype != dto or not x.is_contiguous() \
                     or not y.is_contiguous():
                 raise ValueError("batch inputs/outputs must be contiguous tensors of the planned shapes and dtypes")
         s = stream if stream is not None else torch.cuda.current_stream(ins[0].device)

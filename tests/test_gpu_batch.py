@@ -77,13 +77,37 @@ def test_ragged_batch_cuda_graph(cuda, mode):
     b.close()
 
 
-def test_batch_rejects_unsupported(cuda):
-    from paper_2101_02286_gb300.solver import make_desc
-    # heptadiagonal bands and FP32 input with an FP64 result stay single plans
-    for d in (make_desc((4, 4, 64), 0, lhs=W.HEPTA12["lhs"]),
-              make_desc((4, 4, 64), 0, lhs=(1 / 3,), precision="fp32_refine", in_dtype=torch.float32)):
-        with pytest.raises(abi.CbsError):
-            abi.cbs_batch_create([d])
+def test_batch_of_any_problems_runs_per_problem(cuda):
+    # heptadiagonal bands, FP32 input with an FP64 result, block entries and a
+    # staggered stencil do not fit the persistent launch: the batch takes
+    # them all and runs every problem's own kernels; asking for the
+    # persistent launch is refused
+    from paper_2101_02286_gb300.solver import Plan
+    blk = (np.array([[0.21, 0.07], [-0.05, 0.18]]), np.array([[1.0, 0.15], [-0.12, 0.9]]),
+           np.array([[0.24, -0.06], [0.04, 0.2]]))
+    specs = [((4, 6, 64), 0, dict(lhs=W.HEPTA12["lhs"])),
+             ((4, 64, 6), 1, dict(lhs=(1 / 3,), precision="fp32_refine", in_dtype=torch.float32)),
+             ((64, 4, 6), 2, dict(blocks=blk)),
+             ((4, 6, 64), 0, dict(lhs=W.STAGGERED6["lhs"], rhs=W.STAGGERED6["rhs"], h=0.1, stencil="staggered")),
+             ((4, 4, 64), 0, dict(lhs=(1 / 3,), rhs=(14 / 9, 1 / 9), h=0.1))]
+    with pytest.raises(abi.CbsError) as e:
+        Batch(specs, mode="persistent")
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED and "batch problem 0" in str(e.value)
+    b = Batch(specs)
+    rng = np.random.default_rng(8)
+    ins = [torch.from_numpy(rng.uniform(-1, 1, size=sh)).cuda().to(kw.get("in_dtype", torch.float64))
+           for sh, _, kw in specs]
+    outs = [torch.empty(sh, dtype=torch.float64, device="cuda") for sh, _, _ in specs]
+    b.solve(ins, outs)
+    torch.cuda.synchronize()
+    assert abi.cbs_last_launch_count() >= len(specs)
+    for (sh, d, kw), x, y in zip(specs, ins, outs):
+        pl = Plan(sh, d, **kw)
+        ref = pl.solve(x)
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref), (sh, d)  # the same kernels on the same input
+        pl.close()
+    b.close()
 
 
 @pytest.mark.slow
@@ -149,12 +173,25 @@ def test_batch_mixes_long_lines_with_grids(cuda, precision, mode):
     b.close()
 
 
-def test_batch_rejects_long_lines_off_the_warp_layout(cuda):
-    # long lines whose segments do not hold 32 x 16 rows stay separate plans
-    from paper_2101_02286_gb300.solver import make_desc
-    d = make_desc((1, 2, 1 << 16), 0, lhs=(1 / 3,), rhs=None, segments=16)
-    with pytest.raises(abi.CbsError):
-        abi.cbs_batch_create([d])
+def test_batch_long_lines_off_the_warp_layout_run_per_problem(cuda):
+    # long lines whose segments do not hold 32 x 16 rows (and y-lines) are not
+    # persistent-launch items; the batch runs their plans' own launches
+    from paper_2101_02286_gb300.solver import Plan
+    specs = [((1, 2, 1 << 16), 0, dict(lhs=(1 / 3,), rhs=None, segments=16)),
+             ((2, 4096, 4), 1, dict(lhs=W.PENTA10["lhs"], rhs=None, precision="fp32_refine"))]
+    with pytest.raises(abi.CbsError) as e:
+        Batch(specs, mode="persistent")
+    assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+    b = Batch(specs)
+    rng = np.random.default_rng(6)
+    data = [rng.standard_normal(sh) for sh, _, _ in specs]
+    outs = b.solve([torch.from_numpy(f).cuda() for f in data])
+    torch.cuda.synchronize()
+    ref0 = oracle.solve_cyclic(oracle.toeplitz_bands(1 << 16, (1 / 3,)), data[0][0])
+    assert oracle.rel_err(outs[0].cpu().numpy()[0], ref0) < 1e-12
+    ref1 = oracle.solve_cyclic(oracle.toeplitz_bands(4096, W.PENTA10["lhs"]), data[1], axis=1)
+    assert oracle.rel_err(outs[1].cpu().numpy(), ref1) < 1e-12
+    b.close()
 
 
 @pytest.mark.parametrize("mode", MODES)
