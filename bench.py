@@ -269,7 +269,7 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     from paper_2101_02286_gb300 import abi
     from paper_2101_02286_gb300 import workloads as W
     from paper_2101_02286_gb300.autograd import variable_plan
-    from paper_2101_02286_gb300.solver import Batch, Plan
+    from paper_2101_02286_gb300.solver import Batch, Plan, make_desc
     if check:
         import oracle
     res = []
@@ -322,9 +322,20 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
     items = W.ragged_batch()
     ins = [torch.from_numpy(it.f).to(dev) for it in items]
     unk = sum(int(np.prod(it.shape_zyx)) for it in items)
-    for mode, how in (("auto", "each problem's own kernels, FP64 problems on a second stream"),
-                      ("persistent", "one persistent launch")):
-        b = Batch(batch_specs(items), mode=mode)
+    # the persistent launch with the default partitions (the tuner may pick
+    # partition sizes that only the per-problem kernels take), then the
+    # autotuner on every problem, then the default mode with its choices
+    specs = batch_specs(items)
+    batches = {"persistent": Batch(specs, mode="persistent")}
+    t0 = time.perf_counter()
+    for sh, d, kw in specs:
+        abi.cbs_autotune(make_desc(sh, d, **kw), 3)
+    tune_s = time.perf_counter() - t0
+    batches["auto"] = Batch(specs)
+    for mode, how in (("auto", "each problem's own kernels (autotuned partitions and tiles), FP64 problems on a "
+                               "second stream"),
+                      ("persistent", "one persistent launch (default partitions)")):
+        b = batches[mode]
         outs = [torch.empty_like(x) for x in ins]
         side = torch.cuda.Stream(dev)
         side.wait_stream(stream)
@@ -352,7 +363,8 @@ def other_configs(dev, stream, steps: int, hbm: float, check: bool) -> list:
                 err = max(err, oracle.rel_err(np.stack([yl[i, j] for i, j in idx]), ref))
         res.append(_entry("ragged batch of 48 grids (sizes from {32..384} per axis, seed 3), mixed tri/penta, "
                           "fp64/fp32_refine, %s, under a CUDA graph" % how, unk, ms, 16, hbm, err,
-                          problems=len(items), mode=mode, launches_per_step=launches, sampled_lines=4 * len(items)))
+                          problems=len(items), mode=mode, launches_per_step=launches, sampled_lines=4 * len(items),
+                          **({"autotune_s": round(tune_s, 1)} if mode == "auto" else {})))
         b.close()
         del outs, g
     del ins, items
