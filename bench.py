@@ -68,6 +68,8 @@ def parse():
                          "(smaller captures of the same kernels)")
     ap.add_argument("--directions", default="0,1,2",
                     help="--profile: the line directions solved per step (0 = x, 1 = y, 2 = z)")
+    ap.add_argument("--batch-mode", default="persistent", choices=["persistent", "per_problem", "auto"],
+                    help="--profile --workload batch: how the batch runs (persistent: the one batch_kernel launch)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (64^3 Fourier, long lines, ragged batch, variable alpha)")
     return ap.parse_args()
@@ -551,14 +553,15 @@ def profile_other(args, dev, stream, rank):
     elif args.workload == "batch":
         from paper_2101_02286_gb300.solver import Batch
         items = W.ragged_batch()
-        b = Batch(batch_specs(items))
+        b = Batch(batch_specs(items), mode=args.batch_mode)
         ins = [torch.from_numpy(it.f).to(dev) for it in items]
         outs = [torch.empty_like(x) for x in ins]
         for _ in range(args.warmup + args.steps):
             b.solve(ins, outs, stream)
         torch.cuda.synchronize(dev)
         if rank == 0:
-            print(json.dumps({"profile": True, "workload": "batch", "problems": len(items)}))
+            print(json.dumps({"profile": True, "workload": "batch", "problems": len(items),
+                              "mode": args.batch_mode, "launches_per_step": abi.cbs_last_launch_count()}))
         b.close()
         return
     else:
