@@ -179,8 +179,20 @@ def test_round_trip_interpolation_is_near_identity(cuda):
     assert oracle.rel_err(back.cpu().numpy(), f) < 1e-7  # 2.8e-8 at n = 64
 
 
-def test_batch_rejects_staggered(cuda):
+def test_batch_runs_staggered_per_problem(cuda):
+    # the persistent batch launch has no staggered stencil: a batch holding
+    # one runs every problem's own kernels, and the persistent mode is refused
+    from paper_2101_02286_gb300.solver import Batch
     d = make_desc((2, 2, 64), 0, lhs=W.STAGGERED6["lhs"], rhs=W.STAGGERED6["rhs"], h=0.1, stencil="staggered")
+    h = abi.cbs_batch_create([d])
     with pytest.raises(abi.CbsError) as e:
-        abi.cbs_batch_create([d])
+        abi.cbs_batch_set_mode(h, abi.CBS_BATCH_PERSISTENT)
     assert e.value.status == abi.CBS_ERR_UNSUPPORTED
+    abi.cbs_batch_destroy(h)
+    b = Batch([((2, 2, 64), 0, dict(lhs=W.STAGGERED6["lhs"], rhs=W.STAGGERED6["rhs"], h=0.1, stencil="staggered"))])
+    f = np.random.default_rng(3).uniform(-1, 1, size=(2, 2, 64))
+    (y,) = b.solve([torch.from_numpy(f).cuda()])
+    torch.cuda.synchronize()
+    ref = oracle.staggered_derivative(f, W.STAGGERED6["lhs"], W.STAGGERED6["rhs"], 0.1, 0, axis=2)
+    assert oracle.rel_err(y.cpu().numpy(), ref) < 1e-12
+    b.close()
