@@ -290,7 +290,8 @@ cbs_status cbs_solve(cbs_plan* plan, const void* in, void* out, void* stream);
  * when x and grad_bands are both non-NULL, also writes the band gradient
  * grad_bands_i = -lambda_i (x_{i-1} + x_{i+1}) (same as cbs_band_grad).
  * g, x, lambda, grad_in, grad_bands: device, the plan's dims; g and x of
- * out_dtype, lambda / grad_in / grad_bands of in_dtype. */
+ * out_dtype, lambda / grad_in / grad_bands of in_dtype.  UNSUPPORTED for
+ * long-line and CBS_LHS_BLOCK plans. */
 cbs_status cbs_solve_transpose(cbs_plan* plan, const void* g, const void* x,
                                void* lambda, void* grad_in, void* grad_bands,
                                void* stream);
