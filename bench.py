@@ -57,10 +57,11 @@ def parse():
                     help="headline solves only (W + K steps of x, y, z), for profiler captures")
     ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64", "fp32"],
                     help="path run by --profile (the timed headline is always fp32_refine)")
-    ap.add_argument("--workload", default="cube", choices=["cube", "long", "var", "batch"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "long", "var", "batch", "block"],
                     help="what --profile runs: the n^3 field (cube), the 32 x 2^22 pentadiagonal lines "
                          "(long, FP32 right-hand side, refinement with 1 sweep, default segments), the "
-                         "256^3 variable-alpha forward + adjoint (var) or the ragged batch of 48 grids (batch)")
+                         "256^3 variable-alpha forward + adjoint (var), the ragged batch of 48 grids (batch) or "
+                         "256^2 x-lines of 256 points x 2 unknowns with 2 x 2 block entries (block)")
     ap.add_argument("--segments", default="tune",
                     help="partitions per line: 'tune' (autotuner) or a fixed count")
     ap.add_argument("--profile-shape", default=None,
@@ -532,8 +533,10 @@ def batch_specs(items):
 
 
 def profile_other(args, dev, stream, rank):
-    """--profile for the long-line or variable-alpha workload: W warm-up
-    and K further solves, nothing timed, for profiler captures."""
+    """--profile for the long-line, variable-alpha, batch or block-entry
+    workload: W warm-up and K further solves, nothing timed, for profiler
+    captures."""
+    import numpy as np
     import torch
     from paper_2101_02286_gb300 import abi
     from paper_2101_02286_gb300 import workloads as W
@@ -547,6 +550,18 @@ def profile_other(args, dev, stream, rank):
         prec = args.precision
         pl = Plan((1, lines, n), 0, lhs=W.PENTA10["lhs"], rhs=None, precision=prec, sweeps=1,
                   in_dtype=torch.float32)
+        for _ in range(args.warmup + args.steps):
+            pl.solve(di, do, stream)
+        info = pl.info()
+    elif args.workload == "block":
+        # 256^2 x-lines of 256 points x 2 unknowns, 2 x 2 block entries
+        blk = (np.array([[0.21, 0.07], [-0.05, 0.18]]), np.array([[1.0, 0.15], [-0.12, 0.9]]),
+               np.array([[0.24, -0.06], [0.04, 0.2]]))
+        shape = (256, 256, 512)
+        dt = torch.float64 if args.precision == "fp64" else torch.float32
+        di = torch.from_numpy(np.random.default_rng(23).standard_normal(shape)).to(dev, dt)
+        do = torch.empty_like(di)
+        pl = Plan(shape, 0, blocks=blk, precision="fp64" if dt == torch.float64 else "fp32", in_dtype=dt)
         for _ in range(args.warmup + args.steps):
             pl.solve(di, do, stream)
         info = pl.info()
