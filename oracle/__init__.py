@@ -303,6 +303,8 @@ def solve_cyclic(bands, d, axis=-1, method="auto"):
         assert r == 1
         rc = lib.orc_cyclic_tri(_ptr(b2), stride, _ptr(d2), _ptr(x), lines, n)
     else:
+        if n < 4 * r:  # the capacitance form keeps the 2r corner rows apart
+            raise ValueError("the banded Woodbury solve needs n >= 4r (n = %d, r = %d); use dense_solve" % (n, r))
         rc = lib.orc_cyclic_banded(_ptr(b2), stride, _ptr(d2), _ptr(x), lines, n, r)
     if rc:
         raise ArithmeticError("zero pivot in the oracle solve")

@@ -552,3 +552,13 @@ def test_block_kronecker_closed_form():
 def test_block_partition_bounds_keep_points_whole():
     starts, sizes = oracle.partition_bounds(26, 4, unit=2)
     assert sizes == [8, 6, 6, 6] and starts == [0, 8, 14, 20]
+
+
+def test_woodbury_size_limit_is_reported():
+    # n < 4r: the banded Woodbury path refuses with a clear message instead of
+    # a misleading pivot error; dense_solve covers such tiny systems
+    bands = oracle.toeplitz_bands(8, (0.3, 0.1, 0.02))
+    with pytest.raises(ValueError):
+        oracle.solve_cyclic(bands, np.ones(8))
+    x = oracle.dense_solve(oracle.dense_matrix(bands), np.ones(8))
+    assert np.allclose(oracle.dense_matrix(bands) @ x, 1.0)
